@@ -1,0 +1,150 @@
+"""ctypes front-end of the CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path never does: it shares
+no code with the oracle and fails loudly when its own CUDA library is missing.
+
+Every function is a thin numpy wrapper around ``muca_oracle.c``; see that file
+for the paper passages and the readings each step follows.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        i32, u32, i64, u64, dbl = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64,
+                                   ctypes.c_uint64, ctypes.c_double)
+        P = ctypes.c_void_p
+        L.or_philox4x32_10.argtypes = [P, P, P]
+        L.or_philox4x32_10.restype = None
+        L.or_init_spins.argtypes = [i32, u32, u32, P]
+        L.or_energies.argtypes = [i32, P, P]
+        L.or_build_table.argtypes = [i32, dbl, i32, i32, P, P]
+        L.or_sweeps.argtypes = [i32, i32, i32, P, u32, u32, u64, i32, P, P, P, P, i32]
+        L.or_update_lnW.argtypes = [i32, P, P]
+        L.or_muca_run.argtypes = [i32, dbl, i32, i32, i32, u32, u32, i32, i32, i32,
+                                  P, P, P, P, P, i32, i32]
+        L.or_reweight.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
+        L.or_reweight_q.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
+        for f in ("or_init_spins", "or_energies", "or_build_table", "or_sweeps",
+                  "or_update_lnW", "or_muca_run", "or_reweight", "or_reweight_q"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _ck(rc, what):
+    if rc != 0:
+        raise OracleError(f"{what} failed with code {rc}")
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def init_spins(L, seed, walker_id):
+    s = np.zeros(L ** 3, dtype=np.int8)
+    _ck(lib().or_init_spins(L, seed, walker_id, _p(s)), "init_spins")
+    return s
+
+
+def energies(L, spins):
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    out = np.zeros(3, dtype=np.int64)
+    _ck(lib().or_energies(L, _p(s), _p(out)), "energies")
+    return out
+
+
+def build_table(L, T, e_min, e_max, lnW):
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    nE = e_max - e_min + 1
+    assert lnW.shape == (nE,)
+    thr = np.zeros((nE, 3, 25), dtype=np.uint32)
+    _ck(lib().or_build_table(L, T, e_min, e_max, _p(lnW), _p(thr)), "build_table")
+    return thr
+
+
+def sweeps(L, e_min, e_max, thr, seed, walker_id, sweep0, n_sweeps, spins, tallies,
+           hist=None, record=False, check=False):
+    """Run n_sweeps on one walker in place; returns the time series or None."""
+    assert spins.dtype == np.int8 and spins.flags.c_contiguous
+    assert tallies.dtype == np.int32 and tallies.flags.c_contiguous
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    ts = np.zeros((n_sweeps, 3), dtype=np.int32) if record else None
+    if hist is not None:
+        assert hist.dtype == np.uint64 and hist.flags.c_contiguous
+    _ck(lib().or_sweeps(L, e_min, e_max, _p(thr), seed, walker_id, sweep0, n_sweeps,
+                        _p(spins), _p(tallies), _p(hist), _p(ts), int(check)), "sweeps")
+    return ts
+
+
+def update_lnW(H, lnW):
+    H = np.ascontiguousarray(H, dtype=np.uint64)
+    assert lnW.dtype == np.float64 and lnW.flags.c_contiguous
+    _ck(lib().or_update_lnW(len(H), _p(H), _p(lnW)), "update_lnW")
+
+
+def muca_run(L, T, n_walkers, seed, n_iter, sweeps_per_iter, n_meas=0, e_min=0, e_max=None,
+             walker_id0=0, lnW=None, check=False, n_threads=None, want_spins=True):
+    """A whole run of one (L, T) group; returns a dict of numpy arrays."""
+    V = L ** 3
+    if e_max is None:
+        e_max = V
+    nE = e_max - e_min + 1
+    lnW = np.zeros(nE) if lnW is None else np.array(lnW, dtype=np.float64, copy=True)
+    hist = np.zeros((max(n_iter, 1), nE), dtype=np.uint64)
+    spins = np.zeros((n_walkers, V), dtype=np.int8) if want_spins else None
+    tal = np.zeros((n_walkers, 3), dtype=np.int32)
+    ts = np.zeros((n_walkers, n_meas, 3), dtype=np.int32) if n_meas > 0 else None
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    _ck(lib().or_muca_run(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
+                          sweeps_per_iter, n_meas, _p(lnW), _p(hist), _p(spins), _p(tal),
+                          _p(ts), int(check), n_threads), "muca_run")
+    return {"lnW": lnW, "hist": hist[:n_iter], "spins": spins, "tallies": tal, "ts": ts}
+
+
+def _rw(fn, e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads):
+    e_j = np.ascontiguousarray(e_j, dtype=np.int32).ravel()
+    e_d = np.ascontiguousarray(e_d, dtype=np.int32).ravel()
+    m = np.ascontiguousarray(m, dtype=np.int32).ravel()
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    grid = np.ascontiguousarray(grid, dtype=np.float64)
+    out = np.zeros((len(grid), 5))
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    _ck(fn(_p(e_j), _p(e_d), _p(m), len(e_d), _p(lnW), e_min, len(lnW), beta, V, _p(grid),
+           len(grid), n_threads, _p(out)), "reweight")
+    return out
+
+
+def reweight(e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads=None):
+    """FP64 reweighting; columns <E_J>, <E_Delta>, C, chi, U4."""
+    return _rw(lib().or_reweight, e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads)
+
+
+def reweight_q(e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads=None):
+    """binary128 reweighting (rounded to FP64 on output)."""
+    return _rw(lib().or_reweight_q, e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads)

@@ -1,0 +1,606 @@
+/*
+ * muca_oracle.c -- plain CPU oracle for the parallel multicanonical (MUCA)
+ * Blume-Capel hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code
+ * with the CUDA library; it is written to be read against the paper, not to be
+ * fast: every random word is regenerated where it is used, every neighbour sum
+ * is taken with explicit modular coordinates, and the table and the
+ * reweighting follow their definitions term by term.
+ *
+ * What the paper fixes (Zierenberg, Fytas, Janke, "Parallel multicanonical
+ * study of the three-dimensional Blume-Capel model"):
+ *   - Eq. 1: H = -J sum_<ij> s_i s_j + Delta sum_i s_i^2 = E_J + Delta E_Delta,
+ *     s_i in {-1, 0, +1}, J = 1, k_B = 1, periodic simple-cubic lattice (Sec. I).
+ *   - Sec. II: the Boltzmann factor exp(-beta E_J) exp(-beta Delta E_Delta) is
+ *     replaced by exp(-beta E_J) W(E_Delta); W is adapted iteratively to a flat
+ *     E_Delta histogram; p walkers share W and their histograms are merged.
+ *   - Sec. II, Eq. 3: time-series reweighting to (beta, Delta) with the factor
+ *     exp(-beta Delta E_Delta) / W(E_Delta).
+ *   - Eq. 6: C(Delta) = -beta (<E_J E_Delta> - <E_J><E_Delta>).
+ *   - Sec. II: E_Delta is an integer in [0, V].
+ *
+ * Readings where the paper is silent (each one is also a decision the CUDA
+ * library takes independently):
+ *   R1 site index i = x + L (y + L z); E_J sums the three forward bonds of every
+ *      site (at L = 2 the two bonds between a pair are both counted, matching
+ *      the six-neighbour local field).
+ *   R2 single-site Metropolis in typewriter order i = 0 .. V-1; the proposal is
+ *      one of the two values different from s_i, picked with probability 1/2.
+ *   R3 random numbers: Philox4x32-10 with key (walker id, seed) and counter
+ *      (site >> 2, sweep low word, sweep high word, stream); stream 0 drives the
+ *      updates, stream 1 the initial spins.  Each 32-bit output word serves one
+ *      site (site & 3 selects the word): bit 31 picks the proposal (0 = the
+ *      smaller, 1 = the larger of the two other values), bits 0..30 are the
+ *      uniform draw u in [0, 2^31).
+ *   R4 acceptance: the proposal is rejected if E_Delta + d leaves the window
+ *      [e_min, e_max]; otherwise it is accepted iff u < thr[E_Delta][d][dE_J]
+ *      with thr = 2^31 when x >= 0 and floor(exp(x) 2^31) otherwise, where
+ *      x = -beta dE_J + (lnW[E_Delta + d] - lnW[E_Delta]) in FP64.  thr is 0 when
+ *      E_Delta + d lies outside the window.
+ *   R5 one histogram entry per walker per sweep, after the sweep.
+ *   R6 weight recursion lnW <- lnW - ln H where H > 0, starting from lnW = 0
+ *      (the paper cites the standard recursion without printing it).
+ *   R7 the global sweep index counts every sweep of a walker from 0 (weight
+ *      iterations first, then measurement sweeps).
+ *   R8 chi = beta V (<m^2> - <|m|>^2) and U4 = 1 - <m^4>/(3 <m^2>^2), m = M/V
+ *      (the paper names chi without defining it and does not use U4).
+ */
+#include "muca_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from its published definition (SC'11, "Parallel random     */
+/* numbers: as easy as 1, 2, 3"): ten rounds of two 32x32->64 multiplies,    */
+/* with a Weyl-sequence key schedule between rounds.                          */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += weyl0;
+            k1 += weyl1;
+        }
+        uint64_t p0 = (uint64_t)mult0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)mult1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* The random word of site i in sweep s on the given stream (reading R3). */
+static uint32_t site_word(uint32_t seed, uint32_t walker_id, uint64_t sweep, int64_t site,
+                          uint32_t stream)
+{
+    uint32_t ctr[4], key[2], r[4];
+    ctr[0] = (uint32_t)(site >> 2);
+    ctr[1] = (uint32_t)(sweep & 0xFFFFFFFFu);
+    ctr[2] = (uint32_t)(sweep >> 32);
+    ctr[3] = stream;
+    key[0] = walker_id;
+    key[1] = seed;
+    or_philox4x32_10(ctr, key, r);
+    return r[site & 3];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lattice (Eq. 1, reading R1).                                               */
+/* ------------------------------------------------------------------------ */
+static int64_t site_of(int L, int x, int y, int z)
+{
+    return (int64_t)x + (int64_t)L * ((int64_t)y + (int64_t)L * (int64_t)z);
+}
+
+static int wrap(int a, int L) { return ((a % L) + L) % L; }
+
+/* Sum of the six nearest neighbours of (x, y, z) as currently stored. */
+static int local_field(int L, const int8_t *s, int x, int y, int z)
+{
+    int h = 0;
+    h += s[site_of(L, wrap(x + 1, L), y, z)];
+    h += s[site_of(L, wrap(x - 1, L), y, z)];
+    h += s[site_of(L, x, wrap(y + 1, L), z)];
+    h += s[site_of(L, x, wrap(y - 1, L), z)];
+    h += s[site_of(L, x, y, wrap(z + 1, L))];
+    h += s[site_of(L, x, y, wrap(z - 1, L))];
+    return h;
+}
+
+int or_energies(int L, const int8_t *s, int64_t out[3])
+{
+    if (L < 2 || !s || !out) return OR_ERR_ARG;
+    int64_t ej = 0, ed = 0, m = 0;
+    for (int z = 0; z < L; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                int si = s[site_of(L, x, y, z)];
+                ej -= si * s[site_of(L, wrap(x + 1, L), y, z)];
+                ej -= si * s[site_of(L, x, wrap(y + 1, L), z)];
+                ej -= si * s[site_of(L, x, y, wrap(z + 1, L))];
+                ed += si * si;
+                m += si;
+            }
+    out[0] = ej;
+    out[1] = ed;
+    out[2] = m;
+    return OR_OK;
+}
+
+int or_init_spins(int L, uint32_t seed, uint32_t walker_id, int8_t *spins)
+{
+    if (L < 2 || !spins) return OR_ERR_ARG;
+    int64_t V = (int64_t)L * L * L;
+    for (int64_t i = 0; i < V; ++i) {
+        uint32_t w = site_word(seed, walker_id, 0, i, 1u);
+        /* floor(3 w / 2^32) is uniform on {0, 1, 2} up to 2^-32 bias */
+        int v = (int)(((uint64_t)w * 3u) >> 32);
+        spins[i] = (int8_t)(v - 1);
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Acceptance table (reading R4).                                             */
+/* ------------------------------------------------------------------------ */
+static uint32_t threshold_of(double x)
+{
+    if (x >= 0.0) return 0x80000000u;
+    double p = exp(x);
+    double t = floor(p * 2147483648.0);
+    if (t >= 2147483648.0) return 0x80000000u;
+    return (uint32_t)t;
+}
+
+int or_build_table(int L, double T, int e_min, int e_max, const double *lnW, uint32_t *thr)
+{
+    if (L < 2 || !(T > 0.0) || !lnW || !thr) return OR_ERR_ARG;
+    int64_t V = (int64_t)L * L * L;
+    if (e_min < 0 || e_max > V || e_min > e_max) return OR_ERR_ARG;
+    double beta = 1.0 / T;
+    int nE = e_max - e_min + 1;
+    for (int e = 0; e < nE; ++e) {
+        for (int d = -1; d <= 1; ++d) {
+            for (int dej = -12; dej <= 12; ++dej) {
+                uint32_t t;
+                int en = e + d;
+                if (en < 0 || en >= nE) {
+                    t = 0u;
+                } else {
+                    double x = -(beta * (double)dej) + (lnW[en] - lnW[e]);
+                    t = threshold_of(x);
+                }
+                thr[((int64_t)e * 3 + (d + 1)) * OR_NK + (dej + 12)] = t;
+            }
+        }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Typewriter Metropolis sweeps (Sec. II; readings R2-R5, R7).                */
+/* ------------------------------------------------------------------------ */
+int or_sweeps(int L, int e_min, int e_max, const uint32_t *thr, uint32_t seed,
+              uint32_t walker_id, uint64_t sweep0, int n_sweeps, int8_t *spins,
+              int32_t tallies[3], uint64_t *hist, int32_t *ts, int check)
+{
+    if (L < 2 || !thr || !spins || !tallies || n_sweeps < 0) return OR_ERR_ARG;
+    int64_t ej = tallies[0], ed = tallies[1], m = tallies[2];
+    if (ed < e_min || ed > e_max) return OR_ERR_WINDOW;
+    for (int k = 0; k < n_sweeps; ++k) {
+        uint64_t sweep = sweep0 + (uint64_t)k;
+        for (int z = 0; z < L; ++z)
+            for (int y = 0; y < L; ++y)
+                for (int x = 0; x < L; ++x) {
+                    int64_t i = site_of(L, x, y, z);
+                    uint32_t w = site_word(seed, walker_id, sweep, i, 0u);
+                    uint32_t b = w >> 31;
+                    uint32_t u = w & 0x7FFFFFFFu;
+                    int s = spins[i];
+                    /* the two values different from s, in ascending order */
+                    int other[2], n = 0;
+                    for (int v = -1; v <= 1; ++v)
+                        if (v != s) other[n++] = v;
+                    int sp = other[b];
+                    int h = local_field(L, spins, x, y, z);
+                    int dej = -(sp - s) * h;
+                    int d = sp * sp - s * s;
+                    int64_t en = ed + d;
+                    if (en < e_min || en > e_max) continue;
+                    uint32_t t = thr[((ed - e_min) * 3 + (d + 1)) * OR_NK + (dej + 12)];
+                    if (u < t) {
+                        spins[i] = (int8_t)sp;
+                        ej += dej;
+                        ed = en;
+                        m += sp - s;
+                    }
+                }
+        if (hist) hist[ed - e_min] += 1;
+        if (ts) {
+            ts[3 * (int64_t)k + 0] = (int32_t)ej;
+            ts[3 * (int64_t)k + 1] = (int32_t)ed;
+            ts[3 * (int64_t)k + 2] = (int32_t)m;
+        }
+        if (check) {
+            int64_t e[3];
+            or_energies(L, spins, e);
+            if (e[0] != ej || e[1] != ed || e[2] != m) return OR_ERR_TALLY;
+        }
+    }
+    tallies[0] = (int32_t)ej;
+    tallies[1] = (int32_t)ed;
+    tallies[2] = (int32_t)m;
+    return OR_OK;
+}
+
+int or_update_lnW(int nE, const uint64_t *H, double *lnW)
+{
+    if (nE <= 0 || !H || !lnW) return OR_ERR_ARG;
+    for (int e = 0; e < nE; ++e)
+        if (H[e] > 0) lnW[e] -= log((double)H[e]);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* A whole run of one group: walkers are independent given the table, so the */
+/* walkers of an iteration are split over threads; histograms are summed.    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int L, e_min, e_max, check;
+    const uint32_t *thr;
+    uint32_t seed, walker_id0;
+    uint64_t sweep0;
+    int n_sweeps;
+    int w_begin, w_end;
+    int8_t *spins;       /* [n_walkers][V] */
+    int32_t *tallies;    /* [n_walkers][3] */
+    uint64_t *hist;      /* [nE], private to the job */
+    int32_t *ts;         /* [n_walkers][n_sweeps][3] or NULL */
+    int status;
+} sweep_job;
+
+static void *sweep_job_run(void *arg)
+{
+    sweep_job *j = (sweep_job *)arg;
+    int64_t V = (int64_t)j->L * j->L * j->L;
+    j->status = OR_OK;
+    for (int w = j->w_begin; w < j->w_end; ++w) {
+        int rc = or_sweeps(j->L, j->e_min, j->e_max, j->thr, j->seed,
+                           j->walker_id0 + (uint32_t)w, j->sweep0, j->n_sweeps,
+                           j->spins + (int64_t)w * V, j->tallies + 3 * (int64_t)w, j->hist,
+                           j->ts ? j->ts + (int64_t)w * j->n_sweeps * 3 : NULL, j->check);
+        if (rc != OR_OK) {
+            j->status = rc;
+            return NULL;
+        }
+    }
+    return NULL;
+}
+
+static int sweep_all(int n_walkers, int n_threads, int nE, sweep_job proto, uint64_t *hist_sum)
+{
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_walkers) n_threads = n_walkers;
+    sweep_job *jobs = (sweep_job *)calloc((size_t)n_threads, sizeof(sweep_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    uint64_t *h = (uint64_t *)calloc((size_t)n_threads * (size_t)nE, sizeof(uint64_t));
+    if (!jobs || !tid || !h) {
+        free(jobs);
+        free(tid);
+        free(h);
+        return OR_ERR_NOMEM;
+    }
+    for (int t = 0; t < n_threads; ++t) {
+        jobs[t] = proto;
+        jobs[t].w_begin = (int)((int64_t)n_walkers * t / n_threads);
+        jobs[t].w_end = (int)((int64_t)n_walkers * (t + 1) / n_threads);
+        jobs[t].hist = h + (size_t)t * nE;
+    }
+    for (int t = 1; t < n_threads; ++t) pthread_create(&tid[t], NULL, sweep_job_run, &jobs[t]);
+    sweep_job_run(&jobs[0]);
+    for (int t = 1; t < n_threads; ++t) pthread_join(tid[t], NULL);
+    int status = OR_OK;
+    for (int t = 0; t < n_threads; ++t) {
+        if (jobs[t].status != OR_OK) status = jobs[t].status;
+        if (hist_sum)
+            for (int e = 0; e < nE; ++e) hist_sum[e] += h[(size_t)t * nE + e];
+    }
+    free(jobs);
+    free(tid);
+    free(h);
+    return status;
+}
+
+int or_muca_run(int L, double T, int n_walkers, int e_min, int e_max, uint32_t seed,
+                uint32_t walker_id0, int n_iter, int sweeps_per_iter, int n_meas,
+                double *lnW, uint64_t *hist_iter, int8_t *spins_out,
+                int32_t *tallies_out, int32_t *ts, int check, int n_threads)
+{
+    if (L < 2 || !(T > 0.0) || n_walkers < 1 || n_iter < 0 || sweeps_per_iter < 0 ||
+        n_meas < 0 || !lnW)
+        return OR_ERR_ARG;
+    int64_t V = (int64_t)L * L * L;
+    if (e_min < 0 || e_max > V || e_min > e_max) return OR_ERR_ARG;
+    int nE = e_max - e_min + 1;
+    int8_t *spins = (int8_t *)malloc((size_t)n_walkers * (size_t)V);
+    int32_t *tal = (int32_t *)malloc((size_t)n_walkers * 3 * sizeof(int32_t));
+    uint32_t *thr = (uint32_t *)malloc((size_t)nE * 3 * OR_NK * sizeof(uint32_t));
+    uint64_t *hist = (uint64_t *)malloc((size_t)nE * sizeof(uint64_t));
+    int rc = OR_OK;
+    if (!spins || !tal || !thr || !hist) {
+        rc = OR_ERR_NOMEM;
+        goto done;
+    }
+    for (int w = 0; w < n_walkers; ++w) {
+        int8_t *s = spins + (int64_t)w * V;
+        or_init_spins(L, seed, walker_id0 + (uint32_t)w, s);
+        int64_t e[3];
+        or_energies(L, s, e);
+        if (e[1] < e_min || e[1] > e_max) {
+            rc = OR_ERR_WINDOW;
+            goto done;
+        }
+        tal[3 * w + 0] = (int32_t)e[0];
+        tal[3 * w + 1] = (int32_t)e[1];
+        tal[3 * w + 2] = (int32_t)e[2];
+    }
+    uint64_t sweep = 0;
+    sweep_job proto;
+    memset(&proto, 0, sizeof proto);
+    proto.L = L;
+    proto.e_min = e_min;
+    proto.e_max = e_max;
+    proto.check = check;
+    proto.thr = thr;
+    proto.seed = seed;
+    proto.walker_id0 = walker_id0;
+    proto.spins = spins;
+    proto.tallies = tal;
+    or_build_table(L, T, e_min, e_max, lnW, thr);
+    for (int it = 0; it < n_iter; ++it) {
+        memset(hist, 0, (size_t)nE * sizeof(uint64_t));
+        proto.sweep0 = sweep;
+        proto.n_sweeps = sweeps_per_iter;
+        proto.ts = NULL;
+        rc = sweep_all(n_walkers, n_threads, nE, proto, hist);
+        if (rc != OR_OK) goto done;
+        sweep += (uint64_t)sweeps_per_iter;
+        if (hist_iter) memcpy(hist_iter + (size_t)it * nE, hist, (size_t)nE * sizeof(uint64_t));
+        or_update_lnW(nE, hist, lnW);
+        or_build_table(L, T, e_min, e_max, lnW, thr);
+    }
+    if (n_meas > 0) {
+        proto.sweep0 = sweep;
+        proto.n_sweeps = n_meas;
+        proto.ts = ts;
+        rc = sweep_all(n_walkers, n_threads, nE, proto, NULL);
+        if (rc != OR_OK) goto done;
+    }
+    if (spins_out) memcpy(spins_out, spins, (size_t)n_walkers * (size_t)V);
+    if (tallies_out) memcpy(tallies_out, tal, (size_t)n_walkers * 3 * sizeof(int32_t));
+done:
+    free(spins);
+    free(tal);
+    free(thr);
+    free(hist);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Time-series reweighting (Eq. 3) and the observables (Eq. 6, reading R8).   */
+/* For every Delta_k the exponent a_s = -beta Delta_k E_Delta,s - lnW(E_Delta,s) */
+/* is shifted by its maximum over the samples before exponentiation (the     */
+/* weights span hundreds of decades) and all sums are compensated (Neumaier). */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double s, c;
+} nsum;
+
+static void nsum_add(nsum *a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static double nsum_get(const nsum *a) { return a->s + a->c; }
+
+typedef struct {
+    const int32_t *e_j, *e_d, *m;
+    int64_t n;
+    const double *lnW;
+    int e_min, nE, V;
+    double beta;
+    const double *grid;
+    int k_begin, k_end;
+    double *out;
+} rw_job;
+
+static void reweight_one(const rw_job *j, int k)
+{
+    double c = j->beta * j->grid[k];
+    double amax = -INFINITY;
+    for (int64_t s = 0; s < j->n; ++s) {
+        double a = -(c * (double)j->e_d[s]) - j->lnW[j->e_d[s] - j->e_min];
+        if (a > amax) amax = a;
+    }
+    nsum z = {0, 0}, sj = {0, 0}, sd = {0, 0}, sjd = {0, 0}, sm1 = {0, 0}, sm2 = {0, 0},
+         sm4 = {0, 0};
+    for (int64_t s = 0; s < j->n; ++s) {
+        double a = -(c * (double)j->e_d[s]) - j->lnW[j->e_d[s] - j->e_min];
+        double w = exp(a - amax);
+        double ej = (double)j->e_j[s], ed = (double)j->e_d[s];
+        double mm = (double)j->m[s] / (double)j->V;
+        nsum_add(&z, w);
+        nsum_add(&sj, w * ej);
+        nsum_add(&sd, w * ed);
+        nsum_add(&sjd, w * (ej * ed));
+        nsum_add(&sm1, w * fabs(mm));
+        nsum_add(&sm2, w * (mm * mm));
+        nsum_add(&sm4, w * ((mm * mm) * (mm * mm)));
+    }
+    double Z = nsum_get(&z);
+    double mj = nsum_get(&sj) / Z, md = nsum_get(&sd) / Z, mjd = nsum_get(&sjd) / Z;
+    double m1 = nsum_get(&sm1) / Z, m2 = nsum_get(&sm2) / Z, m4 = nsum_get(&sm4) / Z;
+    double *o = j->out + 5 * (int64_t)k;
+    o[0] = mj;
+    o[1] = md;
+    o[2] = -j->beta * (mjd - mj * md);
+    o[3] = j->beta * (double)j->V * (m2 - m1 * m1);
+    o[4] = 1.0 - m4 / (3.0 * m2 * m2);
+}
+
+static void *rw_job_run(void *arg)
+{
+    rw_job *j = (rw_job *)arg;
+    for (int k = j->k_begin; k < j->k_end; ++k) reweight_one(j, k);
+    return NULL;
+}
+
+static int rw_check(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n,
+                    const double *lnW, int e_min, int nE, int V, const double *grid,
+                    int n_grid, const double *out)
+{
+    if (!e_j || !e_d || !m || n < 1 || !lnW || nE < 1 || V < 1 || !grid || n_grid < 0 || !out)
+        return OR_ERR_ARG;
+    for (int64_t s = 0; s < n; ++s)
+        if (e_d[s] < e_min || e_d[s] >= e_min + nE) return OR_ERR_WINDOW;
+    return OR_OK;
+}
+
+int or_reweight(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n,
+                const double *lnW, int e_min, int nE, double beta, int V,
+                const double *grid, int n_grid, int n_threads, double *out)
+{
+    int rc = rw_check(e_j, e_d, m, n, lnW, e_min, nE, V, grid, n_grid, out);
+    if (rc != OR_OK) return rc;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_grid) n_threads = n_grid > 0 ? n_grid : 1;
+    rw_job *jobs = (rw_job *)calloc((size_t)n_threads, sizeof(rw_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    if (!jobs || !tid) {
+        free(jobs);
+        free(tid);
+        return OR_ERR_NOMEM;
+    }
+    for (int t = 0; t < n_threads; ++t) {
+        rw_job j = {e_j, e_d, m, n, lnW, e_min, nE, V, beta, grid,
+                    (int)((int64_t)n_grid * t / n_threads),
+                    (int)((int64_t)n_grid * (t + 1) / n_threads), out};
+        jobs[t] = j;
+    }
+    for (int t = 1; t < n_threads; ++t) pthread_create(&tid[t], NULL, rw_job_run, &jobs[t]);
+    rw_job_run(&jobs[0]);
+    for (int t = 1; t < n_threads; ++t) pthread_join(tid[t], NULL);
+    free(jobs);
+    free(tid);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* binary128 variant: the same definition evaluated with 113-bit mantissas,  */
+/* used to measure the error of the FP64 oracle itself.                       */
+/* ------------------------------------------------------------------------ */
+#if defined(__aarch64__) || defined(__powerpc64__)
+typedef long double qreal;
+#define QEXP expl
+#define QFABS fabsl
+#else
+#include <quadmath.h>
+typedef __float128 qreal;
+#define QEXP expq
+#define QFABS fabsq
+#endif
+
+static void reweight_one_q(const rw_job *j, int k)
+{
+    qreal c = (qreal)j->beta * (qreal)j->grid[k];
+    qreal amax = 0;
+    int first = 1;
+    for (int64_t s = 0; s < j->n; ++s) {
+        qreal a = -(c * (qreal)j->e_d[s]) - (qreal)j->lnW[j->e_d[s] - j->e_min];
+        if (first || a > amax) amax = a;
+        first = 0;
+    }
+    qreal z = 0, sj = 0, sd = 0, sjd = 0, sm1 = 0, sm2 = 0, sm4 = 0;
+    for (int64_t s = 0; s < j->n; ++s) {
+        qreal a = -(c * (qreal)j->e_d[s]) - (qreal)j->lnW[j->e_d[s] - j->e_min];
+        qreal w = QEXP(a - amax);
+        qreal ej = (qreal)j->e_j[s], ed = (qreal)j->e_d[s];
+        qreal mm = (qreal)j->m[s] / (qreal)j->V;
+        z += w;
+        sj += w * ej;
+        sd += w * ed;
+        sjd += w * (ej * ed);
+        sm1 += w * QFABS(mm);
+        sm2 += w * (mm * mm);
+        sm4 += w * ((mm * mm) * (mm * mm));
+    }
+    qreal mj = sj / z, md = sd / z, mjd = sjd / z, m1 = sm1 / z, m2 = sm2 / z, m4 = sm4 / z;
+    qreal beta = (qreal)j->beta;
+    double *o = j->out + 5 * (int64_t)k;
+    o[0] = (double)mj;
+    o[1] = (double)md;
+    o[2] = (double)(-beta * (mjd - mj * md));
+    o[3] = (double)(beta * (qreal)j->V * (m2 - m1 * m1));
+    o[4] = (double)(1 - m4 / (3 * m2 * m2));
+}
+
+static void *rw_job_run_q(void *arg)
+{
+    rw_job *j = (rw_job *)arg;
+    for (int k = j->k_begin; k < j->k_end; ++k) reweight_one_q(j, k);
+    return NULL;
+}
+
+int or_reweight_q(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n,
+                  const double *lnW, int e_min, int nE, double beta, int V,
+                  const double *grid, int n_grid, int n_threads, double *out)
+{
+    int rc = rw_check(e_j, e_d, m, n, lnW, e_min, nE, V, grid, n_grid, out);
+    if (rc != OR_OK) return rc;
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > n_grid) n_threads = n_grid > 0 ? n_grid : 1;
+    rw_job *jobs = (rw_job *)calloc((size_t)n_threads, sizeof(rw_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)n_threads, sizeof(pthread_t));
+    if (!jobs || !tid) {
+        free(jobs);
+        free(tid);
+        return OR_ERR_NOMEM;
+    }
+    for (int t = 0; t < n_threads; ++t) {
+        rw_job j = {e_j, e_d, m, n, lnW, e_min, nE, V, beta, grid,
+                    (int)((int64_t)n_grid * t / n_threads),
+                    (int)((int64_t)n_grid * (t + 1) / n_threads), out};
+        jobs[t] = j;
+    }
+    for (int t = 1; t < n_threads; ++t) pthread_create(&tid[t], NULL, rw_job_run_q, &jobs[t]);
+    rw_job_run_q(&jobs[0]);
+    for (int t = 1; t < n_threads; ++t) pthread_join(tid[t], NULL);
+    free(jobs);
+    free(tid);
+    return OR_OK;
+}
