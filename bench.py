@@ -1,0 +1,393 @@
+"""Benchmark of the multicanonical Blume-Capel hot path on one GB300.
+
+Workload (N=1): the large first-order configuration, L=48 (110592 sites),
+T=0.9, 4096 walkers, seed 3.  One step is one pass of the whole hot path in
+the production schedule of that workload (40 iterations x 1000 sweeps, then
+10^4 measurement sweeps, i.e. 250 measurement sweeps per iteration):
+  1000 typewriter Metropolis sweeps of every walker with the per-sweep
+  histogram, the merge, the FP64 weight update and the acceptance-table
+  rebuild (one CUDA-graph iteration), then 250 recorded measurement sweeps and
+  the FP32 reweighting of the step's series to a 4096-point Delta grid.
+Metric: spin-update attempts per second (accepted or not) = walkers x L^3 x
+sweeps / time.  "batched" is the graph form, "plain" the same work with one
+launch per call and host-driven merges.  The reweighting sub-benchmark times
+the FP32 and FP64 paths on a 4096-walker x 10^4-sample series of an L=32,
+T=1.4182 run (Delta-grid points per second).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle on the host cores instead (bounded
+walker samples of the same workload).  Under torchrun (N > 1) every rank runs
+an independent replica of the workload (walkers are independent given the
+weights; the histogram merge would be one integer all-reduce and is not
+needed for replicas), timed with a barrier and the maximum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1502_07214_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "spin-update attempts/s at L=48 T=0.9 (batched)"
+UNIT = "attempts/s"
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            with open(p) as f:
+                d = json.load(f)
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    s = wl.LARGE
+    L, T = s["L"], s["T"]
+    V = L ** 3
+    cores = os.cpu_count() or 1
+    # calibrate: one sweep of one walker per core
+    t0 = time.perf_counter()
+    oracle.muca_run(L, T, cores, s["seed"], 1, 1, n_threads=cores, want_spins=False)
+    t1 = time.perf_counter() - t0
+    sweeps = max(1, min(200, int(6.0 / max(t1, 1e-3))))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.muca_run(L, T, cores, s["seed"], 1, sweeps, n_threads=cores, want_spins=False)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    attempts = cores * V * sweeps
+    tot = sum(times)
+    value = attempts * len(times) / tot
+    sample = (f"{cores} walkers (one per core) x {sweeps} sweeps of L={L}, T={T} per step, "
+              f"one weight update per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "L=48 T=0.9 multicanonical sweeps (oracle sample)",
+                   "L": L, "T": T, "walkers": cores, "sweeps_per_step": sweeps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline_sample():
+    """The oracle as it stands on the host cores, on a bounded walker sample."""
+    import oracle
+
+    s = wl.LARGE
+    L, T = s["L"], s["T"]
+    V = L ** 3
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.muca_run(L, T, cores, s["seed"], 1, 1, n_threads=cores, want_spins=False)
+    t1 = time.perf_counter() - t0
+    sweeps = max(1, min(400, int(12.0 / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.muca_run(L, T, cores, s["seed"], 1, sweeps, n_threads=cores, want_spins=False)
+    dt = time.perf_counter() - t0
+    return {"value": cores * V * sweeps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} walkers x {sweeps} sweeps of L={L} T={T} (+ one weight update), "
+                      f"{dt:.1f} s"}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1502_07214_gb300 import muca
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    s = wl.LARGE
+    L, T, W = s["L"], s["T"], s["n_walkers"]
+    V = L ** 3
+    sweeps = s["sweeps"]
+    meas = s["n_meas"] // s["n_iter"]
+    grid = wl.delta_grid(2.964)  # the first-order transition field at T=0.9 (Sec. III)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = muca.Context([{"L": L, "T": T, "n_walkers": W}], seed=s["seed"] + 7919 * rank)
+    ctx.reserve_timeseries(meas)
+    res, wpb = ctx.get_config(0)
+    launches_per_sweep_call = 1
+    attempts_step = W * V * (sweeps + meas)
+
+    def step_batched():
+        ctx.run_graph(1, sweeps)
+        ctx.reserve_timeseries(meas)  # rewind
+        ctx.sweep_iter(meas, record=True)
+        return muca.reweight_context(ctx, 0, grid, 32, stream=stream)
+
+    for _ in range(args.warmup):
+        step_batched()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_batched()
+    e1.record(stream)
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    elapsed = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(elapsed, op=dist.ReduceOp.MAX)
+    ms = float(elapsed.item())
+    value = attempts_step * args.steps * world / (ms / 1e3)
+
+    # plain form: the same step with one launch per call and host-driven merges;
+    # CUDA events on the launching stream around every sweep launch give the
+    # sweep kernel's average duration for the roofline
+    plain_steps = max(1, min(args.steps, 2))
+    ev = []
+    barrier()
+    p0 = time.perf_counter()
+    for _ in range(plain_steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.sweep_iter(sweeps)
+        b.record(stream)
+        ev.append((a, b, sweeps))
+        ctx.merge_update()
+        ctx.reserve_timeseries(meas)
+        ctx.sweep_iter(meas, record=True)
+        muca.reweight_context(ctx, 0, grid, 32, stream=stream)
+    barrier()
+    plain_s = time.perf_counter() - p0
+    plain_value = attempts_step * plain_steps * world / plain_s
+    kern_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    kern_avg_ms = sum(kern_ms) / len(kern_ms)
+    attempts_launch = W * V * sweeps
+
+    # end to end through the public API with host buffers: each step also reads
+    # back the recorded series and the weights to pinned host memory
+    ts_host = torch.empty((meas, 3, W), dtype=torch.int32, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 2))
+    barrier()
+    q0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.run_graph(1, sweeps)
+        ctx.reserve_timeseries(meas)
+        ctx.sweep_iter(meas, record=True)
+        muca.reweight_context(ctx, 0, grid, 32, stream=stream)
+        rc = muca.lib().muca_get_timeseries(ctx._ctx, 0, ts_host.data_ptr())
+        if rc != 0:
+            raise RuntimeError(muca.last_error(ctx._ctx))
+        ctx.get_lnW(0)
+    barrier()
+    e2e_s = time.perf_counter() - q0
+    e2e_value = attempts_step * e2e_steps * world / e2e_s
+    nE = V + 1
+    h2d = nE * 32 * 4 + 16 * 4  # table upload of the merge
+    d2h = nE * 8 + meas * 3 * W * 4 + nE * 8 + grid.size * 5 * 8  # hist, series, lnW, results
+
+    # reweighting sub-benchmark (FP32 vs FP64), rank 0 only
+    rw = None
+    if rank == 0:
+        rw = reweight_bench(torch, muca)
+
+    if rank == 0:
+        pk, pk_kind = peaks()
+        # the sweep is bound by the per-walker dependency chain and integer issue;
+        # the ALU roofline counts the algorithmic integer operations per attempt
+        ops_per_attempt = ALGO_INT_OPS
+        sm_clock = (clk or {}).get("sm_mhz") or 2070.0
+        int_peak = 152 * 128 * sm_clock * 1e6  # INT32 lanes x clock (ops/s)
+        achieved_ops = ops_per_attempt * attempts_launch / (kern_avg_ms / 1e3)
+        hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+        achieved_hbm = 2.0 * attempts_launch / (kern_avg_ms / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "L=48 T=0.9 4096 walkers: 1000-sweep MUCA iteration "
+                                   "(graph) + 250 recorded sweeps + FP32 reweight to 4096 Delta",
+                       "L": L, "T": T, "walkers": W, "sweeps_per_step": sweeps + meas,
+                       "residency": {1: "global", 2: "smem"}.get(res, str(res)),
+                       "walkers_per_block": wpb, "seed": s["seed"],
+                       "l2": "inputs larger than L2 (lattice 453 MB int8)"},
+            "plain": {"value": plain_value, "unit": UNIT, "steps": plain_steps},
+            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": int_peak / 1e12,
+                         "unit": "Tops/s", "frac": achieved_ops / int_peak, "traffic": None,
+                         "kernel": "sweep_global_kernel<false>",
+                         "ops_per_attempt": ops_per_attempt,
+                         "peak_source": f"152 SMs x 128 INT32 lanes x median SM clock "
+                                        f"{sm_clock:.0f} MHz",
+                         "kernel_ms": kern_avg_ms, "attempts_per_launch": attempts_launch,
+                         "hbm": {"achieved_gbs": achieved_hbm, "peak_gbs": hbm_peak,
+                                 "frac": achieved_hbm / hbm_peak,
+                                 "peak_kind": pk_kind, "bytes_per_attempt": 2}},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * (launches_per_sweep_call * 2 + 3),
+            "clocks": clk,
+            "reweight": rw,
+        }
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline_sample()
+        print(json.dumps(line))
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# Algorithmic integer operations of one attempt: a quarter of a Philox4x32-10
+# block (10 rounds x (2 mul-hi + 2 mul-lo + 2 three-way xor + 2 key adds) / 4 = 20),
+# the six-neighbour sum (5), proposal and energy change (6), table index and
+# compare (4), conditional update of the spin and the three tallies (5).
+ALGO_INT_OPS = 40
+
+
+def reweight_bench(torch, muca):
+    s = wl.REWEIGHT
+    ej, ed, m, lnW, dt = wl.synthetic_series()
+    beta = 1.0 / s["T"]
+    V = s["L"] ** 3
+    grid = wl.delta_grid(dt)
+    dj = torch.from_numpy(ej.ravel()).cuda()
+    dd = torch.from_numpy(ed.ravel()).cuda()
+    dm = torch.from_numpy(m.ravel()).cuda()
+    out = {}
+    res = {}
+    for p in (32, 64):
+        r = muca.reweight(dj, dd, dm, lnW, 0, beta, V, grid, p)  # warm-up
+        reps = 5
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = muca.reweight(dj, dd, dm, lnW, 0, beta, V, grid, p)
+        dt_s = (time.perf_counter() - t0) / reps
+        res[p] = r
+        out[f"fp{p}_pts_per_s"] = len(grid) / dt_s
+        out[f"fp{p}_ms"] = dt_s * 1e3
+    scale = np.maximum(np.abs(res[64]), 1e-3 * np.abs(res[64]).max(axis=0, keepdims=True))
+    err = (np.abs(res[32] - res[64]) / np.where(scale == 0, 1, scale)).max(axis=0)
+    out["fp32_vs_fp64_max_rel_err"] = dict(zip(["E_J", "E_Delta", "C", "chi", "U4"],
+                                               [float(x) for x in err]))
+    out["samples"] = int(ed.size)
+    out["grid_points"] = int(len(grid))
+    out["pairs_per_s_fp32"] = out["fp32_pts_per_s"] * ed.size
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

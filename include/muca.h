@@ -1,0 +1,220 @@
+/*
+ * muca.h -- C ABI of the GB300 library for the parallel multicanonical (MUCA)
+ * simulation of the three-dimensional Blume-Capel model.
+ *
+ * The method (Zierenberg, Fytas, Janke, "Parallel multicanonical study of the
+ * three-dimensional Blume-Capel model"):
+ *   Eq. 1   H = -J sum_<ij> s_i s_j + Delta sum_i s_i^2 = E_J + Delta E_Delta,
+ *           s_i in {-1, 0, +1}, J = 1, L^3 simple-cubic lattice, periodic.
+ *   Sec. II the weight exp(-beta Delta E_Delta) is replaced by W(E_Delta), adapted
+ *           iteratively towards a flat E_Delta histogram; p walkers share W and
+ *           their histograms are merged after every iteration.
+ *   Eq. 3   time-series reweighting to any Delta at fixed beta.
+ *   Eq. 6   C(Delta) = -beta (<E_J E_Delta> - <E_J><E_Delta>).
+ *
+ * Conventions of every entry point:
+ *   - returns MUCA_OK (0) or a negative MUCA_ERR_* code; no exception or
+ *     abort crosses the ABI; muca_last_error() gives a one-line reason;
+ *   - a muca_ctx owns all device memory it allocates (freed by muca_destroy);
+ *   - pointers passed in are borrowed for the duration of the call only;
+ *     "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *     global-memory addresses on the context's device (e.g. a torch tensor's
+ *     data_ptr());
+ *   - work is issued on the context's CUDA stream (the one passed to
+ *     muca_init); calls that return host data synchronise that stream;
+ *   - walker ids are global over the groups of a context, in group order.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ * (global walker id, seed) and counter (site >> 2, sweep low, sweep high,
+ * stream); stream 0 drives the updates and stream 1 the initial spins.  Each
+ * 32-bit word serves one site (site & 3): bit 31 chooses the proposal (the
+ * smaller or larger of the two other spin values), bits 0..30 are the uniform
+ * draw u.  A proposal is accepted iff u < thr[E_Delta][d][dE_J] with
+ * thr = 2^31 when x >= 0, else floor(exp(x) 2^31), x = -beta dE_J +
+ * lnW[E_Delta + d] - lnW[E_Delta], d = s'^2 - s^2, and thr = 0 when E_Delta + d
+ * leaves the window.  The table is built on the host in FP64.
+ */
+#ifndef MUCA_H
+#define MUCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MUCA_OK 0
+#define MUCA_ERR_INVALID_ARG (-1)
+#define MUCA_ERR_CUDA (-2)
+#define MUCA_ERR_OOM (-3)
+#define MUCA_ERR_TIMEOUT (-4)
+#define MUCA_ERR_TALLY_MISMATCH (-5)
+#define MUCA_ERR_NOT_SUPPORTED (-6)
+#define MUCA_ERR_WINDOW (-7)
+#define MUCA_ERR_IO (-8)
+
+/* Largest supported linear size (V = L^3 sites per walker). */
+#define MUCA_MAX_L 64
+
+/* Number of logical threshold entries per (E_Delta, d): dE_J = -12 .. 12. */
+#define MUCA_NK 25
+
+typedef struct muca_ctx muca_ctx;
+
+/* One (L, T) group of walkers sharing one weight function W(E_Delta)
+ * (Sec. II: walkers at the same temperature share W and merge histograms). */
+typedef struct {
+    int32_t L;         /* linear size, 2 <= L <= MUCA_MAX_L */
+    double T;          /* temperature > 0, beta = 1 / T */
+    int32_t n_walkers; /* >= 1 */
+    int32_t e_min;     /* E_Delta window [e_min, e_max]; 0 <= e_min <= e_max <= L^3 */
+    int32_t e_max;     /* a negative e_max means L^3 (the full range, Sec. II) */
+} muca_group;
+
+/* Lattice residency of the sweep kernel. */
+#define MUCA_RES_AUTO 0   /* chosen by the autotuner (measured) */
+#define MUCA_RES_GLOBAL 1 /* spins stay in HBM/L2, site-major walker-minor */
+#define MUCA_RES_SMEM 2   /* each block keeps its walkers' lattices in shared memory */
+
+/* debug_flags bits */
+#define MUCA_DEBUG_TALLY_CHECK 1 /* recompute E_J, E_Delta, M after every sweep call */
+
+typedef struct {
+    uint32_t seed;             /* Philox key word 1 */
+    int32_t debug_flags;       /* MUCA_DEBUG_* bits */
+    int32_t residency;         /* MUCA_RES_* */
+    int32_t walkers_per_block; /* 0 = automatic; else a multiple of 32 in [32, 1024]
+                                  for global residency */
+} muca_options;
+
+/* ---------------------------------------------------------------- lifetime */
+
+/* Create a context: allocates the spins (int8, site-major walker-minor), the
+ * running tallies (E_J, E_Delta, M as int32), the histograms and the threshold
+ * tables of every group on the current CUDA device, draws the initial spins
+ * i.i.d. uniform on {-1, 0, +1} (Philox stream 1), computes the tallies, sets
+ * lnW = 0 and uploads the first table.  stream: a cudaStream_t (NULL = the
+ * legacy default stream).  If an initial E_Delta lies outside a restricted
+ * window, the group must receive a state through muca_set_state before the
+ * first sweep (muca_sweep_iter and muca_run_graph fail with MUCA_ERR_WINDOW
+ * until then).  On error *out is NULL. */
+int muca_init(const muca_group *groups, int n_groups, const muca_options *opt,
+              void *stream, muca_ctx **out);
+
+/* Release every resource of ctx (NULL is accepted). */
+void muca_destroy(muca_ctx *ctx);
+
+/* Reason for the most recent failure on ctx; with ctx == NULL, the most recent
+ * failure of any call in this thread (e.g. of muca_init).  Never NULL. */
+const char *muca_last_error(const muca_ctx *ctx);
+
+/* Wait for all work issued on the context's stream. */
+int muca_sync(muca_ctx *ctx);
+
+/* ----------------------------------------------------------- the hot path */
+
+/* n_sweeps typewriter Metropolis sweeps of every walker of every group (Sec. II
+ * acceptance with the current table).  After each sweep the walker's E_Delta
+ * is added to its group's histogram (one entry per walker per sweep).  With
+ * record != 0 each sweep also appends (E_J, E_Delta, M) of every walker to the
+ * time series, which must have room (muca_reserve_timeseries).  Asynchronous
+ * unless MUCA_DEBUG_TALLY_CHECK is set. */
+int muca_sweep_iter(muca_ctx *ctx, int n_sweeps, int record);
+
+/* The merge and weight update of one MUCA iteration for every group (Sec. II):
+ * the merged histogram H is read back, lnW[E] -= ln H[E] wherever H[E] > 0 (in
+ * FP64 on the host), the threshold table is rebuilt in FP64 and uploaded, and
+ * H is cleared.  Synchronises the stream. */
+int muca_merge_update(muca_ctx *ctx);
+
+/* The batched form: n_iters x (sweeps_per_iter sweeps of all groups in one
+ * launch, then merge + update of every group) captured once as a CUDA graph
+ * (the FP64 update runs in a host node) and replayed.  Results are bit-identical
+ * to calling muca_sweep_iter + muca_merge_update n_iters times.
+ * Synchronises the stream. */
+int muca_run_graph(muca_ctx *ctx, int n_iters, int sweeps_per_iter);
+
+/* Time-series reweighting (Eq. 3) of n = n_rows x row_len samples to every
+ * Delta_k of delta_grid, with C from Eq. 6.
+ *   e_j, e_d, m   device int32; sample (r, c) is at [r * row_stride + c]
+ *                 (so the context's [sample][field][walker] series is
+ *                 e_j = base, e_d = base + W, m = base + 2 W, row_len = W,
+ *                 row_stride = 3 W; plain arrays have n_rows = 1)
+ *   lnW           host FP64 [n_e], indexed by E_Delta - e_min; every sample
+ *                 must satisfy e_min <= E_Delta < e_min + n_e
+ *   beta, V       inverse temperature and number of sites
+ *   delta_grid    host FP64 [n_grid]
+ *   precision     64: FP64 arithmetic; 32: FP32 arithmetic (max-shifted
+ *                 exponents carried as float pairs, Kahan-compensated sums)
+ *   out           host FP64 [n_grid][5]: <E_J>, <E_Delta>, C,
+ *                 chi = beta V (<m^2> - <|m|>^2), U4 = 1 - <m^4> / (3 <m^2>^2),
+ *                 m = M / V
+ *   stream        cudaStream_t for the work (NULL = legacy default stream)
+ * Allocates its scratch with cudaMallocAsync on the stream; synchronises the
+ * stream before returning. */
+int muca_reweight(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n_rows,
+                  int32_t row_len, int64_t row_stride, const double *lnW, int32_t e_min,
+                  int32_t n_e, double beta, int32_t V, const double *delta_grid, int32_t n_grid,
+                  int32_t precision, double *out, void *stream);
+
+/* ------------------------------------------------------------ time series */
+
+/* Reserve room for n_samples recorded sweeps per walker (device memory,
+ * [sample][3][n_walkers] int32 per group) and reset the recorded length to 0.
+ * Asking again for the current capacity only rewinds (no allocation). */
+int muca_reserve_timeseries(muca_ctx *ctx, int64_t n_samples);
+
+/* Recorded length (samples per walker) and the device address of group g's
+ * series, laid out [sample][field][walker] with field 0 = E_J, 1 = E_Delta,
+ * 2 = M and a walker stride of n_walkers of the group. */
+int muca_timeseries_device(muca_ctx *ctx, int group, const int32_t **dev, int64_t *n_samples);
+
+/* Copy group g's series to host int32 [n_samples][3][n_walkers]. */
+int muca_get_timeseries(muca_ctx *ctx, int group, int32_t *out);
+
+/* ----------------------------------------------------- inspection / parity */
+
+/* Number of sweeps done so far by group g (the next sweep's Philox index). */
+int muca_get_sweep_count(muca_ctx *ctx, int group, uint64_t *out);
+
+/* lnW of group g, host FP64 [n_e]. set replaces it and rebuilds the table. */
+int muca_get_lnW(muca_ctx *ctx, int group, double *out);
+int muca_set_lnW(muca_ctx *ctx, int group, const double *in);
+
+/* Threshold table of group g in the logical layout, host uint32
+ * [n_e][3][MUCA_NK], index [E_Delta - e_min][d + 1][dE_J + 12].  set uploads a
+ * given table (its d = 0 entries must not depend on E_Delta). */
+int muca_get_table(muca_ctx *ctx, int group, uint32_t *out);
+int muca_set_table(muca_ctx *ctx, int group, const uint32_t *in);
+
+/* Merged histogram of group g since the last merge, host uint64 [n_e]. */
+int muca_get_hist(muca_ctx *ctx, int group, uint64_t *out);
+int muca_set_hist(muca_ctx *ctx, int group, const uint64_t *in);
+
+/* Walker state of group g: spins host int8 [n_walkers][L^3] (site i =
+ * x + L (y + L z)), tallies host int32 [n_walkers][3] = (E_J, E_Delta, M).
+ * Either output may be NULL.  set_state uploads spins and recomputes the
+ * tallies on the device; fails with MUCA_ERR_WINDOW if an E_Delta leaves the
+ * window, MUCA_ERR_INVALID_ARG if a spin is not in {-1, 0, +1}. */
+int muca_get_state(muca_ctx *ctx, int group, int8_t *spins, int32_t *tallies);
+int muca_set_state(muca_ctx *ctx, int group, const int8_t *spins);
+
+/* Recompute E_J, E_Delta, M of every walker on the device and compare with the
+ * running tallies: MUCA_OK or MUCA_ERR_TALLY_MISMATCH. */
+int muca_check_tallies(muca_ctx *ctx);
+
+/* Kernel configuration chosen for group g: residency (MUCA_RES_GLOBAL or
+ * MUCA_RES_SMEM) and walkers per block. */
+int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walkers_per_block);
+
+/* Checkpoint / restore: spins, tallies, lnW, histograms, sweep counters and
+ * the seed, to / from a file.  Philox is counter-based, so a restored run
+ * continues bit-identically.  restore requires a context with the same groups. */
+int muca_checkpoint(muca_ctx *ctx, const char *path);
+int muca_restore(muca_ctx *ctx, const char *path);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUCA_H */

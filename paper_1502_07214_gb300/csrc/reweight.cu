@@ -1,0 +1,543 @@
+// reweight.cu -- time-series reweighting of a multicanonical run to a grid of
+// crystal fields Delta_k (Eq. 3), with C(Delta) from Eq. 6, chi and U4.
+//
+// The multicanonical weight of a sample depends on the sample only through its
+// E_Delta (Eq. 3: exp(-beta Delta E_Delta) / W(E_Delta)).  The GPU path therefore
+// works in two stages:
+//   A. one streaming pass over the samples accumulates, per E_Delta bin, exact
+//      integer sums: count, sum E_J, sum |M|, sum M^2 and sum M^4 (128-bit);
+//   B. for every Delta_k, a pass over the occupied bins: shift the exponents by
+//      their maximum, exponentiate, and form the weighted sums; C and chi are
+//      taken as centred second passes, so no difference of large moments is
+//      ever formed.
+// Stage B runs in FP64, or in FP32 where the exponent -beta Delta_k E - lnW(E)
+// is carried as a float pair (hi + lo, error-free products and sums) so that
+// its O(10^5) magnitude does not eat the 24-bit mantissa, and all sums are
+// Kahan-compensated.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/muca.h"
+#include "muca_internal.h"
+
+namespace {
+
+int rw_fail(int code, const std::string &msg)
+{
+    muca::set_last_error(msg.c_str());
+    return code;
+}
+
+// Integer bin sums of stage A (device scratch).
+struct Bins {
+    unsigned long long *cnt;   // samples per bin
+    unsigned long long *sej;   // sum E_J (two's complement)
+    unsigned long long *sam;   // sum |M|
+    unsigned long long *sm2;   // sum M^2
+    unsigned long long *sm4lo; // sum M^4, low 64 bits
+    unsigned long long *sm4hi; // sum M^4, high 64 bits
+};
+
+// Per-bin statistics consumed by stage B.
+template <typename F>
+struct BinStats {
+    F *n;    // count
+    F *mej;  // mean E_J in the bin
+    F *cm;   // mean |m| in the bin, m = M / V
+    F *vb;   // sum over the bin of (|m| - cm)^2
+    F *q2;   // sum m^2
+    F *q4;   // sum m^4
+    F *lw;   // lnW (FP64) or its high float (FP32)
+    F *lwlo; // FP32 only: lnW - hi
+};
+
+__global__ void bin_kernel(const int32_t *__restrict__ ej, const int32_t *__restrict__ ed,
+                           const int32_t *__restrict__ m, int64_t n_rows, int row_len,
+                           int64_t row_stride, int e_min, int nE, Bins b, int *err)
+{
+    for (int64_t r = blockIdx.y; r < n_rows; r += gridDim.y) {
+        const int64_t base = r * row_stride;
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < row_len;
+             c += gridDim.x * blockDim.x) {
+            const int64_t o = base + c;
+            const int e = __ldg(ed + o) - e_min;
+            if (e < 0 || e >= nE) {
+                atomicOr(err, 1);
+                continue;
+            }
+            const long long j = __ldg(ej + o);
+            const long long mm = __ldg(m + o);
+            const unsigned long long am = (unsigned long long)(mm < 0 ? -mm : mm);
+            const unsigned long long m2 = am * am;
+            const unsigned long long m4lo = m2 * m2, m4hi = __umul64hi(m2, m2);
+            atomicAdd(b.cnt + e, 1ull);
+            atomicAdd(b.sej + e, (unsigned long long)j);
+            atomicAdd(b.sam + e, am);
+            atomicAdd(b.sm2 + e, m2);
+            const unsigned long long old = atomicAdd(b.sm4lo + e, m4lo);
+            const unsigned long long carry = (old + m4lo < old) ? 1ull : 0ull;
+            if (m4hi + carry) atomicAdd(b.sm4hi + e, m4hi + carry);
+        }
+    }
+}
+
+__device__ __forceinline__ double u128_to_double(unsigned long long hi, unsigned long long lo)
+{
+    return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+__device__ __forceinline__ float u128_to_float(unsigned long long hi, unsigned long long lo)
+{
+    return (float)hi * 18446744073709551616.0f + (float)lo;
+}
+
+// Stage A2: integer sums -> per-bin statistics.  vb uses the exact integer
+// n sum M^2 - (sum |M|)^2 (128-bit) before any rounding.
+__global__ void stats_kernel_f64(Bins b, int nE, int V, const double *__restrict__ lnW,
+                                 BinStats<double> s)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    const unsigned long long n = b.cnt[e];
+    s.lw[e] = lnW[e];
+    if (n == 0) {
+        s.n[e] = 0;
+        return;
+    }
+    const double dn = (double)n, dV = (double)V;
+    const long long sej = (long long)b.sej[e];
+    const unsigned long long sam = b.sam[e], sm2 = b.sm2[e];
+    const unsigned __int128 a = (unsigned __int128)n * sm2;
+    const unsigned __int128 c = (unsigned __int128)sam * sam;
+    const unsigned __int128 v = a - c;
+    s.n[e] = dn;
+    s.mej[e] = (double)sej / dn;
+    s.cm[e] = (double)sam / dn / dV;
+    s.vb[e] = u128_to_double((unsigned long long)(v >> 64), (unsigned long long)v) / dn / dV / dV;
+    s.q2[e] = (double)sm2 / dV / dV;
+    s.q4[e] = u128_to_double(b.sm4hi[e], b.sm4lo[e]) / dV / dV / dV / dV;
+}
+
+__global__ void stats_kernel_f32(Bins b, int nE, int V, const float *__restrict__ lw_hi,
+                                 const float *__restrict__ lw_lo, BinStats<float> s)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    const unsigned long long n = b.cnt[e];
+    s.lw[e] = lw_hi[e];
+    s.lwlo[e] = lw_lo[e];
+    if (n == 0) {
+        s.n[e] = 0.f;
+        return;
+    }
+    const float fn = (float)n, fV = (float)V;
+    const long long sej = (long long)b.sej[e];
+    const unsigned long long sam = b.sam[e], sm2 = b.sm2[e];
+    const unsigned __int128 a = (unsigned __int128)n * sm2;
+    const unsigned __int128 c = (unsigned __int128)sam * sam;
+    const unsigned __int128 v = a - c;
+    s.n[e] = fn;
+    s.mej[e] = (float)sej / fn;
+    s.cm[e] = (float)sam / fn / fV;
+    s.vb[e] = u128_to_float((unsigned long long)(v >> 64), (unsigned long long)v) / fn / fV / fV;
+    s.q2[e] = (float)sm2 / fV / fV;
+    s.q4[e] = u128_to_float(b.sm4hi[e], b.sm4lo[e]) / fV / fV / fV / fV;
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename F>
+struct KSum {  // Kahan-compensated accumulator
+    F s, c;
+    __device__ void init() { s = c = F(0); }
+    __device__ void add(F x)
+    {
+        const F y = x - c;
+        const F t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+template <typename F>
+__device__ __forceinline__ F block_max(F v, F *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    F r = sh[0];
+    for (int i = 1; i < nw; ++i) r = fmax(r, sh[i]);
+    return r;
+}
+
+// Sum of K compensated accumulators over the block; every thread gets the sums.
+template <typename F, int K>
+__device__ __forceinline__ void block_sum(KSum<F> (&a)[K], F (&out)[K], F *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        F s = a[k].s, c = -a[k].c;
+        for (int o = 16; o > 0; o >>= 1) {
+            const F s2 = __shfl_xor_sync(0xFFFFFFFFu, s, o);
+            const F c2 = __shfl_xor_sync(0xFFFFFFFFu, c, o);
+            // two-sum of s and s2 keeps the rounding error in c
+            const F t = s + s2;
+            const F bp = t - s;
+            const F err = (s - (t - bp)) + (s2 - bp);
+            s = t;
+            c = c + c2 + err;
+        }
+        __syncthreads();
+        if (lane == 0) {
+            sh[2 * wid] = s;
+            sh[2 * wid + 1] = c;
+        }
+        __syncthreads();
+        KSum<F> tot;
+        tot.init();
+        F cc = F(0);
+        for (int i = 0; i < nw; ++i) {
+            tot.add(sh[2 * i]);
+            cc += sh[2 * i + 1];
+        }
+        out[k] = tot.s + (cc - tot.c);
+    }
+}
+
+// ------------------------------------------------------------ FP64 stage B
+// Exponent exactly as written in Eq. 3: a = -(c E) - lnW(E), c = beta Delta_k.
+__device__ __forceinline__ double expo64(double c, int E, double lw)
+{
+    return __dsub_rn(-__dmul_rn(c, (double)E), lw);
+}
+
+__global__ void __launch_bounds__(256)
+grid_kernel_f64(BinStats<double> s, int nE, int e_min, double beta, int V,
+                const double *__restrict__ cgrid, double *__restrict__ out)
+{
+    __shared__ double sh[64];
+    const int k = blockIdx.x;
+    const double c = cgrid[k];
+    double amax = -INFINITY;
+    for (int e = threadIdx.x; e < nE; e += blockDim.x)
+        if (s.n[e] > 0) amax = fmax(amax, expo64(c, e_min + e, s.lw[e]));
+    amax = block_max(amax, sh);
+    KSum<double> acc[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[i].init();
+    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+        const double n = s.n[e];
+        if (n <= 0) continue;
+        const double d = expo64(c, e_min + e, s.lw[e]) - amax;
+        if (d < -800.0) continue;
+        const double w = exp(d);
+        const double wn = w * n;
+        acc[0].add(wn);
+        acc[1].add(wn * (double)(e_min + e));
+        acc[2].add(wn * s.mej[e]);
+        acc[3].add(wn * s.cm[e]);
+        acc[4].add(w * s.q2[e]);
+        acc[5].add(w * s.q4[e]);
+    }
+    double S[6];
+    block_sum<double, 6>(acc, S, sh);
+    const double Z = S[0], mE = S[1] / Z, mJ = S[2] / Z, mu = S[3] / Z;
+    KSum<double> acc2[2];
+    acc2[0].init();
+    acc2[1].init();
+    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+        const double n = s.n[e];
+        if (n <= 0) continue;
+        const double d = expo64(c, e_min + e, s.lw[e]) - amax;
+        if (d < -800.0) continue;
+        const double w = exp(d);
+        const double wn = w * n;
+        acc2[0].add(wn * ((s.mej[e] - mJ) * ((double)(e_min + e) - mE)));
+        const double dm = s.cm[e] - mu;
+        acc2[1].add(w * s.vb[e] + wn * (dm * dm));
+    }
+    double S2[2];
+    block_sum<double, 2>(acc2, S2, sh);
+    if (threadIdx.x == 0) {
+        double *o = out + 5 * (int64_t)k;
+        o[0] = mJ;
+        o[1] = mE;
+        o[2] = -beta * (S2[0] / Z);
+        o[3] = beta * (double)V * (S2[1] / Z);
+        const double m2 = S[4] / Z, m4 = S[5] / Z;
+        o[4] = 1.0 - m4 / (3.0 * m2 * m2);
+    }
+}
+
+// ------------------------------------------------------------ FP32 stage B
+// a = -(c_hi + c_lo) E - (lw_hi + lw_lo) as an unevaluated float pair.
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 expo32(float chi, float clo, int E, float lwh, float lwl)
+{
+    const float fe = (float)E;                  // exact: E < 2^24
+    // the _rn intrinsics keep the compiler from fusing the error-free steps
+    const float p = __fmul_rn(chi, fe);         // two-product: p + pe = chi E exactly
+    const float pe = fmaf(chi, fe, -p);
+    const float s = __fsub_rn(-p, lwh);         // two-sum of -p and -lwh
+    const float bp = __fadd_rn(s, p);
+    const float se = __fadd_rn(__fsub_rn(-p, __fsub_rn(s, bp)), __fsub_rn(-lwh, bp));
+    const float lo = se - pe - fmaf(clo, fe, lwl);
+    return {s, lo};
+}
+
+__global__ void __launch_bounds__(256)
+grid_kernel_f32(BinStats<float> s, int nE, int e_min, float beta, int V,
+                const float *__restrict__ c_hi, const float *__restrict__ c_lo,
+                double *__restrict__ out)
+{
+    __shared__ float sh[64];
+    const int k = blockIdx.x;
+    const float ch = c_hi[k], cl = c_lo[k];
+    float amax = -INFINITY;
+    for (int e = threadIdx.x; e < nE; e += blockDim.x)
+        if (s.n[e] > 0.f) {
+            const F2 a = expo32(ch, cl, e_min + e, s.lw[e], s.lwlo[e]);
+            amax = fmaxf(amax, a.hi);
+        }
+    amax = block_max(amax, sh);
+    KSum<float> acc[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc[i].init();
+    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+        const float n = s.n[e];
+        if (n <= 0.f) continue;
+        const F2 a = expo32(ch, cl, e_min + e, s.lw[e], s.lwlo[e]);
+        const float d = (a.hi - amax) + a.lo;
+        if (d < -104.f) continue;
+        const float w = expf(d);
+        const float wn = w * n;
+        acc[0].add(wn);
+        acc[1].add(wn * (float)(e_min + e));
+        acc[2].add(wn * s.mej[e]);
+        acc[3].add(wn * s.cm[e]);
+        acc[4].add(w * s.q2[e]);
+        acc[5].add(w * s.q4[e]);
+    }
+    float S[6];
+    block_sum<float, 6>(acc, S, sh);
+    const float Z = S[0], mE = S[1] / Z, mJ = S[2] / Z, mu = S[3] / Z;
+    KSum<float> acc2[2];
+    acc2[0].init();
+    acc2[1].init();
+    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+        const float n = s.n[e];
+        if (n <= 0.f) continue;
+        const F2 a = expo32(ch, cl, e_min + e, s.lw[e], s.lwlo[e]);
+        const float d = (a.hi - amax) + a.lo;
+        if (d < -104.f) continue;
+        const float w = expf(d);
+        const float wn = w * n;
+        acc2[0].add(wn * ((s.mej[e] - mJ) * ((float)(e_min + e) - mE)));
+        const float dm = s.cm[e] - mu;
+        acc2[1].add(w * s.vb[e] + wn * (dm * dm));
+    }
+    float S2[2];
+    block_sum<float, 2>(acc2, S2, sh);
+    if (threadIdx.x == 0) {
+        double *o = out + 5 * (int64_t)k;
+        o[0] = mJ;
+        o[1] = mE;
+        o[2] = -beta * (S2[0] / Z);
+        o[3] = beta * (float)V * (S2[1] / Z);
+        const float m2 = S[4] / Z, m4 = S[5] / Z;
+        o[4] = 1.f - m4 / (3.f * m2 * m2);
+    }
+}
+
+// Scratch layout of one call (bytes), all 256-byte aligned.
+struct Scratch {
+    size_t bins, stats, grid, out, err, total;
+};
+
+Scratch scratch_layout(int nE, int n_grid, int precision)
+{
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    Scratch s{};
+    s.bins = al((size_t)6 * nE * sizeof(unsigned long long));
+    s.stats = al((size_t)8 * nE * (precision == 32 ? sizeof(float) : sizeof(double)) +
+                 (precision == 32 ? 2 * (size_t)nE * sizeof(float) : (size_t)nE * sizeof(double)));
+    s.grid = al((size_t)2 * n_grid * sizeof(double));
+    s.out = al((size_t)5 * n_grid * sizeof(double));
+    s.err = al(sizeof(int));
+    s.total = s.bins + s.stats + s.grid + s.out + s.err;
+    return s;
+}
+
+}  // namespace
+
+namespace muca {
+
+// The whole reweighting on a caller-provided scratch region of
+// scratch_layout(...).total bytes (device memory).
+int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n_rows,
+                        int32_t row_len, int64_t row_stride, const double *lnW, int32_t e_min,
+                        int32_t n_e, double beta, int32_t V, const double *delta_grid,
+                        int32_t n_grid, int32_t precision, double *out, cudaStream_t st,
+                        char *scratch)
+{
+    const Scratch L = scratch_layout(n_e, n_grid, precision);
+    char *p = scratch;
+    Bins b;
+    b.cnt = (unsigned long long *)p;
+    b.sej = b.cnt + n_e;
+    b.sam = b.sej + n_e;
+    b.sm2 = b.sam + n_e;
+    b.sm4lo = b.sm2 + n_e;
+    b.sm4hi = b.sm4lo + n_e;
+    char *ps = p + L.bins;
+    char *pg = ps + L.stats;
+    double *d_out = (double *)(pg + L.grid);
+    int *d_err = (int *)((char *)d_out + L.out);
+    cudaError_t ce;
+#define RCK(call)                                                                   \
+    do {                                                                            \
+        ce = (call);                                                                \
+        if (ce != cudaSuccess)                                                      \
+            return rw_fail(MUCA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(ce)); \
+    } while (0)
+    RCK(cudaMemsetAsync(p, 0, L.bins, st));
+    RCK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    if (n_rows > 0 && row_len > 0) {
+        dim3 grid((unsigned)std::min<int64_t>((row_len + 255) / 256, 1024),
+                  (unsigned)std::min<int64_t>(n_rows, 4096));
+        bin_kernel<<<grid, 256, 0, st>>>(e_j, e_d, m, n_rows, row_len, row_stride, e_min, n_e, b,
+                                         d_err);
+        RCK(cudaGetLastError());
+    }
+    const int sb = (n_e + 255) / 256;
+    if (precision == 64) {
+        BinStats<double> s;
+        double *q = (double *)ps;
+        s.n = q;
+        s.mej = q + n_e;
+        s.cm = q + 2 * (size_t)n_e;
+        s.vb = q + 3 * (size_t)n_e;
+        s.q2 = q + 4 * (size_t)n_e;
+        s.q4 = q + 5 * (size_t)n_e;
+        s.lw = q + 6 * (size_t)n_e;
+        s.lwlo = nullptr;
+        double *d_lnW = q + 7 * (size_t)n_e;
+        double *d_c = (double *)pg;
+        std::vector<double> c(n_grid);
+        for (int k = 0; k < n_grid; ++k) c[k] = beta * delta_grid[k];
+        RCK(cudaMemcpyAsync(d_lnW, lnW, (size_t)n_e * sizeof(double), cudaMemcpyHostToDevice, st));
+        RCK(cudaMemcpyAsync(d_c, c.data(), (size_t)n_grid * sizeof(double),
+                            cudaMemcpyHostToDevice, st));
+        stats_kernel_f64<<<sb, 256, 0, st>>>(b, n_e, V, d_lnW, s);
+        RCK(cudaGetLastError());
+        if (n_grid > 0) grid_kernel_f64<<<n_grid, 256, 0, st>>>(s, n_e, e_min, beta, V, d_c, d_out);
+        RCK(cudaGetLastError());
+        // keep the host vectors alive until the copies are done
+        RCK(cudaStreamSynchronize(st));
+    } else {
+        BinStats<float> s;
+        float *q = (float *)ps;
+        s.n = q;
+        s.mej = q + n_e;
+        s.cm = q + 2 * (size_t)n_e;
+        s.vb = q + 3 * (size_t)n_e;
+        s.q2 = q + 4 * (size_t)n_e;
+        s.q4 = q + 5 * (size_t)n_e;
+        s.lw = q + 6 * (size_t)n_e;
+        s.lwlo = q + 7 * (size_t)n_e;
+        float *d_lh = q + 8 * (size_t)n_e, *d_ll = q + 9 * (size_t)n_e;
+        float *d_ch = (float *)pg, *d_cl = d_ch + n_grid;
+        // inputs handed to the FP32 path as float pairs (hi + lo)
+        std::vector<float> lh(n_e), ll(n_e), ch(n_grid), cl(n_grid);
+        for (int e = 0; e < n_e; ++e) {
+            lh[e] = (float)lnW[e];
+            ll[e] = (float)(lnW[e] - (double)lh[e]);
+        }
+        for (int k = 0; k < n_grid; ++k) {
+            const double c = beta * delta_grid[k];
+            ch[k] = (float)c;
+            cl[k] = (float)(c - (double)ch[k]);
+        }
+        RCK(cudaMemcpyAsync(d_lh, lh.data(), n_e * sizeof(float), cudaMemcpyHostToDevice, st));
+        RCK(cudaMemcpyAsync(d_ll, ll.data(), n_e * sizeof(float), cudaMemcpyHostToDevice, st));
+        RCK(cudaMemcpyAsync(d_ch, ch.data(), n_grid * sizeof(float), cudaMemcpyHostToDevice, st));
+        RCK(cudaMemcpyAsync(d_cl, cl.data(), n_grid * sizeof(float), cudaMemcpyHostToDevice, st));
+        stats_kernel_f32<<<sb, 256, 0, st>>>(b, n_e, V, d_lh, d_ll, s);
+        RCK(cudaGetLastError());
+        if (n_grid > 0)
+            grid_kernel_f32<<<n_grid, 256, 0, st>>>(s, n_e, e_min, (float)beta, V, d_ch, d_cl,
+                                                    d_out);
+        RCK(cudaGetLastError());
+        RCK(cudaStreamSynchronize(st));
+    }
+    int h_err = 0;
+    RCK(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RCK(cudaMemcpyAsync(out, d_out, (size_t)5 * n_grid * sizeof(double), cudaMemcpyDeviceToHost,
+                        st));
+    RCK(cudaStreamSynchronize(st));
+#undef RCK
+    if (h_err) return rw_fail(MUCA_ERR_WINDOW, "a sample's E_Delta lies outside [e_min, e_min + n_e)");
+    return MUCA_OK;
+}
+
+size_t reweight_scratch_bytes(int32_t n_e, int32_t n_grid, int32_t precision)
+{
+    return scratch_layout(n_e, n_grid, precision).total;
+}
+
+int reweight_check_args(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n_rows,
+                        int32_t row_len, int64_t row_stride, const double *lnW, int32_t n_e,
+                        double beta, int32_t V, const double *delta_grid, int32_t n_grid,
+                        int32_t precision, double *out)
+{
+    if (!e_j || !e_d || !m || !lnW || !out || (n_grid > 0 && !delta_grid))
+        return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: null pointer");
+    if (n_rows < 0 || row_len < 0 || (n_rows > 1 && row_stride < row_len) || n_e < 1 || V < 1 ||
+        n_grid < 0)
+        return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: bad sizes");
+    if (n_rows * (int64_t)row_len < 1)
+        return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: no samples");
+    if (precision != 32 && precision != 64)
+        return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: precision must be 32 or 64");
+    if (!(beta > 0.0) || !std::isfinite(beta))
+        return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: beta must be > 0");
+    for (int e = 0; e < n_e; ++e)
+        if (!std::isfinite(lnW[e])) return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: lnW not finite");
+    for (int k = 0; k < n_grid; ++k)
+        if (!std::isfinite(delta_grid[k]))
+            return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: Delta grid not finite");
+    return MUCA_OK;
+}
+
+}  // namespace muca
+
+extern "C" int muca_reweight(const int32_t *e_j, const int32_t *e_d, const int32_t *m,
+                             int64_t n_rows, int32_t row_len, int64_t row_stride,
+                             const double *lnW, int32_t e_min, int32_t n_e, double beta, int32_t V,
+                             const double *delta_grid, int32_t n_grid, int32_t precision,
+                             double *out, void *stream)
+{
+    int rc = muca::reweight_check_args(e_j, e_d, m, n_rows, row_len, row_stride, lnW, n_e, beta,
+                                       V, delta_grid, n_grid, precision, out);
+    if (rc != MUCA_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = muca::reweight_scratch_bytes(n_e, n_grid, precision);
+    void *scratch = nullptr;
+    cudaError_t ce = cudaMallocAsync(&scratch, bytes, st);
+    if (ce != cudaSuccess)
+        return rw_fail(ce == cudaErrorMemoryAllocation ? MUCA_ERR_OOM : MUCA_ERR_CUDA,
+                       std::string("cudaMallocAsync: ") + cudaGetErrorString(ce));
+    rc = muca::reweight_on_scratch(e_j, e_d, m, n_rows, row_len, row_stride, lnW, e_min, n_e, beta,
+                                   V, delta_grid, n_grid, precision, out, st, (char *)scratch);
+    cudaFreeAsync(scratch, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}

@@ -1,0 +1,1030 @@
+// runtime.cu -- host runtime behind the muca_* C ABI: context and device
+// buffers, the FP64 weight recursion and acceptance-table build (Sec. II),
+// kernel configuration (autotuned), CUDA-graph capture of the iteration loop,
+// and checkpoint / restore.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/muca.h"
+#include "muca_internal.h"
+
+using namespace muca;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+struct Group {
+    muca_group spec{};
+    int L = 0, V = 0, W = 0, Wpad = 0, e_min = 0, e_max = 0, nE = 0;
+    double T = 0, beta = 0;
+    uint32_t walker0 = 0;
+    // device
+    int8_t *spins = nullptr;
+    int32_t *tal = nullptr;
+    unsigned long long *hist = nullptr;
+    uint32_t *thrE = nullptr;
+    uint32_t *thr0 = nullptr;
+    int32_t *ts = nullptr;
+    // host
+    std::vector<double> lnW;
+    std::vector<uint32_t> injected;  // logical table given by muca_set_table (empty if none)
+    uint32_t *h_thrE = nullptr;      // pinned packed table [nE][kRow]
+    uint32_t *h_thr0 = nullptr;      // pinned [kThr0]
+    unsigned long long *h_hist = nullptr;  // pinned [nE]
+    // every walker's E_Delta lies in [e_min, e_max] (required before sweeping)
+    bool in_window = false;
+    // kernel configuration
+    int residency = MUCA_RES_GLOBAL;
+    int wpb = 32;
+};
+
+struct GraphKey {
+    int n_iters, sweeps;
+    uint64_t sweep0;
+};
+
+}  // namespace
+
+struct muca_ctx {
+    std::vector<Group> g;
+    uint32_t seed = 0;
+    int debug = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;  // second stream for the shared-memory blocks
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    uint64_t sweep = 0;
+    int64_t ts_cap = 0, ts_len = 0;
+    std::string err = "no error";
+    int *d_err = nullptr;
+    GroupDev *d_groups = nullptr;
+    BlockDesc *d_blocks_g = nullptr, *d_blocks_s = nullptr;
+    int n_blocks_g = 0, n_blocks_s = 0, threads_g = 32, threads_s = 32;
+    size_t smem_bytes = 0;
+};
+
+namespace {
+
+int fail(muca_ctx *ctx, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MUCA_ERR_OOM : MUCA_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Acceptance thresholds (Sec. II weights, built in FP64):
+//   x = -beta dE_J + (lnW[E + d] - lnW[E]);  thr = 2^31 if x >= 0,
+//   else floor(exp(x) 2^31); thr = 0 when E + d leaves the window.
+// The arithmetic is written out exactly as it must round (the library is built
+// with -ffp-contract=off, so no multiply-add is fused).
+// ---------------------------------------------------------------------------
+inline uint32_t thr_of(double x)
+{
+    if (x >= 0.0) return 0x80000000u;
+    if (x < -21.5) return 0u;  // exp(x) 2^31 < 0.99: floor is 0
+    const double t = std::floor(std::exp(x) * 2147483648.0);
+    return t >= 2147483648.0 ? 0x80000000u : (uint32_t)t;
+}
+
+inline uint32_t thr_entry(const Group &g, int e, int d, int dej)
+{
+    const int en = e + d;
+    if (en < 0 || en >= g.nE) return 0u;
+    const double x = -(g.beta * (double)dej) + (g.lnW[en] - g.lnW[e]);
+    return thr_of(x);
+}
+
+template <class F>
+void parallel_rows(int n, F f)
+{
+    const int min_rows = 4096;
+    int nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+    if (n < 2 * min_rows || nt <= 1) {
+        f(0, n);
+        return;
+    }
+    nt = std::min(nt, n / min_rows);
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t)
+        th.emplace_back(f, (int)((int64_t)n * t / nt), (int)((int64_t)n * (t + 1) / nt));
+    f(0, (int)((int64_t)n / nt));
+    for (auto &x : th) x.join();
+}
+
+// Packed table of group g from its lnW into the pinned host buffers.
+void build_packed(Group &g)
+{
+    uint32_t *T = g.h_thrE;
+    parallel_rows(g.nE, [&g, T](int b, int e_end) {
+        for (int e = b; e < e_end; ++e) {
+            uint32_t *row = T + (size_t)e * kRow;
+            for (int dej = -6; dej <= 6; ++dej) {
+                row[dej + 6] = thr_entry(g, e, -1, dej);
+                row[kRowPlus + dej + 6] = thr_entry(g, e, +1, dej);
+            }
+            for (int c = 2 * kRowPlus; c < kRow; ++c) row[c] = 0u;
+        }
+    });
+    for (int k = 0; k < kThr0; ++k) g.h_thr0[k] = k < 13 ? thr_entry(g, 0, 0, 2 * k - 12) : 0u;
+}
+
+// Pack a logical [nE][3][25] table.
+int pack_logical(muca_ctx *ctx, Group &g, const uint32_t *lg)
+{
+    for (int e = 0; e < g.nE; ++e) {
+        const uint32_t *r = lg + (size_t)e * 3 * MUCA_NK;
+        uint32_t *row = g.h_thrE + (size_t)e * kRow;
+        for (int dej = -6; dej <= 6; ++dej) {
+            row[dej + 6] = r[0 * MUCA_NK + dej + 12];
+            row[kRowPlus + dej + 6] = r[2 * MUCA_NK + dej + 12];
+        }
+        for (int c = 2 * kRowPlus; c < kRow; ++c) row[c] = 0u;
+        for (int k = 0; k < 13; ++k)
+            if (r[1 * MUCA_NK + 2 * k] != lg[1 * MUCA_NK + 2 * k])
+                return fail(ctx, MUCA_ERR_INVALID_ARG,
+                            "set_table: d = 0 entries must not depend on E_Delta (row %d)", e);
+    }
+    for (int k = 0; k < kThr0; ++k) g.h_thr0[k] = k < 13 ? lg[1 * MUCA_NK + 2 * k] : 0u;
+    return MUCA_OK;
+}
+
+int upload_table(muca_ctx *ctx, Group &g)
+{
+    CK(cudaMemcpyAsync(g.thrE, g.h_thrE, (size_t)g.nE * kRow * sizeof(uint32_t),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(g.thr0, g.h_thr0, kThr0 * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    return MUCA_OK;
+}
+
+// The weight recursion of one iteration: lnW[E] -= ln H[E] where H[E] > 0.
+void update_lnW(Group &g)
+{
+    for (int e = 0; e < g.nE; ++e)
+        if (g.h_hist[e] > 0) g.lnW[e] -= std::log((double)g.h_hist[e]);
+}
+
+GroupDev dev_of(const Group &g)
+{
+    GroupDev d{};
+    d.L = g.L;
+    d.V = g.V;
+    d.W = g.W;
+    d.Wpad = g.Wpad;
+    d.e_min = g.e_min;
+    d.nE = g.nE;
+    d.walker0 = g.walker0;
+    d.spins = g.spins;
+    d.tal = g.tal;
+    d.hist = g.hist;
+    d.thrE = g.thrE;
+    d.thr0 = g.thr0;
+    d.ts = g.ts;
+    return d;
+}
+
+int upload_groups(muca_ctx *ctx)
+{
+    std::vector<GroupDev> gd;
+    for (auto &g : ctx->g) gd.push_back(dev_of(g));
+    CK(cudaMemcpy(ctx->d_groups, gd.data(), gd.size() * sizeof(GroupDev), cudaMemcpyHostToDevice));
+    return MUCA_OK;
+}
+
+// Block lists of the global-residency and shared-memory-resident launches.
+// A shared-memory block of group g holds wpb_g lattices as a [V_g][wpb_g] tile.
+int build_blocks(muca_ctx *ctx)
+{
+    std::vector<BlockDesc> bg, bs;
+    int wpb_g = 0, G = 0;
+    size_t smem = 0;
+    for (size_t gi = 0; gi < ctx->g.size(); ++gi) {
+        const Group &g = ctx->g[gi];
+        if (g.residency == MUCA_RES_SMEM) {
+            G = std::max(G, g.wpb);
+            smem = std::max(smem, smem_bytes_for(g.V, g.wpb));
+        } else {
+            wpb_g = std::max(wpb_g, g.wpb);
+        }
+        for (int w0 = 0; w0 < g.W; w0 += g.wpb) {
+            BlockDesc b{(int)gi, w0, std::min(g.wpb, g.W - w0), g.wpb};
+            (g.residency == MUCA_RES_SMEM ? bs : bg).push_back(b);
+        }
+    }
+    if (smem > 0) {
+        if ((int64_t)smem + 1024 > (int64_t)max_smem_per_block())
+            return fail(ctx, MUCA_ERR_INVALID_ARG, "shared-memory tile of %zu bytes does not fit",
+                        smem);
+        CK(prepare_smem_kernel(smem));
+    }
+    if (ctx->d_blocks_g) cudaFree(ctx->d_blocks_g);
+    if (ctx->d_blocks_s) cudaFree(ctx->d_blocks_s);
+    ctx->d_blocks_g = ctx->d_blocks_s = nullptr;
+    if (!bg.empty()) {
+        CK(cudaMalloc(&ctx->d_blocks_g, bg.size() * sizeof(BlockDesc)));
+        CK(cudaMemcpy(ctx->d_blocks_g, bg.data(), bg.size() * sizeof(BlockDesc),
+                      cudaMemcpyHostToDevice));
+    }
+    if (!bs.empty()) {
+        CK(cudaMalloc(&ctx->d_blocks_s, bs.size() * sizeof(BlockDesc)));
+        CK(cudaMemcpy(ctx->d_blocks_s, bs.data(), bs.size() * sizeof(BlockDesc),
+                      cudaMemcpyHostToDevice));
+    }
+    ctx->n_blocks_g = (int)bg.size();
+    ctx->n_blocks_s = (int)bs.size();
+    ctx->threads_g = wpb_g > 0 ? wpb_g : 32;
+    ctx->threads_s = G > 0 ? ((G + 31) / 32) * 32 : 32;
+    ctx->smem_bytes = smem;
+    return MUCA_OK;
+}
+
+// One launch (or two, on forked streams, when both residencies are in use)
+// sweeping every walker of every group.
+int launch_all(muca_ctx *ctx, int n_sweeps, bool record)
+{
+    const bool both = ctx->n_blocks_g > 0 && ctx->n_blocks_s > 0;
+    if (both) {
+        CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    }
+    if (ctx->n_blocks_g > 0)
+        CK(launch_sweeps(ctx->d_groups, ctx->d_blocks_g, ctx->n_blocks_g, ctx->threads_g, 0,
+                         ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record, ctx->stream));
+    if (ctx->n_blocks_s > 0)
+        CK(launch_sweeps(ctx->d_groups, ctx->d_blocks_s, ctx->n_blocks_s, ctx->threads_s,
+                         ctx->smem_bytes, ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record,
+                         both ? ctx->side : ctx->stream));
+    if (both) {
+        CK(cudaEventRecord(ctx->ev_join, ctx->side));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    }
+    return MUCA_OK;
+}
+
+int check_group_index(muca_ctx *ctx, int group)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    if (group < 0 || group >= (int)ctx->g.size())
+        return fail(ctx, MUCA_ERR_INVALID_ARG, "group %d out of range [0, %d)", group,
+                    (int)ctx->g.size());
+    return MUCA_OK;
+}
+
+int run_tally_check(muca_ctx *ctx)
+{
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    for (auto &g : ctx->g) CK(launch_energies(dev_of(g), 1, ctx->d_err, ctx->stream));
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h) return fail(ctx, MUCA_ERR_TALLY_MISMATCH, "running tallies differ from recomputed");
+    return MUCA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: for MUCA_RES_AUTO / walkers_per_block = 0, time a few sweeps of
+// each candidate configuration on a scratch copy of the group's state (the
+// real state is restored, so results never depend on the choice) and keep
+// the fastest.  Choices are cached per (L, walkers) for the process.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, std::pair<int, int>> g_tune_cache;
+
+struct Cand {
+    int res, wpb;
+};
+
+std::vector<Cand> candidates(const Group &g, int residency, int wpb, int smem_max)
+{
+    std::vector<Cand> c;
+    const bool want_g = residency == MUCA_RES_AUTO || residency == MUCA_RES_GLOBAL;
+    const bool want_s = residency == MUCA_RES_AUTO || residency == MUCA_RES_SMEM;
+    if (want_g) {
+        if (wpb > 0) c.push_back({MUCA_RES_GLOBAL, wpb});
+        else
+            for (int w : {32, 64, 128})
+                if (w <= std::max(32, g.Wpad)) c.push_back({MUCA_RES_GLOBAL, w});
+    }
+    if (want_s) {
+        const int fit = (int)std::min<int64_t>(32, (int64_t)(smem_max - 1024) / g.V);
+        if (wpb > 0 && wpb <= fit) c.push_back({MUCA_RES_SMEM, wpb});
+        else if (wpb <= 0)
+            for (int G : {32, 16, 8})
+                if (G <= fit) c.push_back({MUCA_RES_SMEM, G});
+    }
+    return c;
+}
+
+}  // namespace
+
+static int tune_group(muca_ctx *ctx, size_t gi, int residency, int wpb)
+{
+    Group &g = ctx->g[gi];
+    const int smem_max = max_smem_per_block();
+    std::vector<Cand> cands = candidates(g, residency, wpb, smem_max);
+    if (cands.empty())
+        return fail(ctx, MUCA_ERR_INVALID_ARG,
+                    "no kernel configuration fits group %d (L=%d, residency %d, wpb %d)", (int)gi,
+                    g.L, residency, wpb);
+    // a group outside its window cannot be swept yet: take the first candidate
+    if (cands.size() == 1 || !g.in_window) {
+        g.residency = cands[0].res;
+        g.wpb = cands[0].wpb;
+        return MUCA_OK;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find({g.L, g.W});
+        if (it != g_tune_cache.end()) {
+            g.residency = it->second.first;
+            g.wpb = it->second.second;
+            return MUCA_OK;
+        }
+    }
+    // scratch copy of the state
+    const size_t sb = (size_t)g.V * g.Wpad, tb = (size_t)3 * g.Wpad * sizeof(int32_t),
+                 hb = (size_t)g.nE * sizeof(unsigned long long);
+    int8_t *s0 = nullptr;
+    int32_t *t0 = nullptr;
+    unsigned long long *h0 = nullptr;
+    CK(cudaMalloc(&s0, sb));
+    CK(cudaMalloc(&t0, tb));
+    CK(cudaMalloc(&h0, hb));
+    CK(cudaMemcpyAsync(s0, g.spins, sb, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(t0, g.tal, tb, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(h0, g.hist, hb, cudaMemcpyDeviceToDevice, ctx->stream));
+    // a one-group context view for the trial launches
+    std::vector<Group> saved_groups;
+    saved_groups.swap(ctx->g);
+    ctx->g.push_back(saved_groups[gi]);
+    GroupDev *saved_dg = ctx->d_groups;
+    GroupDev *dg = nullptr;
+    CK(cudaMalloc(&dg, sizeof(GroupDev)));
+    ctx->d_groups = dg;
+    int rc = upload_groups(ctx);
+    const int trial_sweeps = std::max(1, std::min(8, (int)(4096 * 4 / std::max(1, g.V))));
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    Cand pick = cands[0];
+    for (const Cand &c : cands) {
+        if (rc != MUCA_OK) break;
+        ctx->g[0].residency = c.res;
+        ctx->g[0].wpb = c.wpb;
+        rc = build_blocks(ctx);
+        if (rc != MUCA_OK) break;
+        rc = launch_all(ctx, 1, false);  // warm-up
+        cudaEventRecord(a, ctx->stream);
+        if (rc == MUCA_OK) rc = launch_all(ctx, trial_sweeps, false);
+        cudaEventRecord(b, ctx->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) rc = MUCA_ERR_CUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rc == MUCA_OK && ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->g.swap(saved_groups);
+    ctx->d_groups = saved_dg;
+    cudaFree(dg);
+    // restore the state
+    cudaMemcpyAsync(g.spins, s0, sb, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(g.tal, t0, tb, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaMemcpyAsync(g.hist, h0, hb, cudaMemcpyDeviceToDevice, ctx->stream);
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(s0);
+    cudaFree(t0);
+    cudaFree(h0);
+    if (rc != MUCA_OK) return rc;
+    g.residency = pick.res;
+    g.wpb = pick.wpb;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[{g.L, g.W}] = {pick.res, pick.wpb};
+    return MUCA_OK;
+}
+
+static void free_group(Group &g)
+{
+    cudaFree(g.spins);
+    cudaFree(g.tal);
+    cudaFree(g.hist);
+    cudaFree(g.thrE);
+    cudaFree(g.thr0);
+    cudaFree(g.ts);
+    cudaFreeHost(g.h_thrE);
+    cudaFreeHost(g.h_thr0);
+    cudaFreeHost(g.h_hist);
+    g.spins = nullptr;
+    g.tal = nullptr;
+    g.hist = nullptr;
+    g.thrE = g.thr0 = nullptr;
+    g.ts = nullptr;
+    g.h_thrE = g.h_thr0 = nullptr;
+    g.h_hist = nullptr;
+}
+
+namespace muca {
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace muca
+
+extern "C" {
+
+const char *muca_last_error(const muca_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+void muca_destroy(muca_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &g : ctx->g) free_group(g);
+    cudaFree(ctx->d_err);
+    cudaFree(ctx->d_groups);
+    cudaFree(ctx->d_blocks_g);
+    cudaFree(ctx->d_blocks_s);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    delete ctx;
+}
+
+int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, void *stream,
+              muca_ctx **out)
+{
+    muca_ctx *ctx = nullptr;
+    if (!out) return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: out is NULL");
+    *out = nullptr;
+    if (!groups || n_groups < 1 || !opt)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: need >= 1 group and options");
+    if (opt->residency < MUCA_RES_AUTO || opt->residency > MUCA_RES_SMEM)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad residency %d", opt->residency);
+    if (opt->walkers_per_block < 0 || opt->walkers_per_block > 1024)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad walkers_per_block %d",
+                    opt->walkers_per_block);
+    int64_t total_w = 0;
+    for (int i = 0; i < n_groups; ++i) {
+        const muca_group &s = groups[i];
+        if (s.L < 2 || s.L > MUCA_MAX_L)
+            return fail(nullptr, MUCA_ERR_INVALID_ARG, "group %d: L=%d outside [2, %d]", i, s.L,
+                        MUCA_MAX_L);
+        if (!(s.T > 0.0) || !std::isfinite(s.T))
+            return fail(nullptr, MUCA_ERR_INVALID_ARG, "group %d: T must be > 0", i);
+        if (s.n_walkers < 1)
+            return fail(nullptr, MUCA_ERR_INVALID_ARG, "group %d: n_walkers < 1", i);
+        const int V = s.L * s.L * s.L;
+        const int emax = s.e_max < 0 ? V : s.e_max;
+        if (s.e_min < 0 || emax > V || s.e_min > emax)
+            return fail(nullptr, MUCA_ERR_INVALID_ARG, "group %d: window [%d, %d] not in [0, %d]",
+                        i, s.e_min, emax, V);
+        total_w += s.n_walkers;
+    }
+    if (total_w > 0x7FFFFFFF)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "too many walkers");
+    ctx = new muca_ctx();
+    ctx->seed = opt->seed;
+    ctx->debug = opt->debug_flags;
+    ctx->stream = (cudaStream_t)stream;
+    int rc = MUCA_OK;
+#define CKI(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            rc = fail(ctx, e_ == cudaErrorMemoryAllocation ? MUCA_ERR_OOM : MUCA_ERR_CUDA, \
+                      "%s: %s", #call, cudaGetErrorString(e_));                            \
+            goto bad;                                                                      \
+        }                                                                                  \
+    } while (0)
+    {
+        CKI(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        CKI(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        CKI(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+        CKI(cudaMalloc(&ctx->d_err, sizeof(int)));
+        CKI(cudaMalloc(&ctx->d_groups, n_groups * sizeof(GroupDev)));
+        uint32_t w0 = 0;
+        ctx->g.resize(n_groups);
+        for (int i = 0; i < n_groups; ++i) {
+            Group &g = ctx->g[i];
+            g.spec = groups[i];
+            g.L = groups[i].L;
+            g.V = g.L * g.L * g.L;
+            g.W = groups[i].n_walkers;
+            g.Wpad = ((g.W + 31) / 32) * 32;
+            g.e_min = groups[i].e_min;
+            g.e_max = groups[i].e_max < 0 ? g.V : groups[i].e_max;
+            g.spec.e_max = g.e_max;
+            g.nE = g.e_max - g.e_min + 1;
+            g.T = groups[i].T;
+            g.beta = 1.0 / g.T;
+            g.walker0 = w0;
+            w0 += (uint32_t)g.W;
+            g.lnW.assign(g.nE, 0.0);
+            CKI(cudaMalloc(&g.spins, (size_t)g.V * g.Wpad));
+            CKI(cudaMemsetAsync(g.spins, 0, (size_t)g.V * g.Wpad, ctx->stream));
+            CKI(cudaMalloc(&g.tal, (size_t)3 * g.Wpad * sizeof(int32_t)));
+            CKI(cudaMemsetAsync(g.tal, 0, (size_t)3 * g.Wpad * sizeof(int32_t), ctx->stream));
+            CKI(cudaMalloc(&g.hist, (size_t)g.nE * sizeof(unsigned long long)));
+            CKI(cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long), ctx->stream));
+            CKI(cudaMalloc(&g.thrE, (size_t)g.nE * kRow * sizeof(uint32_t)));
+            CKI(cudaMalloc(&g.thr0, kThr0 * sizeof(uint32_t)));
+            CKI(cudaMallocHost(&g.h_thrE, (size_t)g.nE * kRow * sizeof(uint32_t)));
+            CKI(cudaMallocHost(&g.h_thr0, kThr0 * sizeof(uint32_t)));
+            CKI(cudaMallocHost(&g.h_hist, (size_t)g.nE * sizeof(unsigned long long)));
+            CKI(launch_init_spins(dev_of(g), ctx->seed, ctx->stream));
+            CKI(launch_energies(dev_of(g), 0, ctx->d_err, ctx->stream));
+            build_packed(g);
+            if ((rc = upload_table(ctx, g)) != MUCA_OK) goto bad;
+        }
+        if ((rc = upload_groups(ctx)) != MUCA_OK) goto bad;
+        CKI(cudaStreamSynchronize(ctx->stream));
+        // a group whose initial E_Delta values leave its window must get a
+        // state through muca_set_state before it can be swept
+        for (int i = 0; i < n_groups; ++i) {
+            Group &g = ctx->g[i];
+            std::vector<int32_t> ed(g.W);
+            CKI(cudaMemcpy(ed.data(), g.tal + g.Wpad, g.W * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost));
+            g.in_window = true;
+            for (int w = 0; w < g.W; ++w)
+                if (ed[w] < g.e_min || ed[w] > g.e_max) g.in_window = false;
+        }
+        for (int i = 0; i < n_groups; ++i)
+            if ((rc = tune_group(ctx, i, opt->residency, opt->walkers_per_block)) != MUCA_OK)
+                goto bad;
+        if ((rc = build_blocks(ctx)) != MUCA_OK) goto bad;
+        CKI(cudaStreamSynchronize(ctx->stream));
+    }
+#undef CKI
+    *out = ctx;
+    return MUCA_OK;
+bad:
+    g_last_error = ctx->err;
+    muca_destroy(ctx);
+    return rc;
+}
+
+int muca_sync(muca_ctx *ctx)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_sweep_iter(muca_ctx *ctx, int n_sweeps, int record)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    if (n_sweeps < 0) return fail(ctx, MUCA_ERR_INVALID_ARG, "n_sweeps < 0");
+    if (n_sweeps == 0) return MUCA_OK;
+    for (size_t i = 0; i < ctx->g.size(); ++i)
+        if (!ctx->g[i].in_window)
+            return fail(ctx, MUCA_ERR_WINDOW,
+                        "group %d has walkers outside its E_Delta window: set a state first",
+                        (int)i);
+    if (record && ctx->ts_len + n_sweeps > ctx->ts_cap)
+        return fail(ctx, MUCA_ERR_INVALID_ARG,
+                    "time series full: %lld recorded + %d > capacity %lld (muca_reserve_timeseries)",
+                    (long long)ctx->ts_len, n_sweeps, (long long)ctx->ts_cap);
+    int rc = launch_all(ctx, n_sweeps, record != 0);
+    if (rc != MUCA_OK) return rc;
+    ctx->sweep += (uint64_t)n_sweeps;
+    if (record) ctx->ts_len += n_sweeps;
+    if (ctx->debug & MUCA_DEBUG_TALLY_CHECK) return run_tally_check(ctx);
+    return MUCA_OK;
+}
+
+int muca_merge_update(muca_ctx *ctx)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    for (auto &g : ctx->g)
+        CK(cudaMemcpyAsync(g.h_hist, g.hist, (size_t)g.nE * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (auto &g : ctx->g) {
+        update_lnW(g);
+        g.injected.clear();
+        build_packed(g);
+        int rc = upload_table(ctx, g);
+        if (rc != MUCA_OK) return rc;
+        CK(cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long), ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct HostUpdateArg {
+    Group *g;
+};
+
+void CUDART_CB host_update(void *p)
+{
+    Group &g = *static_cast<Group *>(p);
+    update_lnW(g);
+    g.injected.clear();
+    build_packed(g);
+}
+
+}  // namespace
+
+extern "C" int muca_run_graph(muca_ctx *ctx, int n_iters, int sweeps_per_iter)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    if (n_iters < 0 || sweeps_per_iter < 0)
+        return fail(ctx, MUCA_ERR_INVALID_ARG, "negative n_iters or sweeps_per_iter");
+    if (n_iters == 0) return MUCA_OK;
+    for (size_t i = 0; i < ctx->g.size(); ++i)
+        if (!ctx->g[i].in_window)
+            return fail(ctx, MUCA_ERR_WINDOW,
+                        "group %d has walkers outside its E_Delta window: set a state first",
+                        (int)i);
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const uint64_t sweep_start = ctx->sweep;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = MUCA_OK;
+    for (int it = 0; it < n_iters && rc == MUCA_OK; ++it) {
+        rc = launch_all(ctx, sweeps_per_iter, false);
+        ctx->sweep += (uint64_t)sweeps_per_iter;
+        for (auto &g : ctx->g) {
+            if (rc != MUCA_OK) break;
+            if (cudaMemcpyAsync(g.h_hist, g.hist, (size_t)g.nE * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+                cudaLaunchHostFunc(ctx->stream, host_update, &g) != cudaSuccess ||
+                cudaMemcpyAsync(g.thrE, g.h_thrE, (size_t)g.nE * kRow * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+                cudaMemcpyAsync(g.thr0, g.h_thr0, kThr0 * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+                cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long),
+                                ctx->stream) != cudaSuccess)
+                rc = fail(ctx, MUCA_ERR_CUDA, "graph capture of the merge failed");
+        }
+    }
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (rc == MUCA_OK && ce != cudaSuccess)
+        rc = fail(ctx, MUCA_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ce));
+    if (rc == MUCA_OK) {
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (ce != cudaSuccess)
+            rc = fail(ctx, MUCA_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ce));
+    }
+    if (rc == MUCA_OK) {
+        ce = cudaGraphLaunch(exec, ctx->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+        if (ce != cudaSuccess)
+            rc = fail(ctx, MUCA_ERR_CUDA, "graph launch: %s", cudaGetErrorString(ce));
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != MUCA_OK) ctx->sweep = sweep_start;
+    return rc;
+}
+
+extern "C" {
+
+int muca_reserve_timeseries(muca_ctx *ctx, int64_t n_samples)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    if (n_samples < 0) return fail(ctx, MUCA_ERR_INVALID_ARG, "n_samples < 0");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->ts_len = 0;
+    if (n_samples == ctx->ts_cap) return MUCA_OK;  // same capacity: only rewind
+    for (auto &g : ctx->g) {
+        cudaFree(g.ts);
+        g.ts = nullptr;
+    }
+    ctx->ts_cap = 0;
+    for (auto &g : ctx->g)
+        if (n_samples > 0) CK(cudaMalloc(&g.ts, (size_t)n_samples * 3 * g.W * sizeof(int32_t)));
+    ctx->ts_cap = n_samples;
+    return upload_groups(ctx);
+}
+
+int muca_timeseries_device(muca_ctx *ctx, int group, const int32_t **dev, int64_t *n_samples)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (dev) *dev = ctx->g[group].ts;
+    if (n_samples) *n_samples = ctx->ts_len;
+    return MUCA_OK;
+}
+
+int muca_get_timeseries(muca_ctx *ctx, int group, int32_t *out)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!out) return fail(ctx, MUCA_ERR_INVALID_ARG, "out is NULL");
+    Group &g = ctx->g[group];
+    if (ctx->ts_len > 0)
+        CK(cudaMemcpyAsync(out, g.ts, (size_t)ctx->ts_len * 3 * g.W * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_get_sweep_count(muca_ctx *ctx, int group, uint64_t *out)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!out) return fail(ctx, MUCA_ERR_INVALID_ARG, "out is NULL");
+    *out = ctx->sweep;
+    return MUCA_OK;
+}
+
+int muca_get_lnW(muca_ctx *ctx, int group, double *out)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!out) return fail(ctx, MUCA_ERR_INVALID_ARG, "out is NULL");
+    const Group &g = ctx->g[group];
+    std::memcpy(out, g.lnW.data(), g.nE * sizeof(double));
+    return MUCA_OK;
+}
+
+int muca_set_lnW(muca_ctx *ctx, int group, const double *in)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!in) return fail(ctx, MUCA_ERR_INVALID_ARG, "in is NULL");
+    Group &g = ctx->g[group];
+    for (int e = 0; e < g.nE; ++e)
+        if (!std::isfinite(in[e])) return fail(ctx, MUCA_ERR_INVALID_ARG, "lnW[%d] not finite", e);
+    CK(cudaStreamSynchronize(ctx->stream));  // the pinned table may still be in flight
+    std::memcpy(g.lnW.data(), in, g.nE * sizeof(double));
+    g.injected.clear();
+    build_packed(g);
+    rc = upload_table(ctx, g);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_get_table(muca_ctx *ctx, int group, uint32_t *out)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!out) return fail(ctx, MUCA_ERR_INVALID_ARG, "out is NULL");
+    const Group &g = ctx->g[group];
+    if (!g.injected.empty()) {
+        std::memcpy(out, g.injected.data(), g.injected.size() * sizeof(uint32_t));
+        return MUCA_OK;
+    }
+    for (int e = 0; e < g.nE; ++e)
+        for (int d = -1; d <= 1; ++d)
+            for (int dej = -12; dej <= 12; ++dej)
+                out[((size_t)e * 3 + (d + 1)) * MUCA_NK + (dej + 12)] = thr_entry(g, e, d, dej);
+    return MUCA_OK;
+}
+
+int muca_set_table(muca_ctx *ctx, int group, const uint32_t *in)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!in) return fail(ctx, MUCA_ERR_INVALID_ARG, "in is NULL");
+    Group &g = ctx->g[group];
+    CK(cudaStreamSynchronize(ctx->stream));
+    rc = pack_logical(ctx, g, in);
+    if (rc) return rc;
+    g.injected.assign(in, in + (size_t)g.nE * 3 * MUCA_NK);
+    rc = upload_table(ctx, g);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_get_hist(muca_ctx *ctx, int group, uint64_t *out)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!out) return fail(ctx, MUCA_ERR_INVALID_ARG, "out is NULL");
+    Group &g = ctx->g[group];
+    CK(cudaMemcpyAsync(out, g.hist, (size_t)g.nE * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_set_hist(muca_ctx *ctx, int group, const uint64_t *in)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!in) return fail(ctx, MUCA_ERR_INVALID_ARG, "in is NULL");
+    Group &g = ctx->g[group];
+    CK(cudaMemcpyAsync(g.hist, in, (size_t)g.nE * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_get_state(muca_ctx *ctx, int group, int8_t *spins, int32_t *tallies)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    Group &g = ctx->g[group];
+    if (spins) {
+        std::vector<int8_t> dev((size_t)g.V * g.Wpad);
+        CK(cudaMemcpyAsync(dev.data(), g.spins, dev.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int w = 0; w < g.W; ++w)
+            for (int i = 0; i < g.V; ++i)
+                spins[(size_t)w * g.V + i] = dev[(size_t)i * g.Wpad + w];
+    }
+    if (tallies) {
+        std::vector<int32_t> t((size_t)3 * g.Wpad);
+        CK(cudaMemcpyAsync(t.data(), g.tal, t.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int w = 0; w < g.W; ++w)
+            for (int f = 0; f < 3; ++f) tallies[3 * w + f] = t[(size_t)f * g.Wpad + w];
+    }
+    return MUCA_OK;
+}
+
+int muca_set_state(muca_ctx *ctx, int group, const int8_t *spins)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!spins) return fail(ctx, MUCA_ERR_INVALID_ARG, "spins is NULL");
+    Group &g = ctx->g[group];
+    std::vector<int8_t> dev((size_t)g.V * g.Wpad, 0);
+    for (int w = 0; w < g.W; ++w)
+        for (int i = 0; i < g.V; ++i) {
+            const int8_t s = spins[(size_t)w * g.V + i];
+            if (s < -1 || s > 1)
+                return fail(ctx, MUCA_ERR_INVALID_ARG, "walker %d site %d: spin %d", w, i, s);
+            dev[(size_t)i * g.Wpad + w] = s;
+        }
+    std::vector<int32_t> old((size_t)3 * g.Wpad);
+    CK(cudaMemcpyAsync(old.data(), g.tal, old.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    std::vector<int8_t> old_spins(dev.size());
+    CK(cudaMemcpyAsync(old_spins.data(), g.spins, dev.size(), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(g.spins, dev.data(), dev.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_energies(dev_of(g), 0, ctx->d_err, ctx->stream));
+    std::vector<int32_t> t((size_t)3 * g.Wpad);
+    CK(cudaMemcpyAsync(t.data(), g.tal, t.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int w = 0; w < g.W; ++w) {
+        const int ed = t[(size_t)g.Wpad + w];
+        if (ed < g.e_min || ed > g.e_max) {
+            // put the previous state back
+            CK(cudaMemcpyAsync(g.spins, old_spins.data(), old_spins.size(),
+                               cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(g.tal, old.data(), old.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            return fail(ctx, MUCA_ERR_WINDOW, "walker %d: E_Delta=%d outside [%d, %d]", w, ed,
+                        g.e_min, g.e_max);
+        }
+    }
+    g.in_window = true;
+    return MUCA_OK;
+}
+
+int muca_check_tallies(muca_ctx *ctx)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    return run_tally_check(ctx);
+}
+
+int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walkers_per_block)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (residency) *residency = ctx->g[group].residency;
+    if (walkers_per_block) *walkers_per_block = ctx->g[group].wpb;
+    return MUCA_OK;
+}
+
+// Checkpoint file: magic, version, seed, sweep, n_groups, per group the spec,
+// then per group lnW[nE], hist[nE], tallies[3][Wpad], spins[V][Wpad].
+static const char kMagic[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '1'};
+
+int muca_checkpoint(muca_ctx *ctx, const char *path)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    if (!path) return fail(ctx, MUCA_ERR_INVALID_ARG, "path is NULL");
+    CK(cudaStreamSynchronize(ctx->stream));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, MUCA_ERR_IO, "cannot open %s for writing", path);
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
+    const int32_t ng = (int32_t)ctx->g.size();
+    ok = ok && std::fwrite(&ctx->seed, sizeof ctx->seed, 1, f) == 1;
+    ok = ok && std::fwrite(&ctx->sweep, sizeof ctx->sweep, 1, f) == 1;
+    ok = ok && std::fwrite(&ng, sizeof ng, 1, f) == 1;
+    for (auto &g : ctx->g) ok = ok && std::fwrite(&g.spec, sizeof g.spec, 1, f) == 1;
+    for (auto &g : ctx->g) {
+        if (!ok) break;
+        std::vector<unsigned long long> h(g.nE);
+        std::vector<int32_t> t((size_t)3 * g.Wpad);
+        std::vector<int8_t> s((size_t)g.V * g.Wpad);
+        if (cudaMemcpy(h.data(), g.hist, h.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(t.data(), g.tal, t.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(s.data(), g.spins, s.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(f);
+            return fail(ctx, MUCA_ERR_CUDA, "checkpoint: device read failed");
+        }
+        ok = ok && std::fwrite(g.lnW.data(), 8, g.nE, f) == (size_t)g.nE;
+        ok = ok && std::fwrite(h.data(), 8, h.size(), f) == h.size();
+        ok = ok && std::fwrite(t.data(), 4, t.size(), f) == t.size();
+        ok = ok && std::fwrite(s.data(), 1, s.size(), f) == s.size();
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(ctx, MUCA_ERR_IO, "checkpoint: write to %s failed", path);
+    return MUCA_OK;
+}
+
+int muca_restore(muca_ctx *ctx, const char *path)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    if (!path) return fail(ctx, MUCA_ERR_INVALID_ARG, "path is NULL");
+    CK(cudaStreamSynchronize(ctx->stream));
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, MUCA_ERR_IO, "cannot open %s", path);
+    char magic[8];
+    uint32_t seed = 0;
+    uint64_t sweep = 0;
+    int32_t ng = 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0;
+    ok = ok && std::fread(&seed, sizeof seed, 1, f) == 1;
+    ok = ok && std::fread(&sweep, sizeof sweep, 1, f) == 1;
+    ok = ok && std::fread(&ng, sizeof ng, 1, f) == 1 && ng == (int32_t)ctx->g.size();
+    for (auto &g : ctx->g) {
+        muca_group s{};
+        ok = ok && std::fread(&s, sizeof s, 1, f) == 1 && s.L == g.spec.L && s.T == g.spec.T &&
+             s.n_walkers == g.spec.n_walkers && s.e_min == g.spec.e_min &&
+             s.e_max == g.spec.e_max;
+    }
+    if (!ok) {
+        std::fclose(f);
+        return fail(ctx, MUCA_ERR_INVALID_ARG, "restore: %s does not match this context", path);
+    }
+    for (auto &g : ctx->g) {
+        std::vector<double> lnW(g.nE);
+        std::vector<unsigned long long> h(g.nE);
+        std::vector<int32_t> t((size_t)3 * g.Wpad);
+        std::vector<int8_t> s((size_t)g.V * g.Wpad);
+        ok = std::fread(lnW.data(), 8, g.nE, f) == (size_t)g.nE &&
+             std::fread(h.data(), 8, h.size(), f) == h.size() &&
+             std::fread(t.data(), 4, t.size(), f) == t.size() &&
+             std::fread(s.data(), 1, s.size(), f) == s.size();
+        if (!ok) {
+            std::fclose(f);
+            return fail(ctx, MUCA_ERR_IO, "restore: %s is truncated", path);
+        }
+        g.lnW = lnW;
+        g.injected.clear();
+        g.in_window = true;
+        if (cudaMemcpy(g.hist, h.data(), h.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(g.tal, t.data(), t.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(g.spins, s.data(), s.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(f);
+            return fail(ctx, MUCA_ERR_CUDA, "restore: device write failed");
+        }
+        build_packed(g);
+        int rc = upload_table(ctx, g);
+        if (rc) {
+            std::fclose(f);
+            return rc;
+        }
+    }
+    std::fclose(f);
+    ctx->seed = seed;
+    ctx->sweep = sweep;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,299 @@
+"""Thin Python binding of ``libmuca.so`` (the C ABI in ``include/muca.h``).
+
+Argument marshalling only: every step of the simulation and of the
+reweighting runs in the library's CUDA kernels.  Device buffers handed to the
+library are torch CUDA tensors (``data_ptr()``), streams are torch streams
+(``cuda_stream``).  There is no CPU fallback: if the library cannot be loaded
+the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmuca.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CUDA = -2
+ERR_OOM = -3
+ERR_TIMEOUT = -4
+ERR_TALLY_MISMATCH = -5
+ERR_NOT_SUPPORTED = -6
+ERR_WINDOW = -7
+ERR_IO = -8
+
+RES_AUTO, RES_GLOBAL, RES_SMEM = 0, 1, 2
+DEBUG_TALLY_CHECK = 1
+NK = 25
+
+
+class MucaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class Group(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("T", ctypes.c_double), ("n_walkers", ctypes.c_int32),
+                ("e_min", ctypes.c_int32), ("e_max", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint32), ("debug_flags", ctypes.c_int32),
+                ("residency", ctypes.c_int32), ("walkers_per_block", ctypes.c_int32)]
+
+
+_lib = None
+
+# exported symbols and their argument types
+_P = ctypes.c_void_p
+_I32, _I64, _U64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+SIGNATURES = {
+    "muca_init": [_P, ctypes.c_int, _P, _P, _P],
+    "muca_destroy": [_P],
+    "muca_last_error": [_P],
+    "muca_sync": [_P],
+    "muca_sweep_iter": [_P, ctypes.c_int, ctypes.c_int],
+    "muca_merge_update": [_P],
+    "muca_run_graph": [_P, ctypes.c_int, ctypes.c_int],
+    "muca_reweight": [_P, _P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _P, _I32, _I32,
+                      _P, _P],
+    "muca_reserve_timeseries": [_P, _I64],
+    "muca_timeseries_device": [_P, ctypes.c_int, _P, _P],
+    "muca_get_timeseries": [_P, ctypes.c_int, _P],
+    "muca_get_sweep_count": [_P, ctypes.c_int, _P],
+    "muca_get_lnW": [_P, ctypes.c_int, _P],
+    "muca_set_lnW": [_P, ctypes.c_int, _P],
+    "muca_get_table": [_P, ctypes.c_int, _P],
+    "muca_set_table": [_P, ctypes.c_int, _P],
+    "muca_get_hist": [_P, ctypes.c_int, _P],
+    "muca_set_hist": [_P, ctypes.c_int, _P],
+    "muca_get_state": [_P, ctypes.c_int, _P, _P],
+    "muca_set_state": [_P, ctypes.c_int, _P],
+    "muca_check_tallies": [_P],
+    "muca_get_config": [_P, ctypes.c_int, _P, _P],
+    "muca_checkpoint": [_P, ctypes.c_char_p],
+    "muca_restore": [_P, ctypes.c_char_p],
+}
+
+
+def lib(path=None):
+    """Load libmuca.so (building it first if it is missing); raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    L = ctypes.CDLL(path)
+    for name, argt in SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = argt
+        f.restype = ctypes.c_int
+    L.muca_destroy.restype = None
+    L.muca_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def last_error(ctx=None):
+    return lib().muca_last_error(ctx).decode()
+
+
+def _ck(rc, ctx=None):
+    if rc != OK:
+        raise MucaError(rc, last_error(ctx))
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Context:
+    """A set of (L, T) walker groups on one GPU (``muca_init`` .. ``muca_destroy``)."""
+
+    def __init__(self, groups, seed=0, debug_flags=0, residency=RES_AUTO, walkers_per_block=0,
+                 stream=None):
+        L = lib()
+        self.specs = []
+        arr = (Group * len(groups))()
+        for i, g in enumerate(groups):
+            g = dict(g)
+            e_max = g.get("e_max", -1)
+            arr[i] = Group(int(g["L"]), float(g["T"]), int(g["n_walkers"]), int(g.get("e_min", 0)),
+                           int(e_max))
+            V = int(g["L"]) ** 3
+            self.specs.append({"L": int(g["L"]), "T": float(g["T"]), "n_walkers": int(g["n_walkers"]),
+                               "e_min": int(g.get("e_min", 0)),
+                               "e_max": V if e_max < 0 else int(e_max), "V": V})
+        opt = Options(seed, debug_flags, residency, walkers_per_block)
+        self._stream = _stream_ptr(stream)
+        self._ctx = ctypes.c_void_p()
+        _ck(L.muca_init(ctypes.cast(arr, _P), len(groups), ctypes.byref(opt), self._stream,
+                        ctypes.byref(self._ctx)))
+
+    # -- lifetime
+    def close(self):
+        if self._ctx:
+            lib().muca_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _c(self, rc):
+        _ck(rc, self._ctx)
+
+    def n_e(self, g):
+        s = self.specs[g]
+        return s["e_max"] - s["e_min"] + 1
+
+    # -- hot path
+    def sweep_iter(self, n_sweeps, record=False):
+        self._c(lib().muca_sweep_iter(self._ctx, n_sweeps, int(bool(record))))
+
+    def merge_update(self):
+        self._c(lib().muca_merge_update(self._ctx))
+
+    def run_graph(self, n_iters, sweeps_per_iter):
+        self._c(lib().muca_run_graph(self._ctx, n_iters, sweeps_per_iter))
+
+    def sync(self):
+        self._c(lib().muca_sync(self._ctx))
+
+    # -- time series
+    def reserve_timeseries(self, n_samples):
+        self._c(lib().muca_reserve_timeseries(self._ctx, n_samples))
+
+    def timeseries_device(self, g):
+        p = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        self._c(lib().muca_timeseries_device(self._ctx, g, ctypes.byref(p), ctypes.byref(n)))
+        return p.value, n.value
+
+    def get_timeseries(self, g):
+        _, n = self.timeseries_device(g)
+        out = np.zeros((n, 3, self.specs[g]["n_walkers"]), dtype=np.int32)
+        if n:
+            self._c(lib().muca_get_timeseries(self._ctx, g, _np_ptr(out)))
+        return out
+
+    # -- inspection
+    def sweep_count(self, g=0):
+        v = ctypes.c_uint64()
+        self._c(lib().muca_get_sweep_count(self._ctx, g, ctypes.byref(v)))
+        return v.value
+
+    def get_lnW(self, g):
+        out = np.zeros(self.n_e(g))
+        self._c(lib().muca_get_lnW(self._ctx, g, _np_ptr(out)))
+        return out
+
+    def set_lnW(self, g, lnW):
+        a = np.ascontiguousarray(lnW, dtype=np.float64)
+        assert a.shape == (self.n_e(g),)
+        self._c(lib().muca_set_lnW(self._ctx, g, _np_ptr(a)))
+
+    def get_table(self, g):
+        out = np.zeros((self.n_e(g), 3, NK), dtype=np.uint32)
+        self._c(lib().muca_get_table(self._ctx, g, _np_ptr(out)))
+        return out
+
+    def set_table(self, g, thr):
+        a = np.ascontiguousarray(thr, dtype=np.uint32)
+        assert a.shape == (self.n_e(g), 3, NK)
+        self._c(lib().muca_set_table(self._ctx, g, _np_ptr(a)))
+
+    def get_hist(self, g):
+        out = np.zeros(self.n_e(g), dtype=np.uint64)
+        self._c(lib().muca_get_hist(self._ctx, g, _np_ptr(out)))
+        return out
+
+    def set_hist(self, g, h):
+        a = np.ascontiguousarray(h, dtype=np.uint64)
+        assert a.shape == (self.n_e(g),)
+        self._c(lib().muca_set_hist(self._ctx, g, _np_ptr(a)))
+
+    def get_state(self, g):
+        s = self.specs[g]
+        spins = np.zeros((s["n_walkers"], s["V"]), dtype=np.int8)
+        tal = np.zeros((s["n_walkers"], 3), dtype=np.int32)
+        self._c(lib().muca_get_state(self._ctx, g, _np_ptr(spins), _np_ptr(tal)))
+        return spins, tal
+
+    def set_state(self, g, spins):
+        s = self.specs[g]
+        a = np.ascontiguousarray(spins, dtype=np.int8)
+        assert a.shape == (s["n_walkers"], s["V"])
+        self._c(lib().muca_set_state(self._ctx, g, _np_ptr(a)))
+
+    def check_tallies(self):
+        self._c(lib().muca_check_tallies(self._ctx))
+
+    def get_config(self, g):
+        r = ctypes.c_int32()
+        w = ctypes.c_int32()
+        self._c(lib().muca_get_config(self._ctx, g, ctypes.byref(r), ctypes.byref(w)))
+        return r.value, w.value
+
+    def checkpoint(self, path):
+        self._c(lib().muca_checkpoint(self._ctx, os.fsencode(path)))
+
+    def restore(self, path):
+        self._c(lib().muca_restore(self._ctx, os.fsencode(path)))
+
+
+def reweight(e_j, e_d, m, lnW, e_min, beta, V, delta_grid, precision=64, n_rows=None,
+             row_len=None, row_stride=None, stream=None):
+    """``muca_reweight``: e_j, e_d, m are torch int32 CUDA tensors (or raw device
+    addresses with n_rows/row_len/row_stride given).  Returns numpy [n_grid][5]:
+    <E_J>, <E_Delta>, C, chi, U4."""
+    L = lib()
+    ptrs = []
+    for t in (e_j, e_d, m):
+        if isinstance(t, int):
+            ptrs.append(ctypes.c_void_p(t))
+        else:
+            import torch
+            assert t.is_cuda and t.dtype == torch.int32, "samples must be int32 CUDA tensors"
+            assert t.is_contiguous()
+            ptrs.append(ctypes.c_void_p(t.data_ptr()))
+    if n_rows is None:
+        n_rows, row_len, row_stride = 1, int(e_d.numel()), int(e_d.numel())
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    grid = np.ascontiguousarray(delta_grid, dtype=np.float64)
+    out = np.zeros((len(grid), 5))
+    rc = L.muca_reweight(ptrs[0], ptrs[1], ptrs[2], n_rows, row_len, row_stride, _np_ptr(lnW),
+                         e_min, len(lnW), beta, V, _np_ptr(grid), len(grid), precision,
+                         _np_ptr(out), _stream_ptr(stream))
+    _ck(rc)
+    return out
+
+
+def reweight_context(ctx, g, delta_grid, precision=64, stream=None):
+    """Reweight group g's recorded series with its current lnW."""
+    s = ctx.specs[g]
+    base, n = ctx.timeseries_device(g)
+    W = s["n_walkers"]
+    return reweight(base, base + 4 * W, base + 8 * W, ctx.get_lnW(g), s["e_min"], 1.0 / s["T"],
+                    s["V"], delta_grid, precision, n_rows=n, row_len=W, row_stride=3 * W,
+                    stream=stream)

@@ -1,0 +1,143 @@
+"""GPU reweighting (Eq. 3, Eq. 6) against the CPU oracle.
+
+Tolerances (per observable, every Delta_k): FP64 within 1e-12 and FP32
+within 1e-5, as relative errors against the FP64 oracle with the denominator
+max(|ref_k|, 1e-3 max_k |ref_k|) so that an observable crossing zero (C far
+from the transition) is judged on the scale of its own curve.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_07214_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+TOL = {64: 1e-12, 32: 1e-5}
+NAMES = ["E_J", "E_Delta", "C", "chi", "U4"]
+
+
+def muca():
+    from paper_1502_07214_gb300 import muca as m
+
+    return m
+
+
+def rel_err(got, ref):
+    scale = np.maximum(np.abs(ref), 1e-3 * np.abs(ref).max(axis=0, keepdims=True))
+    scale = np.where(scale == 0, 1.0, scale)
+    return np.abs(got - ref) / scale
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32).ravel()).cuda()
+
+
+def series(L, n_walkers, n_samples, seed, T=1.4182):
+    ej, ed, m, lnW, dt = wl.synthetic_series(L=L, T=T, n_walkers=n_walkers, n_samples=n_samples,
+                                             seed=seed)
+    return ej, ed, m, lnW, dt
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("L,nw,ns", [(8, 256, 400), (12, 333, 101), (16, 64, 1000)])
+def test_reweight_matches_oracle(precision, L, nw, ns):
+    T = 1.4182
+    beta = 1 / T
+    ej, ed, m, lnW, dt = series(L, nw, ns, seed=L)
+    grid = wl.delta_grid(dt, 0.05, 97)
+    ref = oracle.reweight(ej, ed, m, lnW, 0, beta, L ** 3, grid)
+    got = muca().reweight(dev(ej), dev(ed), dev(m), lnW, 0, beta, L ** 3, grid, precision)
+    err = rel_err(got, ref)
+    worst = dict(zip(NAMES, err.max(axis=0)))
+    assert (err <= TOL[precision]).all(), worst
+
+
+def test_fp64_against_binary128():
+    L, T = 10, 1.4182
+    ej, ed, m, lnW, dt = series(L, 128, 300, seed=3)
+    grid = wl.delta_grid(dt, 0.05, 33)
+    q = oracle.reweight_q(ej, ed, m, lnW, 0, 1 / T, L ** 3, grid)
+    got = muca().reweight(dev(ej), dev(ed), dev(m), lnW, 0, 1 / T, L ** 3, grid, 64)
+    assert (rel_err(got, q) <= 1e-12).all()
+
+
+def test_strided_layout_of_the_context_series():
+    """[sample][field][walker] rows with a stride, as the context records them."""
+    L, T, W, S = 6, 1.0, 45, 70
+    ej, ed, m, lnW, dt = series(L, W, S, seed=9, T=T)
+    packed = np.stack([ej, ed, m], axis=1).astype(np.int32)  # [S][3][W]
+    buf = torch.from_numpy(packed.ravel()).cuda()
+    base = buf.data_ptr()
+    grid = wl.delta_grid(dt, 0.05, 16)
+    got = muca().reweight(base, base + 4 * W, base + 8 * W, lnW, 0, 1 / T, L ** 3, grid, 64,
+                          n_rows=S, row_len=W, row_stride=3 * W)
+    ref = oracle.reweight(ej, ed, m, lnW, 0, 1 / T, L ** 3, grid)
+    assert (rel_err(got, ref) <= 1e-12).all()
+
+
+def test_context_series_end_to_end():
+    """A recorded run reweighted on the GPU equals the oracle's reweighting of
+    the oracle's own run (the two series are bit-identical)."""
+    L, T, W, seed = 4, 1.4182, 64, 13
+    c = muca().Context([{"L": L, "T": T, "n_walkers": W}], seed=seed)
+    for _ in range(4):
+        c.sweep_iter(50)
+        c.merge_update()
+    c.reserve_timeseries(200)
+    c.sweep_iter(200, record=True)
+    grid = np.linspace(2.0, 3.5, 40)
+    got64 = muca().reweight_context(c, 0, grid, 64)
+    got32 = muca().reweight_context(c, 0, grid, 32)
+    c.close()
+    ref = oracle.muca_run(L, T, W, seed, 4, 50, n_meas=200)
+    ts = ref["ts"]
+    want = oracle.reweight(ts[..., 0], ts[..., 1], ts[..., 2], ref["lnW"], 0, 1 / T, L ** 3, grid)
+    assert (rel_err(got64, want) <= 1e-12).all()
+    assert (rel_err(got32, want) <= 1e-5).all()
+
+
+def test_degenerate_inputs():
+    # one sample; all samples in one E_Delta bin (C = 0, chi from |m| only)
+    V, beta = 64, 0.5
+    lnW = np.zeros(V + 1)
+    got = muca().reweight(dev([-10]), dev([20]), dev([-4]), lnW, 0, beta, V, [1.0, 2.0], 64)
+    assert np.allclose(got[:, 0], -10) and np.allclose(got[:, 1], 20)
+    assert np.allclose(got[:, 2], 0) and np.allclose(got[:, 3], 0)
+    ed = np.full(500, 33)
+    ej = np.arange(500) - 250
+    m = (np.arange(500) % 7) - 3
+    for p in (64, 32):
+        got = muca().reweight(dev(ej), dev(ed), dev(m), lnW, 0, beta, V, [0.5, 3.0], p)
+        ref = oracle.reweight(ej, ed, m, lnW, 0, beta, V, [0.5, 3.0])
+        assert np.allclose(got[:, 2], 0, atol=1e-9)
+        assert np.allclose(got[:, [0, 1, 3, 4]], ref[:, [0, 1, 3, 4]], rtol=TOL[p], atol=1e-12)
+    # an E_Delta outside [e_min, e_min + n_e) is an error, not a fault
+    with pytest.raises(muca().MucaError) as e:
+        muca().reweight(dev([0, 1]), dev([5, 70]), dev([0, 0]), lnW, 0, beta, V, [1.0], 64)
+    assert e.value.code == muca().ERR_WINDOW
+    with pytest.raises(muca().MucaError):
+        muca().reweight(dev([0]), dev([5]), dev([0]), lnW, 0, beta, V, [1.0], 16)
+
+
+def test_full_size_reweight_sampled_grid_points():
+    """4096 walkers x 10^4 samples of an L=32 series, 4096 grid points: the
+    oracle recomputes a sample of grid points."""
+    s = wl.REWEIGHT
+    ej, ed, m, lnW, dt = wl.synthetic_series()
+    beta = 1 / s["T"]
+    V = s["L"] ** 3
+    grid = wl.delta_grid(dt)
+    e_j, e_d, mm = dev(ej), dev(ed), dev(m)
+    got64 = muca().reweight(e_j, e_d, mm, lnW, 0, beta, V, grid, 64)
+    got32 = muca().reweight(e_j, e_d, mm, lnW, 0, beta, V, grid, 32)
+    ks = np.array([0, 1, 1500, 2047, 2048, 3333, 4095])
+    ref = oracle.reweight(ej, ed, m, lnW, 0, beta, V, grid[ks])
+    full_scale = np.abs(got64).max(axis=0, keepdims=True)
+    for got, p in ((got64, 64), (got32, 32)):
+        sc = np.maximum(np.abs(ref), 1e-3 * full_scale)
+        err = np.abs(got[ks] - ref) / sc
+        assert (err <= TOL[p]).all(), (p, dict(zip(NAMES, err.max(axis=0))))
+    assert np.isfinite(got64).all() and np.isfinite(got32).all()
