@@ -46,6 +46,7 @@
  *      iterations first, then measurement sweeps).
  *   R8 chi = beta V (<m^2> - <|m|>^2) and U4 = 1 - <m^4>/(3 <m^2>^2), m = M/V
  *      (the paper names chi without defining it and does not use U4).
+ *   R9, R10 (rounding of the reweighting) are stated where they are used.
  */
 #include "muca_oracle.h"
 
@@ -408,9 +409,14 @@ done:
 
 /* ------------------------------------------------------------------------ */
 /* Time-series reweighting (Eq. 3) and the observables (Eq. 6, reading R8).   */
-/* For every Delta_k the exponent a_s = -beta Delta_k E_Delta,s - lnW(E_Delta,s) */
-/* is shifted by its maximum over the samples before exponentiation (the     */
-/* weights span hundreds of decades) and all sums are compensated (Neumaier). */
+/* The weight of sample s at Delta_k is exp(a_s) with                         */
+/* a_s = -beta Delta_k E_Delta,s - lnW(E_Delta,s); Eq. 3 only needs it up to a */
+/* common factor, so it is normalised by the largest one, exp(a_s - a_max).   */
+/* Reading R9: a_s - a_max is evaluated as                                    */
+/*   -beta Delta_k (E_s - E*) - (lnW(E_s) - lnW(E*)),  E* the sample of a_max, */
+/* the same number without subtracting two O(beta Delta V) terms (they carry */
+/* ~1e-11 absolute rounding at V = 32768).  All sums are compensated         */
+/* (Neumaier).                                                                */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     double s, c;
@@ -443,33 +449,49 @@ static void reweight_one(const rw_job *j, int k)
 {
     double c = j->beta * j->grid[k];
     double amax = -INFINITY;
+    int32_t estar = j->e_d[0];
     for (int64_t s = 0; s < j->n; ++s) {
         double a = -(c * (double)j->e_d[s]) - j->lnW[j->e_d[s] - j->e_min];
-        if (a > amax) amax = a;
+        if (a > amax) {
+            amax = a;
+            estar = j->e_d[s];
+        }
     }
-    nsum z = {0, 0}, sj = {0, 0}, sd = {0, 0}, sjd = {0, 0}, sm1 = {0, 0}, sm2 = {0, 0},
-         sm4 = {0, 0};
+    double lstar = j->lnW[estar - j->e_min];
+    nsum z = {0, 0}, sj = {0, 0}, sd = {0, 0}, sm1 = {0, 0}, sm2 = {0, 0}, sm4 = {0, 0};
     for (int64_t s = 0; s < j->n; ++s) {
-        double a = -(c * (double)j->e_d[s]) - j->lnW[j->e_d[s] - j->e_min];
-        double w = exp(a - amax);
+        double a = -(c * (double)(j->e_d[s] - estar)) - (j->lnW[j->e_d[s] - j->e_min] - lstar);
+        double w = exp(a);
         double ej = (double)j->e_j[s], ed = (double)j->e_d[s];
         double mm = (double)j->m[s] / (double)j->V;
         nsum_add(&z, w);
         nsum_add(&sj, w * ej);
         nsum_add(&sd, w * ed);
-        nsum_add(&sjd, w * (ej * ed));
         nsum_add(&sm1, w * fabs(mm));
         nsum_add(&sm2, w * (mm * mm));
         nsum_add(&sm4, w * ((mm * mm) * (mm * mm)));
     }
     double Z = nsum_get(&z);
-    double mj = nsum_get(&sj) / Z, md = nsum_get(&sd) / Z, mjd = nsum_get(&sjd) / Z;
+    double mj = nsum_get(&sj) / Z, md = nsum_get(&sd) / Z;
     double m1 = nsum_get(&sm1) / Z, m2 = nsum_get(&sm2) / Z, m4 = nsum_get(&sm4) / Z;
+    /* reading R10: the covariance of Eq. 6 and the variance in chi are summed
+     * in their centred forms <(E_J - <E_J>)(E_Delta - <E_Delta>)> and
+     * <(|m| - <|m|>)^2> (equal in exact arithmetic; the uncentred forms cancel
+     * about four digits at L = 32) */
+    nsum sc = {0, 0}, sx = {0, 0};
+    for (int64_t s = 0; s < j->n; ++s) {
+        double a = -(c * (double)(j->e_d[s] - estar)) - (j->lnW[j->e_d[s] - j->e_min] - lstar);
+        double w = exp(a);
+        double dj = (double)j->e_j[s] - mj, dd = (double)j->e_d[s] - md;
+        double dm = fabs((double)j->m[s] / (double)j->V) - m1;
+        nsum_add(&sc, w * (dj * dd));
+        nsum_add(&sx, w * (dm * dm));
+    }
     double *o = j->out + 5 * (int64_t)k;
     o[0] = mj;
     o[1] = md;
-    o[2] = -j->beta * (mjd - mj * md);
-    o[3] = j->beta * (double)j->V * (m2 - m1 * m1);
+    o[2] = -j->beta * (nsum_get(&sc) / Z);
+    o[3] = j->beta * (double)j->V * (nsum_get(&sx) / Z);
     o[4] = 1.0 - m4 / (3.0 * m2 * m2);
 }
 
@@ -521,8 +543,8 @@ int or_reweight(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_
 }
 
 /* ------------------------------------------------------------------------ */
-/* binary128 variant: the same definition evaluated with 113-bit mantissas,  */
-/* used to measure the error of the FP64 oracle itself.                       */
+/* binary128 variant: Eq. 3 and Eq. 6 evaluated literally (uncentred moments) */
+/* with 113-bit mantissas; it pins the FP64 oracle's own rounding.            */
 /* ------------------------------------------------------------------------ */
 #if defined(__aarch64__) || defined(__powerpc64__)
 typedef long double qreal;
@@ -539,16 +561,21 @@ static void reweight_one_q(const rw_job *j, int k)
 {
     qreal c = (qreal)j->beta * (qreal)j->grid[k];
     qreal amax = 0;
+    int32_t estar = j->e_d[0];
     int first = 1;
     for (int64_t s = 0; s < j->n; ++s) {
         qreal a = -(c * (qreal)j->e_d[s]) - (qreal)j->lnW[j->e_d[s] - j->e_min];
-        if (first || a > amax) amax = a;
+        if (first || a > amax) {
+            amax = a;
+            estar = j->e_d[s];
+        }
         first = 0;
     }
+    qreal lstar = (qreal)j->lnW[estar - j->e_min];
     qreal z = 0, sj = 0, sd = 0, sjd = 0, sm1 = 0, sm2 = 0, sm4 = 0;
     for (int64_t s = 0; s < j->n; ++s) {
-        qreal a = -(c * (qreal)j->e_d[s]) - (qreal)j->lnW[j->e_d[s] - j->e_min];
-        qreal w = QEXP(a - amax);
+        qreal a = -(c * (qreal)(j->e_d[s] - estar)) - ((qreal)j->lnW[j->e_d[s] - j->e_min] - lstar);
+        qreal w = QEXP(a);
         qreal ej = (qreal)j->e_j[s], ed = (qreal)j->e_d[s];
         qreal mm = (qreal)j->m[s] / (qreal)j->V;
         z += w;

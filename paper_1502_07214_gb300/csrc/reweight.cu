@@ -210,10 +210,45 @@ __device__ __forceinline__ void block_sum(KSum<F> (&a)[K], F (&out)[K], F *sh)
 }
 
 // ------------------------------------------------------------ FP64 stage B
-// Exponent exactly as written in Eq. 3: a = -(c E) - lnW(E), c = beta Delta_k.
+// Exponent of Eq. 3: a = -(c E) - lnW(E), c = beta Delta_k.  It is used to
+// find the bin E* of the largest weight; the normalised exponents are then
+// formed as -c (E - E*) - (lnW(E) - lnW(E*)) so that two O(beta Delta V) numbers
+// are never subtracted.
 __device__ __forceinline__ double expo64(double c, int E, double lw)
 {
     return __dsub_rn(-__dmul_rn(c, (double)E), lw);
+}
+
+__device__ __forceinline__ double rel64(double c, int dE, double lw, double lstar)
+{
+    return __dsub_rn(-__dmul_rn(c, (double)dE), __dsub_rn(lw, lstar));
+}
+
+// Block-wide argmax of (value, bin); ties go to the smaller bin.
+__device__ __forceinline__ void block_argmax(double &v, int &e, double *shv, int *she)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        const int e2 = __shfl_xor_sync(0xFFFFFFFFu, e, o);
+        if (v2 > v || (v2 == v && e2 < e)) {
+            v = v2;
+            e = e2;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        shv[wid] = v;
+        she[wid] = e;
+    }
+    __syncthreads();
+    v = shv[0];
+    e = she[0];
+    for (int i = 1; i < nw; ++i)
+        if (shv[i] > v || (shv[i] == v && she[i] < e)) {
+            v = shv[i];
+            e = she[i];
+        }
 }
 
 __global__ void __launch_bounds__(256)
@@ -221,19 +256,28 @@ grid_kernel_f64(BinStats<double> s, int nE, int e_min, double beta, int V,
                 const double *__restrict__ cgrid, double *__restrict__ out)
 {
     __shared__ double sh[64];
+    __shared__ int she[32];
     const int k = blockIdx.x;
     const double c = cgrid[k];
     double amax = -INFINITY;
+    int estar = 0x7FFFFFFF;
     for (int e = threadIdx.x; e < nE; e += blockDim.x)
-        if (s.n[e] > 0) amax = fmax(amax, expo64(c, e_min + e, s.lw[e]));
-    amax = block_max(amax, sh);
+        if (s.n[e] > 0) {
+            const double a = expo64(c, e_min + e, s.lw[e]);
+            if (a > amax) {
+                amax = a;
+                estar = e;
+            }
+        }
+    block_argmax(amax, estar, sh, she);
+    const double lstar = s.lw[estar];
     KSum<double> acc[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) acc[i].init();
     for (int e = threadIdx.x; e < nE; e += blockDim.x) {
         const double n = s.n[e];
         if (n <= 0) continue;
-        const double d = expo64(c, e_min + e, s.lw[e]) - amax;
+        const double d = rel64(c, e - estar, s.lw[e], lstar);
         if (d < -800.0) continue;
         const double w = exp(d);
         const double wn = w * n;
@@ -253,7 +297,7 @@ grid_kernel_f64(BinStats<double> s, int nE, int e_min, double beta, int V,
     for (int e = threadIdx.x; e < nE; e += blockDim.x) {
         const double n = s.n[e];
         if (n <= 0) continue;
-        const double d = expo64(c, e_min + e, s.lw[e]) - amax;
+        const double d = rel64(c, e - estar, s.lw[e], lstar);
         if (d < -800.0) continue;
         const double w = exp(d);
         const double wn = w * n;

@@ -25,21 +25,19 @@ thread_local std::string g_last_error = "no error";
 
 struct Group {
     muca_group spec{};
-    int L = 0, V = 0, W = 0, Wpad = 0, e_min = 0, e_max = 0, nE = 0;
+    int L = 0, V = 0, W = 0, Wpad = 0, Lw = 0, e_min = 0, e_max = 0, nE = 0;
     double T = 0, beta = 0;
     uint32_t walker0 = 0;
     // device
-    int8_t *spins = nullptr;
+    uint32_t *spins = nullptr;  // [L * L][Lw][Wpad] packed words
     int32_t *tal = nullptr;
     unsigned long long *hist = nullptr;
-    uint32_t *thrE = nullptr;
-    uint32_t *thr0 = nullptr;
+    uint32_t *thr = nullptr;    // [nE][kRow]
     int32_t *ts = nullptr;
     // host
     std::vector<double> lnW;
     std::vector<uint32_t> injected;  // logical table given by muca_set_table (empty if none)
-    uint32_t *h_thrE = nullptr;      // pinned packed table [nE][kRow]
-    uint32_t *h_thr0 = nullptr;      // pinned [kThr0]
+    uint32_t *h_thr = nullptr;       // pinned packed table [nE][kRow]
     unsigned long long *h_hist = nullptr;  // pinned [nE]
     // every walker's E_Delta lies in [e_min, e_max] (required before sweeping)
     bool in_window = false;
@@ -134,49 +132,42 @@ void parallel_rows(int n, F f)
     for (auto &x : th) x.join();
 }
 
-// Packed table of group g from its lnW into the pinned host buffers.
+// Packed table of group g from its lnW into the pinned host buffer.
 void build_packed(Group &g)
 {
-    uint32_t *T = g.h_thrE;
+    uint32_t *T = g.h_thr;
     parallel_rows(g.nE, [&g, T](int b, int e_end) {
         for (int e = b; e < e_end; ++e) {
             uint32_t *row = T + (size_t)e * kRow;
             for (int dej = -6; dej <= 6; ++dej) {
                 row[dej + 6] = thr_entry(g, e, -1, dej);
-                row[kRowPlus + dej + 6] = thr_entry(g, e, +1, dej);
+                row[2 * kBlk + dej + 6] = thr_entry(g, e, +1, dej);
             }
-            for (int c = 2 * kRowPlus; c < kRow; ++c) row[c] = 0u;
+            for (int k = 0; k < kBlk; ++k) row[kBlk + k] = thr_entry(g, e, 0, 2 * k - 12);
+            for (int c = 3 * kBlk; c < kRow; ++c) row[c] = 0u;
         }
     });
-    for (int k = 0; k < kThr0; ++k) g.h_thr0[k] = k < 13 ? thr_entry(g, 0, 0, 2 * k - 12) : 0u;
 }
 
 // Pack a logical [nE][3][25] table.
-int pack_logical(muca_ctx *ctx, Group &g, const uint32_t *lg)
+void pack_logical(Group &g, const uint32_t *lg)
 {
     for (int e = 0; e < g.nE; ++e) {
         const uint32_t *r = lg + (size_t)e * 3 * MUCA_NK;
-        uint32_t *row = g.h_thrE + (size_t)e * kRow;
+        uint32_t *row = g.h_thr + (size_t)e * kRow;
         for (int dej = -6; dej <= 6; ++dej) {
             row[dej + 6] = r[0 * MUCA_NK + dej + 12];
-            row[kRowPlus + dej + 6] = r[2 * MUCA_NK + dej + 12];
+            row[2 * kBlk + dej + 6] = r[2 * MUCA_NK + dej + 12];
         }
-        for (int c = 2 * kRowPlus; c < kRow; ++c) row[c] = 0u;
-        for (int k = 0; k < 13; ++k)
-            if (r[1 * MUCA_NK + 2 * k] != lg[1 * MUCA_NK + 2 * k])
-                return fail(ctx, MUCA_ERR_INVALID_ARG,
-                            "set_table: d = 0 entries must not depend on E_Delta (row %d)", e);
+        for (int k = 0; k < kBlk; ++k) row[kBlk + k] = r[1 * MUCA_NK + 2 * k];
+        for (int c = 3 * kBlk; c < kRow; ++c) row[c] = 0u;
     }
-    for (int k = 0; k < kThr0; ++k) g.h_thr0[k] = k < 13 ? lg[1 * MUCA_NK + 2 * k] : 0u;
-    return MUCA_OK;
 }
 
 int upload_table(muca_ctx *ctx, Group &g)
 {
-    CK(cudaMemcpyAsync(g.thrE, g.h_thrE, (size_t)g.nE * kRow * sizeof(uint32_t),
+    CK(cudaMemcpyAsync(g.thr, g.h_thr, (size_t)g.nE * kRow * sizeof(uint32_t),
                        cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(g.thr0, g.h_thr0, kThr0 * sizeof(uint32_t), cudaMemcpyHostToDevice,
-                       ctx->stream));
     return MUCA_OK;
 }
 
@@ -194,14 +185,14 @@ GroupDev dev_of(const Group &g)
     d.V = g.V;
     d.W = g.W;
     d.Wpad = g.Wpad;
+    d.Lw = g.Lw;
     d.e_min = g.e_min;
     d.nE = g.nE;
     d.walker0 = g.walker0;
     d.spins = g.spins;
     d.tal = g.tal;
     d.hist = g.hist;
-    d.thrE = g.thrE;
-    d.thr0 = g.thr0;
+    d.thr = g.thr;
     d.ts = g.ts;
     return d;
 }
@@ -225,7 +216,7 @@ int build_blocks(muca_ctx *ctx)
         const Group &g = ctx->g[gi];
         if (g.residency == MUCA_RES_SMEM) {
             G = std::max(G, g.wpb);
-            smem = std::max(smem, smem_bytes_for(g.V, g.wpb));
+            smem = std::max(smem, smem_bytes_for(g.L, g.wpb));
         } else {
             wpb_g = std::max(wpb_g, g.wpb);
         }
@@ -323,13 +314,14 @@ std::vector<Cand> candidates(const Group &g, int residency, int wpb, int smem_ma
     const bool want_g = residency == MUCA_RES_AUTO || residency == MUCA_RES_GLOBAL;
     const bool want_s = residency == MUCA_RES_AUTO || residency == MUCA_RES_SMEM;
     if (want_g) {
-        if (wpb > 0) c.push_back({MUCA_RES_GLOBAL, wpb});
+        if (wpb > 0 && wpb % 32 == 0 && wpb <= 128) c.push_back({MUCA_RES_GLOBAL, wpb});
         else
             for (int w : {32, 64, 128})
                 if (w <= std::max(32, g.Wpad)) c.push_back({MUCA_RES_GLOBAL, w});
     }
     if (want_s) {
-        const int fit = (int)std::min<int64_t>(32, (int64_t)(smem_max - 1024) / g.V);
+        const int fit =
+            (int)std::min<int64_t>(32, (int64_t)(smem_max - 1024) / (int64_t)lattice_bytes(g.L));
         if (wpb > 0 && wpb <= fit) c.push_back({MUCA_RES_SMEM, wpb});
         else if (wpb <= 0)
             for (int G : {32, 16, 8})
@@ -365,9 +357,9 @@ static int tune_group(muca_ctx *ctx, size_t gi, int residency, int wpb)
         }
     }
     // scratch copy of the state
-    const size_t sb = (size_t)g.V * g.Wpad, tb = (size_t)3 * g.Wpad * sizeof(int32_t),
+    const size_t sb = (size_t)g.L * g.L * g.Lw * g.Wpad * sizeof(uint32_t), tb = (size_t)3 * g.Wpad * sizeof(int32_t),
                  hb = (size_t)g.nE * sizeof(unsigned long long);
-    int8_t *s0 = nullptr;
+    uint32_t *s0 = nullptr;
     int32_t *t0 = nullptr;
     unsigned long long *h0 = nullptr;
     CK(cudaMalloc(&s0, sb));
@@ -435,18 +427,16 @@ static void free_group(Group &g)
     cudaFree(g.spins);
     cudaFree(g.tal);
     cudaFree(g.hist);
-    cudaFree(g.thrE);
-    cudaFree(g.thr0);
+    cudaFree(g.thr);
     cudaFree(g.ts);
-    cudaFreeHost(g.h_thrE);
-    cudaFreeHost(g.h_thr0);
+    cudaFreeHost(g.h_thr);
     cudaFreeHost(g.h_hist);
     g.spins = nullptr;
     g.tal = nullptr;
     g.hist = nullptr;
-    g.thrE = g.thr0 = nullptr;
+    g.thr = nullptr;
     g.ts = nullptr;
-    g.h_thrE = g.h_thr0 = nullptr;
+    g.h_thr = nullptr;
     g.h_hist = nullptr;
 }
 
@@ -486,7 +476,7 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: need >= 1 group and options");
     if (opt->residency < MUCA_RES_AUTO || opt->residency > MUCA_RES_SMEM)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad residency %d", opt->residency);
-    if (opt->walkers_per_block < 0 || opt->walkers_per_block > 1024)
+    if (opt->walkers_per_block < 0 || opt->walkers_per_block > 128)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad walkers_per_block %d",
                     opt->walkers_per_block);
     int64_t total_w = 0;
@@ -537,6 +527,7 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
             g.V = g.L * g.L * g.L;
             g.W = groups[i].n_walkers;
             g.Wpad = ((g.W + 31) / 32) * 32;
+            g.Lw = (g.L + 3) / 4;
             g.e_min = groups[i].e_min;
             g.e_max = groups[i].e_max < 0 ? g.V : groups[i].e_max;
             g.spec.e_max = g.e_max;
@@ -546,16 +537,15 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
             g.walker0 = w0;
             w0 += (uint32_t)g.W;
             g.lnW.assign(g.nE, 0.0);
-            CKI(cudaMalloc(&g.spins, (size_t)g.V * g.Wpad));
-            CKI(cudaMemsetAsync(g.spins, 0, (size_t)g.V * g.Wpad, ctx->stream));
+            const size_t sbytes = (size_t)g.L * g.L * g.Lw * g.Wpad * sizeof(uint32_t);
+            CKI(cudaMalloc(&g.spins, sbytes));
+            CKI(cudaMemsetAsync(g.spins, 0, sbytes, ctx->stream));
             CKI(cudaMalloc(&g.tal, (size_t)3 * g.Wpad * sizeof(int32_t)));
             CKI(cudaMemsetAsync(g.tal, 0, (size_t)3 * g.Wpad * sizeof(int32_t), ctx->stream));
             CKI(cudaMalloc(&g.hist, (size_t)g.nE * sizeof(unsigned long long)));
             CKI(cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long), ctx->stream));
-            CKI(cudaMalloc(&g.thrE, (size_t)g.nE * kRow * sizeof(uint32_t)));
-            CKI(cudaMalloc(&g.thr0, kThr0 * sizeof(uint32_t)));
-            CKI(cudaMallocHost(&g.h_thrE, (size_t)g.nE * kRow * sizeof(uint32_t)));
-            CKI(cudaMallocHost(&g.h_thr0, kThr0 * sizeof(uint32_t)));
+            CKI(cudaMalloc(&g.thr, (size_t)g.nE * kRow * sizeof(uint32_t)));
+            CKI(cudaMallocHost(&g.h_thr, (size_t)g.nE * kRow * sizeof(uint32_t)));
             CKI(cudaMallocHost(&g.h_hist, (size_t)g.nE * sizeof(unsigned long long)));
             CKI(launch_init_spins(dev_of(g), ctx->seed, ctx->stream));
             CKI(launch_energies(dev_of(g), 0, ctx->d_err, ctx->stream));
@@ -681,9 +671,7 @@ extern "C" int muca_run_graph(muca_ctx *ctx, int n_iters, int sweeps_per_iter)
             if (cudaMemcpyAsync(g.h_hist, g.hist, (size_t)g.nE * sizeof(unsigned long long),
                                 cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
                 cudaLaunchHostFunc(ctx->stream, host_update, &g) != cudaSuccess ||
-                cudaMemcpyAsync(g.thrE, g.h_thrE, (size_t)g.nE * kRow * sizeof(uint32_t),
-                                cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
-                cudaMemcpyAsync(g.thr0, g.h_thr0, kThr0 * sizeof(uint32_t),
+                cudaMemcpyAsync(g.thr, g.h_thr, (size_t)g.nE * kRow * sizeof(uint32_t),
                                 cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
                 cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long),
                                 ctx->stream) != cudaSuccess)
@@ -813,8 +801,7 @@ int muca_set_table(muca_ctx *ctx, int group, const uint32_t *in)
     if (!in) return fail(ctx, MUCA_ERR_INVALID_ARG, "in is NULL");
     Group &g = ctx->g[group];
     CK(cudaStreamSynchronize(ctx->stream));
-    rc = pack_logical(ctx, g, in);
-    if (rc) return rc;
+    pack_logical(g, in);
     g.injected.assign(in, in + (size_t)g.nE * 3 * MUCA_NK);
     rc = upload_table(ctx, g);
     if (rc) return rc;
@@ -852,12 +839,18 @@ int muca_get_state(muca_ctx *ctx, int group, int8_t *spins, int32_t *tallies)
     if (rc) return rc;
     Group &g = ctx->g[group];
     if (spins) {
-        std::vector<int8_t> dev((size_t)g.V * g.Wpad);
-        CK(cudaMemcpyAsync(dev.data(), g.spins, dev.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        const size_t nwords = (size_t)g.L * g.L * g.Lw;
+        std::vector<uint32_t> dev(nwords * g.Wpad);
+        CK(cudaMemcpyAsync(dev.data(), g.spins, dev.size() * sizeof(uint32_t),
+                           cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         for (int w = 0; w < g.W; ++w)
-            for (int i = 0; i < g.V; ++i)
-                spins[(size_t)w * g.V + i] = dev[(size_t)i * g.Wpad + w];
+            for (int row = 0; row < g.L * g.L; ++row)
+                for (int x = 0; x < g.L; ++x) {
+                    const uint32_t word = dev[((size_t)row * g.Lw + (x >> 2)) * g.Wpad + w];
+                    spins[(size_t)w * g.V + (size_t)row * g.L + x] =
+                        (int8_t)(uint8_t)(word >> (8 * (x & 3)));
+                }
     }
     if (tallies) {
         std::vector<int32_t> t((size_t)3 * g.Wpad);
@@ -876,21 +869,26 @@ int muca_set_state(muca_ctx *ctx, int group, const int8_t *spins)
     if (rc) return rc;
     if (!spins) return fail(ctx, MUCA_ERR_INVALID_ARG, "spins is NULL");
     Group &g = ctx->g[group];
-    std::vector<int8_t> dev((size_t)g.V * g.Wpad, 0);
+    const size_t nwords = (size_t)g.L * g.L * g.Lw;
+    std::vector<uint32_t> dev(nwords * g.Wpad, 0u);
     for (int w = 0; w < g.W; ++w)
-        for (int i = 0; i < g.V; ++i) {
-            const int8_t s = spins[(size_t)w * g.V + i];
-            if (s < -1 || s > 1)
-                return fail(ctx, MUCA_ERR_INVALID_ARG, "walker %d site %d: spin %d", w, i, s);
-            dev[(size_t)i * g.Wpad + w] = s;
-        }
+        for (int row = 0; row < g.L * g.L; ++row)
+            for (int x = 0; x < g.L; ++x) {
+                const int8_t s = spins[(size_t)w * g.V + (size_t)row * g.L + x];
+                if (s < -1 || s > 1)
+                    return fail(ctx, MUCA_ERR_INVALID_ARG, "walker %d site %d: spin %d", w,
+                                row * g.L + x, s);
+                dev[((size_t)row * g.Lw + (x >> 2)) * g.Wpad + w] |=
+                    (uint32_t)(uint8_t)s << (8 * (x & 3));
+            }
     std::vector<int32_t> old((size_t)3 * g.Wpad);
+    std::vector<uint32_t> old_spins(dev.size());
     CK(cudaMemcpyAsync(old.data(), g.tal, old.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
                        ctx->stream));
-    std::vector<int8_t> old_spins(dev.size());
-    CK(cudaMemcpyAsync(old_spins.data(), g.spins, dev.size(), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(old_spins.data(), g.spins, dev.size() * sizeof(uint32_t),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(g.spins, dev.data(), dev.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
                        ctx->stream));
-    CK(cudaMemcpyAsync(g.spins, dev.data(), dev.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(launch_energies(dev_of(g), 0, ctx->d_err, ctx->stream));
     std::vector<int32_t> t((size_t)3 * g.Wpad);
     CK(cudaMemcpyAsync(t.data(), g.tal, t.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
@@ -900,7 +898,7 @@ int muca_set_state(muca_ctx *ctx, int group, const int8_t *spins)
         const int ed = t[(size_t)g.Wpad + w];
         if (ed < g.e_min || ed > g.e_max) {
             // put the previous state back
-            CK(cudaMemcpyAsync(g.spins, old_spins.data(), old_spins.size(),
+            CK(cudaMemcpyAsync(g.spins, old_spins.data(), old_spins.size() * sizeof(uint32_t),
                                cudaMemcpyHostToDevice, ctx->stream));
             CK(cudaMemcpyAsync(g.tal, old.data(), old.size() * sizeof(int32_t),
                                cudaMemcpyHostToDevice, ctx->stream));
@@ -949,17 +947,17 @@ int muca_checkpoint(muca_ctx *ctx, const char *path)
         if (!ok) break;
         std::vector<unsigned long long> h(g.nE);
         std::vector<int32_t> t((size_t)3 * g.Wpad);
-        std::vector<int8_t> s((size_t)g.V * g.Wpad);
+        std::vector<uint32_t> s((size_t)g.L * g.L * g.Lw * g.Wpad);
         if (cudaMemcpy(h.data(), g.hist, h.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(t.data(), g.tal, t.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(s.data(), g.spins, s.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaMemcpy(s.data(), g.spins, s.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
             std::fclose(f);
             return fail(ctx, MUCA_ERR_CUDA, "checkpoint: device read failed");
         }
         ok = ok && std::fwrite(g.lnW.data(), 8, g.nE, f) == (size_t)g.nE;
         ok = ok && std::fwrite(h.data(), 8, h.size(), f) == h.size();
         ok = ok && std::fwrite(t.data(), 4, t.size(), f) == t.size();
-        ok = ok && std::fwrite(s.data(), 1, s.size(), f) == s.size();
+        ok = ok && std::fwrite(s.data(), 4, s.size(), f) == s.size();
     }
     ok = (std::fclose(f) == 0) && ok;
     if (!ok) return fail(ctx, MUCA_ERR_IO, "checkpoint: write to %s failed", path);
@@ -995,11 +993,11 @@ int muca_restore(muca_ctx *ctx, const char *path)
         std::vector<double> lnW(g.nE);
         std::vector<unsigned long long> h(g.nE);
         std::vector<int32_t> t((size_t)3 * g.Wpad);
-        std::vector<int8_t> s((size_t)g.V * g.Wpad);
+        std::vector<uint32_t> s((size_t)g.L * g.L * g.Lw * g.Wpad);
         ok = std::fread(lnW.data(), 8, g.nE, f) == (size_t)g.nE &&
              std::fread(h.data(), 8, h.size(), f) == h.size() &&
              std::fread(t.data(), 4, t.size(), f) == t.size() &&
-             std::fread(s.data(), 1, s.size(), f) == s.size();
+             std::fread(s.data(), 4, s.size(), f) == s.size();
         if (!ok) {
             std::fclose(f);
             return fail(ctx, MUCA_ERR_IO, "restore: %s is truncated", path);
@@ -1009,7 +1007,7 @@ int muca_restore(muca_ctx *ctx, const char *path)
         g.in_window = true;
         if (cudaMemcpy(g.hist, h.data(), h.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(g.tal, t.data(), t.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(g.spins, s.data(), s.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaMemcpy(g.spins, s.data(), s.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
             std::fclose(f);
             return fail(ctx, MUCA_ERR_CUDA, "restore: device write failed");
         }

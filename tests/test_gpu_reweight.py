@@ -55,13 +55,17 @@ def test_reweight_matches_oracle(precision, L, nw, ns):
     assert (err <= TOL[precision]).all(), worst
 
 
-def test_fp64_against_binary128():
+def test_against_binary128():
+    """Both precisions against the literal definition in binary128; FP64 within
+    the FP64 oracle's own bound (1e-10, see the oracle pins), FP32 within 1e-5."""
     L, T = 10, 1.4182
     ej, ed, m, lnW, dt = series(L, 128, 300, seed=3)
     grid = wl.delta_grid(dt, 0.05, 33)
     q = oracle.reweight_q(ej, ed, m, lnW, 0, 1 / T, L ** 3, grid)
     got = muca().reweight(dev(ej), dev(ed), dev(m), lnW, 0, 1 / T, L ** 3, grid, 64)
-    assert (rel_err(got, q) <= 1e-12).all()
+    assert (rel_err(got, q) <= 1e-10).all()
+    got = muca().reweight(dev(ej), dev(ed), dev(m), lnW, 0, 1 / T, L ** 3, grid, 32)
+    assert (rel_err(got, q) <= 1e-5).all()
 
 
 def test_strided_layout_of_the_context_series():
