@@ -203,7 +203,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_stream(stream)
     ctx = muca.Context([{"L": L, "T": T, "n_walkers": W}], seed=s["seed"] + 7919 * rank)
     ctx.reserve_timeseries(meas)
-    res, wpb = ctx.get_config(0)
+    res, wpb, lanes = ctx.get_config(0)
     launches_per_sweep_call = 1
     attempts_step = W * V * (sweeps + meas)
 
@@ -304,7 +304,7 @@ def run_ours(args, rank, world, local_rank):
                                    "(graph) + 250 recorded sweeps + FP32 reweight to 4096 Delta",
                        "L": L, "T": T, "walkers": W, "sweeps_per_step": sweeps + meas,
                        "residency": {1: "global", 2: "smem"}.get(res, str(res)),
-                       "walkers_per_block": wpb, "seed": s["seed"],
+                       "walkers_per_block": wpb, "lanes_per_walker": lanes, "seed": s["seed"],
                        "l2": "inputs larger than L2 (lattice 453 MB int8)"},
             "plain": {"value": plain_value, "unit": UNIT, "steps": plain_steps},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": int_peak / 1e12,

@@ -84,8 +84,10 @@ typedef struct {
     uint32_t seed;             /* Philox key word 1 */
     int32_t debug_flags;       /* MUCA_DEBUG_* bits */
     int32_t residency;         /* MUCA_RES_* */
-    int32_t walkers_per_block; /* 0 = automatic; else a multiple of 32 in [32, 1024]
-                                  for global residency */
+    int32_t walkers_per_block; /* 0 = automatic; else 1 .. 128 with walkers_per_block x
+                                  lanes_per_walker a multiple of 32 and <= 128 */
+    int32_t lanes_per_walker;  /* 0 = automatic; else 1, 2, 4 or 8 threads serve one
+                                  walker (they share its random numbers) */
 } muca_options;
 
 /* ---------------------------------------------------------------- lifetime */
@@ -205,8 +207,9 @@ int muca_set_state(muca_ctx *ctx, int group, const int8_t *spins);
 int muca_check_tallies(muca_ctx *ctx);
 
 /* Kernel configuration chosen for group g: residency (MUCA_RES_GLOBAL or
- * MUCA_RES_SMEM) and walkers per block. */
-int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walkers_per_block);
+ * MUCA_RES_SMEM), walkers per block and lanes per walker.  Any may be NULL. */
+int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walkers_per_block,
+                    int32_t *lanes_per_walker);
 
 /* Checkpoint / restore: spins, tallies, lnW, histograms, sweep counters and
  * the seed, to / from a file.  Philox is counter-based, so a restored run

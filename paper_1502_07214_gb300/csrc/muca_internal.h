@@ -7,16 +7,22 @@
 
 namespace muca {
 
-// Packed acceptance table of one group, as the sweep kernel reads it: one
-// row of kRow uint32 per E_Delta in the window (row e <-> E_Delta = e_min + e):
-//   [0 .. 12]   d = -1 (s = +-1 -> 0),   dE_J = -6 .. 6
-//   [13 .. 25]  d =  0 (s = +-1 -> -+1), dE_J = -12, -10, .., 12
-//   [26 .. 38]  d = +1 (s = 0 -> +-1),   dE_J = -6 .. 6
-//   [39]        unused (0)
-// Every proposal of a site therefore reads one entry of the row of the
-// walker's current E_Delta: column 13 (d + 1) + (d == 0 ? (dE_J + 12) / 2 : dE_J + 6).
-constexpr int kRow = 40;
-constexpr int kBlk = 13;
+// Packed acceptance table of one group, as the sweep kernel reads it.  One
+// allocation of table_rows(nE) rows of kRow uint32 (one 128-byte line each):
+//   row 0                 the d = 0 moves (s = +-1 -> -+1), which do not depend on
+//                         E_Delta: column (dE_J + 12) / 2, dE_J = -12, -10, .., 12
+//   rows 1 .. kGuard      zero (guard)
+//   rows kGuard+1 + e     E_Delta = e_min + e, e = 0 .. nE-1:
+//                           columns 0 .. 12        d = -1 (s = +-1 -> 0), dE_J + 6
+//                           columns kPlus .. kPlus+12  d = +1 (s = 0 -> +-1), dE_J + 6
+//   last kGuard rows      zero (guard)
+// The guard rows let the kernel prefetch the rows E_Delta +- 2 without bounds
+// checks; they are never compared against (moves that leave the window read 0
+// from the window's own rows).
+constexpr int kRow = 32;
+constexpr int kPlus = 16;
+constexpr int kGuard = 2;
+inline size_t table_rows(int nE) { return (size_t)nE + 2 * kGuard + 1; }
 
 // Spin layout of a group: int8 spins packed four consecutive sites of a row
 // per 32-bit word, walker-minor: word (row, j) of walker w is at
@@ -32,33 +38,42 @@ struct GroupDev {
     uint32_t *spins;            // [L * L][Lw][Wpad] packed words
     int32_t *tal;               // [3][Wpad]: E_J, E_Delta, M
     unsigned long long *hist;   // [nE]
-    const uint32_t *thr;        // [nE][kRow]
+    const uint32_t *thr0;       // the d = 0 row of the table allocation
+    const uint32_t *thrE;       // the row of E_Delta = e_min in the table allocation
     int32_t *ts;                // [cap][3][W] or nullptr
 };
 
 // A block of the sweep grid: which group, first walker, walkers in the block,
-// and (shared-memory blocks) the walker stride G of the lattice tile.
+// walker slots S of the block (the stride of its staging area and, for
+// shared-memory blocks, of its lattice tile; a multiple of 4 for global
+// blocks), and the number P of lanes that serve one walker (thread t is lane
+// t % P of walker slot t / P; P divides 32).
 struct BlockDesc {
     int group;
     int w0;
     int nw;
-    int G;
+    int S;
+    int P;
 };
 
 // Launch helpers implemented in sweep.cu.  All return a cudaError_t.
 cudaError_t launch_init_spins(const GroupDev &g, uint32_t seed, cudaStream_t st);
 // mode 0: write the recomputed tallies; mode 1: compare and raise *err on mismatch.
 cudaError_t launch_energies(const GroupDev &g, int mode, int *err, cudaStream_t st);
-// One launch sweeping every block of `blocks` (n_blocks of them).  smem_bytes > 0
-// selects the shared-memory-resident kernel (prepare it once with
-// prepare_smem_kernel outside any stream capture).
+// One launch sweeping every block of `blocks` (n_blocks of them) with
+// smem_bytes of dynamic shared memory; smem_kernel selects the
+// shared-memory-resident kernel (prepare it once with prepare_smem_kernel
+// outside any stream capture).
 cudaError_t launch_sweeps(const GroupDev *groups_dev, const BlockDesc *blocks_dev, int n_blocks,
-                          int threads, size_t smem_bytes, uint32_t seed, uint64_t sweep0,
-                          int n_sweeps, int64_t ts_pos, bool record, cudaStream_t st);
+                          int threads, size_t smem_bytes, bool smem_kernel, uint32_t seed,
+                          uint64_t sweep0, int n_sweeps, int64_t ts_pos, bool record,
+                          cudaStream_t st);
 cudaError_t prepare_smem_kernel(size_t smem_bytes);
-// Bytes of one walker's lattice (padded rows) and of a shared-memory tile.
+// Bytes of one walker's lattice (padded rows), of a shared-memory tile, and of
+// the per-row staging area of `slots` walkers.
 size_t lattice_bytes(int L);
 size_t smem_bytes_for(int L, int walkers);
+size_t stage_bytes_for(int slots);
 int max_smem_per_block();
 
 // Last-error text reported by muca_last_error(NULL) (thread-local).

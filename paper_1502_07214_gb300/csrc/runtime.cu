@@ -12,6 +12,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/muca.h"
@@ -32,18 +33,19 @@ struct Group {
     uint32_t *spins = nullptr;  // [L * L][Lw][Wpad] packed words
     int32_t *tal = nullptr;
     unsigned long long *hist = nullptr;
-    uint32_t *thr = nullptr;    // [nE][kRow]
+    uint32_t *thr = nullptr;    // table allocation, table_rows(nE) x kRow
     int32_t *ts = nullptr;
     // host
     std::vector<double> lnW;
     std::vector<uint32_t> injected;  // logical table given by muca_set_table (empty if none)
-    uint32_t *h_thr = nullptr;       // pinned packed table [nE][kRow]
+    uint32_t *h_thr = nullptr;       // pinned copy of the table allocation
     unsigned long long *h_hist = nullptr;  // pinned [nE]
     // every walker's E_Delta lies in [e_min, e_max] (required before sweeping)
     bool in_window = false;
     // kernel configuration
     int residency = MUCA_RES_GLOBAL;
-    int wpb = 32;
+    int wpb = 32;  // walkers per block
+    int P = 1;     // lanes per walker
 };
 
 struct GraphKey {
@@ -59,6 +61,7 @@ struct muca_ctx {
     int debug = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;  // second stream for the shared-memory blocks
+    cudaStream_t cap = nullptr;   // stream the iteration graph is captured on
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint64_t sweep = 0;
     int64_t ts_cap = 0, ts_len = 0;
@@ -67,7 +70,7 @@ struct muca_ctx {
     GroupDev *d_groups = nullptr;
     BlockDesc *d_blocks_g = nullptr, *d_blocks_s = nullptr;
     int n_blocks_g = 0, n_blocks_s = 0, threads_g = 32, threads_s = 32;
-    size_t smem_bytes = 0;
+    size_t smem_g = 0, smem_s = 0;  // dynamic shared memory of the two launches
 };
 
 namespace {
@@ -136,37 +139,47 @@ void parallel_rows(int n, F f)
 void build_packed(Group &g)
 {
     uint32_t *T = g.h_thr;
-    parallel_rows(g.nE, [&g, T](int b, int e_end) {
+    std::memset(T, 0, table_rows(g.nE) * kRow * sizeof(uint32_t));
+    for (int k = 0; k < 13; ++k) T[k] = thr_entry(g, 0, 0, 2 * k - 12);
+    uint32_t *E0 = T + (size_t)(1 + kGuard) * kRow;
+    parallel_rows(g.nE, [&g, E0](int b, int e_end) {
         for (int e = b; e < e_end; ++e) {
-            uint32_t *row = T + (size_t)e * kRow;
+            uint32_t *row = E0 + (size_t)e * kRow;
             for (int dej = -6; dej <= 6; ++dej) {
                 row[dej + 6] = thr_entry(g, e, -1, dej);
-                row[2 * kBlk + dej + 6] = thr_entry(g, e, +1, dej);
+                row[kPlus + dej + 6] = thr_entry(g, e, +1, dej);
             }
-            for (int k = 0; k < kBlk; ++k) row[kBlk + k] = thr_entry(g, e, 0, 2 * k - 12);
-            for (int c = 3 * kBlk; c < kRow; ++c) row[c] = 0u;
         }
     });
 }
 
-// Pack a logical [nE][3][25] table.
-void pack_logical(Group &g, const uint32_t *lg)
+// Pack a logical [nE][3][25] table; its d = 0 entries must not depend on
+// E_Delta (they never do for a table built from weights: lnW[E] - lnW[E] = 0).
+int pack_logical(muca_ctx *ctx, Group &g, const uint32_t *lg)
 {
+    for (int e = 0; e < g.nE; ++e)
+        for (int k = 0; k < 13; ++k)
+            if (lg[((size_t)e * 3 + 1) * MUCA_NK + 2 * k] != lg[1 * MUCA_NK + 2 * k])
+                return fail(ctx, MUCA_ERR_INVALID_ARG,
+                            "set_table: d = 0 entries must not depend on E_Delta (row %d)", e);
+    uint32_t *T = g.h_thr;
+    std::memset(T, 0, table_rows(g.nE) * kRow * sizeof(uint32_t));
+    for (int k = 0; k < 13; ++k) T[k] = lg[1 * MUCA_NK + 2 * k];
+    uint32_t *E0 = T + (size_t)(1 + kGuard) * kRow;
     for (int e = 0; e < g.nE; ++e) {
         const uint32_t *r = lg + (size_t)e * 3 * MUCA_NK;
-        uint32_t *row = g.h_thr + (size_t)e * kRow;
+        uint32_t *row = E0 + (size_t)e * kRow;
         for (int dej = -6; dej <= 6; ++dej) {
             row[dej + 6] = r[0 * MUCA_NK + dej + 12];
-            row[2 * kBlk + dej + 6] = r[2 * MUCA_NK + dej + 12];
+            row[kPlus + dej + 6] = r[2 * MUCA_NK + dej + 12];
         }
-        for (int k = 0; k < kBlk; ++k) row[kBlk + k] = r[1 * MUCA_NK + 2 * k];
-        for (int c = 3 * kBlk; c < kRow; ++c) row[c] = 0u;
     }
+    return MUCA_OK;
 }
 
 int upload_table(muca_ctx *ctx, Group &g)
 {
-    CK(cudaMemcpyAsync(g.thr, g.h_thr, (size_t)g.nE * kRow * sizeof(uint32_t),
+    CK(cudaMemcpyAsync(g.thr, g.h_thr, table_rows(g.nE) * kRow * sizeof(uint32_t),
                        cudaMemcpyHostToDevice, ctx->stream));
     return MUCA_OK;
 }
@@ -192,7 +205,8 @@ GroupDev dev_of(const Group &g)
     d.spins = g.spins;
     d.tal = g.tal;
     d.hist = g.hist;
-    d.thr = g.thr;
+    d.thr0 = g.thr;
+    d.thrE = g.thr ? g.thr + (size_t)(1 + kGuard) * kRow : nullptr;
     d.ts = g.ts;
     return d;
 }
@@ -206,30 +220,35 @@ int upload_groups(muca_ctx *ctx)
 }
 
 // Block lists of the global-residency and shared-memory-resident launches.
-// A shared-memory block of group g holds wpb_g lattices as a [V_g][wpb_g] tile.
+// A block of group g serves wpb_g walkers with P_g lanes each; a
+// shared-memory block also holds their lattices as a [L*L][Lw][wpb_g] tile.
+// Every block of one launch has the launch's thread count (the largest
+// wpb * P of its groups; surplus threads idle).
 int build_blocks(muca_ctx *ctx)
 {
     std::vector<BlockDesc> bg, bs;
-    int wpb_g = 0, G = 0;
-    size_t smem = 0;
+    int thr_g = 0, thr_s = 0;
+    size_t smem_g = 0, smem_s = 0;
     for (size_t gi = 0; gi < ctx->g.size(); ++gi) {
         const Group &g = ctx->g[gi];
+        const int threads = g.wpb * g.P;
         if (g.residency == MUCA_RES_SMEM) {
-            G = std::max(G, g.wpb);
-            smem = std::max(smem, smem_bytes_for(g.L, g.wpb));
+            thr_s = std::max(thr_s, threads);
+            smem_s = std::max(smem_s, smem_bytes_for(g.L, g.wpb) + stage_bytes_for(g.wpb));
         } else {
-            wpb_g = std::max(wpb_g, g.wpb);
+            thr_g = std::max(thr_g, threads);
+            smem_g = std::max(smem_g, stage_bytes_for(g.wpb));
         }
         for (int w0 = 0; w0 < g.W; w0 += g.wpb) {
-            BlockDesc b{(int)gi, w0, std::min(g.wpb, g.W - w0), g.wpb};
+            BlockDesc b{(int)gi, w0, std::min(g.wpb, g.W - w0), g.wpb, g.P};
             (g.residency == MUCA_RES_SMEM ? bs : bg).push_back(b);
         }
     }
-    if (smem > 0) {
-        if ((int64_t)smem + 1024 > (int64_t)max_smem_per_block())
+    if (smem_s > 0) {
+        if ((int64_t)smem_s + 1024 > (int64_t)max_smem_per_block())
             return fail(ctx, MUCA_ERR_INVALID_ARG, "shared-memory tile of %zu bytes does not fit",
-                        smem);
-        CK(prepare_smem_kernel(smem));
+                        smem_s);
+        CK(prepare_smem_kernel(smem_s));
     }
     if (ctx->d_blocks_g) cudaFree(ctx->d_blocks_g);
     if (ctx->d_blocks_s) cudaFree(ctx->d_blocks_s);
@@ -246,31 +265,33 @@ int build_blocks(muca_ctx *ctx)
     }
     ctx->n_blocks_g = (int)bg.size();
     ctx->n_blocks_s = (int)bs.size();
-    ctx->threads_g = wpb_g > 0 ? wpb_g : 32;
-    ctx->threads_s = G > 0 ? ((G + 31) / 32) * 32 : 32;
-    ctx->smem_bytes = smem;
+    ctx->threads_g = thr_g > 0 ? thr_g : 32;
+    ctx->threads_s = thr_s > 0 ? thr_s : 32;
+    ctx->smem_g = smem_g;
+    ctx->smem_s = smem_s;
     return MUCA_OK;
 }
 
 // One launch (or two, on forked streams, when both residencies are in use)
 // sweeping every walker of every group.
-int launch_all(muca_ctx *ctx, int n_sweeps, bool record)
+int launch_all(muca_ctx *ctx, int n_sweeps, bool record, cudaStream_t st)
 {
     const bool both = ctx->n_blocks_g > 0 && ctx->n_blocks_s > 0;
     if (both) {
-        CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+        CK(cudaEventRecord(ctx->ev_fork, st));
         CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
     }
     if (ctx->n_blocks_g > 0)
-        CK(launch_sweeps(ctx->d_groups, ctx->d_blocks_g, ctx->n_blocks_g, ctx->threads_g, 0,
-                         ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record, ctx->stream));
+        CK(launch_sweeps(ctx->d_groups, ctx->d_blocks_g, ctx->n_blocks_g, ctx->threads_g,
+                         ctx->smem_g, false, ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record,
+                         st));
     if (ctx->n_blocks_s > 0)
         CK(launch_sweeps(ctx->d_groups, ctx->d_blocks_s, ctx->n_blocks_s, ctx->threads_s,
-                         ctx->smem_bytes, ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record,
-                         both ? ctx->side : ctx->stream));
+                         ctx->smem_s, true, ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record,
+                         both ? ctx->side : st));
     if (both) {
         CK(cudaEventRecord(ctx->ev_join, ctx->side));
-        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+        CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     }
     return MUCA_OK;
 }
@@ -302,57 +323,78 @@ int run_tally_check(muca_ctx *ctx)
 // the fastest.  Choices are cached per (L, walkers) for the process.
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, std::pair<int, int>> g_tune_cache;
 
 struct Cand {
-    int res, wpb;
+    int res, wpb, P;
 };
 
-std::vector<Cand> candidates(const Group &g, int residency, int wpb, int smem_max)
+bool fixed_path(int L) { return L % 4 == 0 && L <= 48 && L != 36 && L != 40 && L != 44; }
+
+// Candidate configurations: (residency, walkers per block, lanes per walker).
+// Fewer walkers per warp spread the chains over more SM sub-partitions and
+// let the extra lanes share the Philox work; the autotuner measures.
+std::vector<Cand> candidates(const Group &g, int residency, int wpb, int P, int smem_max)
 {
     std::vector<Cand> c;
     const bool want_g = residency == MUCA_RES_AUTO || residency == MUCA_RES_GLOBAL;
     const bool want_s = residency == MUCA_RES_AUTO || residency == MUCA_RES_SMEM;
-    if (want_g) {
-        if (wpb > 0 && wpb % 32 == 0 && wpb <= 128) c.push_back({MUCA_RES_GLOBAL, wpb});
-        else
-            for (int w : {32, 64, 128})
-                if (w <= std::max(32, g.Wpad)) c.push_back({MUCA_RES_GLOBAL, w});
-    }
+    const std::vector<int> Ps = !fixed_path(g.L) ? std::vector<int>{1}
+                                : P > 0          ? std::vector<int>{P}
+                                                 : std::vector<int>{1, 2, 4, 8};
+    if (want_g)
+        for (int p : Ps) {
+            if (wpb > 0) {
+                if (wpb * p % 32 == 0 && wpb * p <= 128) c.push_back({MUCA_RES_GLOBAL, wpb, p});
+            } else {
+                c.push_back({MUCA_RES_GLOBAL, 32 / p, p});
+            }
+        }
     if (want_s) {
-        const int fit =
-            (int)std::min<int64_t>(32, (int64_t)(smem_max - 1024) / (int64_t)lattice_bytes(g.L));
-        if (wpb > 0 && wpb <= fit) c.push_back({MUCA_RES_SMEM, wpb});
-        else if (wpb <= 0)
-            for (int G : {32, 16, 8})
-                if (G <= fit) c.push_back({MUCA_RES_SMEM, G});
+        const int64_t per = (int64_t)lattice_bytes(g.L) + (int64_t)stage_bytes_for(1);
+        const int fit = (int)std::min<int64_t>(32, (int64_t)(smem_max - 1024) / per);
+        for (int p : Ps) {
+            if (wpb > 0) {
+                if (wpb <= fit && wpb * p <= 128 && (wpb * p) % 32 == 0)
+                    c.push_back({MUCA_RES_SMEM, wpb, p});
+            } else {
+                const int G = std::min(fit, 32 / p);
+                if (G >= 1 && (G * p) % 32 == 0) c.push_back({MUCA_RES_SMEM, G, p});
+            }
+        }
     }
     return c;
 }
 
+// choices of the autotuner per (L, walkers, requested residency, walkers per
+// block, lanes per walker)
+std::map<std::tuple<int, int, int, int, int>, Cand> g_tune_cache;
+
 }  // namespace
 
-static int tune_group(muca_ctx *ctx, size_t gi, int residency, int wpb)
+static int tune_group(muca_ctx *ctx, size_t gi, int residency, int wpb, int P)
 {
     Group &g = ctx->g[gi];
     const int smem_max = max_smem_per_block();
-    std::vector<Cand> cands = candidates(g, residency, wpb, smem_max);
+    std::vector<Cand> cands = candidates(g, residency, wpb, P, smem_max);
     if (cands.empty())
         return fail(ctx, MUCA_ERR_INVALID_ARG,
-                    "no kernel configuration fits group %d (L=%d, residency %d, wpb %d)", (int)gi,
-                    g.L, residency, wpb);
+                    "no kernel configuration fits group %d (L=%d, residency %d, walkers per block "
+                    "%d, lanes per walker %d)",
+                    (int)gi, g.L, residency, wpb, P);
     // a group outside its window cannot be swept yet: take the first candidate
     if (cands.size() == 1 || !g.in_window) {
         g.residency = cands[0].res;
         g.wpb = cands[0].wpb;
+        g.P = cands[0].P;
         return MUCA_OK;
     }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find({g.L, g.W});
+        auto it = g_tune_cache.find(std::make_tuple(g.L, g.W, residency, wpb, P));
         if (it != g_tune_cache.end()) {
-            g.residency = it->second.first;
-            g.wpb = it->second.second;
+            g.residency = it->second.res;
+            g.wpb = it->second.wpb;
+            g.P = it->second.P;
             return MUCA_OK;
         }
     }
@@ -387,11 +429,12 @@ static int tune_group(muca_ctx *ctx, size_t gi, int residency, int wpb)
         if (rc != MUCA_OK) break;
         ctx->g[0].residency = c.res;
         ctx->g[0].wpb = c.wpb;
+        ctx->g[0].P = c.P;
         rc = build_blocks(ctx);
         if (rc != MUCA_OK) break;
-        rc = launch_all(ctx, 1, false);  // warm-up
+        rc = launch_all(ctx, 1, false, ctx->stream);  // warm-up
         cudaEventRecord(a, ctx->stream);
-        if (rc == MUCA_OK) rc = launch_all(ctx, trial_sweeps, false);
+        if (rc == MUCA_OK) rc = launch_all(ctx, trial_sweeps, false, ctx->stream);
         cudaEventRecord(b, ctx->stream);
         if (cudaEventSynchronize(b) != cudaSuccess) rc = MUCA_ERR_CUDA;
         float ms = 0;
@@ -417,8 +460,9 @@ static int tune_group(muca_ctx *ctx, size_t gi, int residency, int wpb)
     if (rc != MUCA_OK) return rc;
     g.residency = pick.res;
     g.wpb = pick.wpb;
+    g.P = pick.P;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[{g.L, g.W}] = {pick.res, pick.wpb};
+    g_tune_cache[std::make_tuple(g.L, g.W, residency, wpb, P)] = pick;
     return MUCA_OK;
 }
 
@@ -461,6 +505,7 @@ void muca_destroy(muca_ctx *ctx)
     cudaFree(ctx->d_blocks_g);
     cudaFree(ctx->d_blocks_s);
     if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
@@ -479,6 +524,10 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
     if (opt->walkers_per_block < 0 || opt->walkers_per_block > 128)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad walkers_per_block %d",
                     opt->walkers_per_block);
+    if (opt->lanes_per_walker != 0 && opt->lanes_per_walker != 1 && opt->lanes_per_walker != 2 &&
+        opt->lanes_per_walker != 4 && opt->lanes_per_walker != 8)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad lanes_per_walker %d",
+                    opt->lanes_per_walker);
     int64_t total_w = 0;
     for (int i = 0; i < n_groups; ++i) {
         const muca_group &s = groups[i];
@@ -514,6 +563,7 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
     } while (0)
     {
         CKI(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        CKI(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
         CKI(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
         CKI(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
         CKI(cudaMalloc(&ctx->d_err, sizeof(int)));
@@ -544,8 +594,8 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
             CKI(cudaMemsetAsync(g.tal, 0, (size_t)3 * g.Wpad * sizeof(int32_t), ctx->stream));
             CKI(cudaMalloc(&g.hist, (size_t)g.nE * sizeof(unsigned long long)));
             CKI(cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long), ctx->stream));
-            CKI(cudaMalloc(&g.thr, (size_t)g.nE * kRow * sizeof(uint32_t)));
-            CKI(cudaMallocHost(&g.h_thr, (size_t)g.nE * kRow * sizeof(uint32_t)));
+            CKI(cudaMalloc(&g.thr, table_rows(g.nE) * kRow * sizeof(uint32_t)));
+            CKI(cudaMallocHost(&g.h_thr, table_rows(g.nE) * kRow * sizeof(uint32_t)));
             CKI(cudaMallocHost(&g.h_hist, (size_t)g.nE * sizeof(unsigned long long)));
             CKI(launch_init_spins(dev_of(g), ctx->seed, ctx->stream));
             CKI(launch_energies(dev_of(g), 0, ctx->d_err, ctx->stream));
@@ -566,7 +616,8 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
                 if (ed[w] < g.e_min || ed[w] > g.e_max) g.in_window = false;
         }
         for (int i = 0; i < n_groups; ++i)
-            if ((rc = tune_group(ctx, i, opt->residency, opt->walkers_per_block)) != MUCA_OK)
+            if ((rc = tune_group(ctx, i, opt->residency, opt->walkers_per_block,
+                                 opt->lanes_per_walker)) != MUCA_OK)
                 goto bad;
         if ((rc = build_blocks(ctx)) != MUCA_OK) goto bad;
         CKI(cudaStreamSynchronize(ctx->stream));
@@ -601,7 +652,7 @@ int muca_sweep_iter(muca_ctx *ctx, int n_sweeps, int record)
         return fail(ctx, MUCA_ERR_INVALID_ARG,
                     "time series full: %lld recorded + %d > capacity %lld (muca_reserve_timeseries)",
                     (long long)ctx->ts_len, n_sweeps, (long long)ctx->ts_cap);
-    int rc = launch_all(ctx, n_sweeps, record != 0);
+    int rc = launch_all(ctx, n_sweeps, record != 0, ctx->stream);
     if (rc != MUCA_OK) return rc;
     ctx->sweep += (uint64_t)n_sweeps;
     if (record) ctx->ts_len += n_sweeps;
@@ -658,27 +709,31 @@ extern "C" int muca_run_graph(muca_ctx *ctx, int n_iters, int sweeps_per_iter)
                         "group %d has walkers outside its E_Delta window: set a state first",
                         (int)i);
     CK(cudaStreamSynchronize(ctx->stream));
+    // captured on the context's own non-blocking stream (the caller's stream
+    // may be the legacy default stream, which cannot be captured), launched on
+    // the caller's stream
+    cudaStream_t cs = ctx->cap;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const uint64_t sweep_start = ctx->sweep;
-    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int rc = MUCA_OK;
     for (int it = 0; it < n_iters && rc == MUCA_OK; ++it) {
-        rc = launch_all(ctx, sweeps_per_iter, false);
+        rc = launch_all(ctx, sweeps_per_iter, false, cs);
         ctx->sweep += (uint64_t)sweeps_per_iter;
         for (auto &g : ctx->g) {
             if (rc != MUCA_OK) break;
             if (cudaMemcpyAsync(g.h_hist, g.hist, (size_t)g.nE * sizeof(unsigned long long),
-                                cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-                cudaLaunchHostFunc(ctx->stream, host_update, &g) != cudaSuccess ||
-                cudaMemcpyAsync(g.thr, g.h_thr, (size_t)g.nE * kRow * sizeof(uint32_t),
-                                cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
-                cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long),
-                                ctx->stream) != cudaSuccess)
+                                cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+                cudaLaunchHostFunc(cs, host_update, &g) != cudaSuccess ||
+                cudaMemcpyAsync(g.thr, g.h_thr, table_rows(g.nE) * kRow * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+                cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long), cs) !=
+                    cudaSuccess)
                 rc = fail(ctx, MUCA_ERR_CUDA, "graph capture of the merge failed");
         }
     }
-    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (rc == MUCA_OK && ce != cudaSuccess)
         rc = fail(ctx, MUCA_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ce));
     if (rc == MUCA_OK) {
@@ -801,7 +856,8 @@ int muca_set_table(muca_ctx *ctx, int group, const uint32_t *in)
     if (!in) return fail(ctx, MUCA_ERR_INVALID_ARG, "in is NULL");
     Group &g = ctx->g[group];
     CK(cudaStreamSynchronize(ctx->stream));
-    pack_logical(g, in);
+    rc = pack_logical(ctx, g, in);
+    if (rc) return rc;
     g.injected.assign(in, in + (size_t)g.nE * 3 * MUCA_NK);
     rc = upload_table(ctx, g);
     if (rc) return rc;
@@ -917,12 +973,14 @@ int muca_check_tallies(muca_ctx *ctx)
     return run_tally_check(ctx);
 }
 
-int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walkers_per_block)
+int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walkers_per_block,
+                    int32_t *lanes_per_walker)
 {
     int rc = check_group_index(ctx, group);
     if (rc) return rc;
     if (residency) *residency = ctx->g[group].residency;
     if (walkers_per_block) *walkers_per_block = ctx->g[group].wpb;
+    if (lanes_per_walker) *lanes_per_walker = ctx->g[group].P;
     return MUCA_OK;
 }
 

@@ -42,7 +42,8 @@ class Group(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint32), ("debug_flags", ctypes.c_int32),
-                ("residency", ctypes.c_int32), ("walkers_per_block", ctypes.c_int32)]
+                ("residency", ctypes.c_int32), ("walkers_per_block", ctypes.c_int32),
+                ("lanes_per_walker", ctypes.c_int32)]
 
 
 _lib = None
@@ -73,7 +74,7 @@ SIGNATURES = {
     "muca_get_state": [_P, ctypes.c_int, _P, _P],
     "muca_set_state": [_P, ctypes.c_int, _P],
     "muca_check_tallies": [_P],
-    "muca_get_config": [_P, ctypes.c_int, _P, _P],
+    "muca_get_config": [_P, ctypes.c_int, _P, _P, _P],
     "muca_checkpoint": [_P, ctypes.c_char_p],
     "muca_restore": [_P, ctypes.c_char_p],
 }
@@ -123,7 +124,7 @@ class Context:
     """A set of (L, T) walker groups on one GPU (``muca_init`` .. ``muca_destroy``)."""
 
     def __init__(self, groups, seed=0, debug_flags=0, residency=RES_AUTO, walkers_per_block=0,
-                 stream=None):
+                 lanes_per_walker=0, stream=None):
         L = lib()
         self.specs = []
         arr = (Group * len(groups))()
@@ -136,7 +137,7 @@ class Context:
             self.specs.append({"L": int(g["L"]), "T": float(g["T"]), "n_walkers": int(g["n_walkers"]),
                                "e_min": int(g.get("e_min", 0)),
                                "e_max": V if e_max < 0 else int(e_max), "V": V})
-        opt = Options(seed, debug_flags, residency, walkers_per_block)
+        opt = Options(seed, debug_flags, residency, walkers_per_block, lanes_per_walker)
         self._stream = _stream_ptr(stream)
         self._ctx = ctypes.c_void_p()
         _ck(L.muca_init(ctypes.cast(arr, _P), len(groups), ctypes.byref(opt), self._stream,
@@ -164,6 +165,8 @@ class Context:
         _ck(rc, self._ctx)
 
     def n_e(self, g):
+        if not 0 <= g < len(self.specs):
+            raise MucaError(ERR_INVALID_ARG, f"group {g} out of range [0, {len(self.specs)})")
         s = self.specs[g]
         return s["e_max"] - s["e_min"] + 1
 
@@ -234,6 +237,7 @@ class Context:
         self._c(lib().muca_set_hist(self._ctx, g, _np_ptr(a)))
 
     def get_state(self, g):
+        self.n_e(g)
         s = self.specs[g]
         spins = np.zeros((s["n_walkers"], s["V"]), dtype=np.int8)
         tal = np.zeros((s["n_walkers"], 3), dtype=np.int32)
@@ -250,10 +254,13 @@ class Context:
         self._c(lib().muca_check_tallies(self._ctx))
 
     def get_config(self, g):
+        """(residency, walkers per block, lanes per walker) of group g."""
         r = ctypes.c_int32()
         w = ctypes.c_int32()
-        self._c(lib().muca_get_config(self._ctx, g, ctypes.byref(r), ctypes.byref(w)))
-        return r.value, w.value
+        p = ctypes.c_int32()
+        self._c(lib().muca_get_config(self._ctx, g, ctypes.byref(r), ctypes.byref(w),
+                                      ctypes.byref(p)))
+        return r.value, w.value, p.value
 
     def checkpoint(self, path):
         self._c(lib().muca_checkpoint(self._ctx, os.fsencode(path)))

@@ -116,13 +116,18 @@ def compare_group(got, ref, n_iter):
     assert np.array_equal(got["tallies"], ref["tallies"])
 
 
-@pytest.mark.parametrize("residency,wpb", [(1, 32), (1, 64), (2, 32), (2, 8), (0, 0)])
-def test_small_workload_full_run_bit_exact(residency, wpb):
-    """L=8, T=2.0, 64 walkers, 10 iterations x 200 sweeps, seed 0, in full."""
+@pytest.mark.parametrize("residency,wpb,P", [(1, 32, 1), (1, 64, 1), (1, 16, 2), (1, 8, 4),
+                                             (1, 4, 8), (2, 32, 1), (2, 8, 4), (2, 4, 8),
+                                             (0, 0, 0)])
+def test_small_workload_full_run_bit_exact(residency, wpb, P):
+    """L=8, T=2.0, 64 walkers, 10 iterations x 200 sweeps, seed 0, in full,
+    in every kernel configuration (results never depend on it)."""
     s = wl.SMALL
     g = [{"L": s["L"], "T": s["T"], "n_walkers": s["n_walkers"]}]
     got = gpu_run(g, s["seed"], s["n_iter"], s["sweeps"], n_meas=50, residency=residency,
-                  walkers_per_block=wpb)[0]
+                  walkers_per_block=wpb, lanes_per_walker=P)[0]
+    if residency:
+        assert got["config"] == (residency, wpb, P)
     ref = oracle.muca_run(s["L"], s["T"], s["n_walkers"], s["seed"], s["n_iter"], s["sweeps"],
                           n_meas=50)
     compare_group(got, ref, s["n_iter"])
@@ -152,6 +157,21 @@ def test_mixed_groups_reduced_bit_exact():
         assert np.array_equal(got[g]["ts"], ref["ts"].transpose(1, 2, 0))
 
 
+@pytest.mark.parametrize("P", [1, 2, 8])
+def test_generic_and_unrolled_sizes_in_one_launch(P):
+    """Sizes of the unrolled row path and of the plain per-site path (L % 4 != 0)
+    side by side; lanes per walker apply to the unrolled sizes only."""
+    groups = [{"L": L, "T": T, "n_walkers": nw}
+              for L, T, nw in [(2, 1.0, 7), (3, 2.0, 33), (4, 0.9, 40), (5, 1.4182, 9),
+                               (12, 1.0, 65), (20, 2.0, 31)]]
+    got = gpu_run(groups, 23, 2, 4, n_meas=3, residency=1, lanes_per_walker=P)
+    for g, (spec, w0) in enumerate(zip(groups, walker_offsets(groups))):
+        ref = oracle.muca_run(spec["L"], spec["T"], spec["n_walkers"], 23, 2, 4, n_meas=3,
+                              walker_id0=w0)
+        compare_group(got[g], ref, 2)
+        assert np.array_equal(got[g]["ts"], ref["ts"].transpose(1, 2, 0))
+
+
 def test_medium_workload_reduced_bit_exact():
     """L=16, T=1.0, 1024 walkers, seed 1: 2 iterations x 8 sweeps + 4 measured."""
     s = wl.MEDIUM
@@ -166,8 +186,8 @@ def sample_walkers(W):
     return sorted({0, 1, 31, 32, 33, W // 2, W - 33, W - 1} & set(range(W)))
 
 
-@pytest.mark.parametrize("residency", [0, 1])
-def test_large_workload_full_size_sampled_walkers(residency):
+@pytest.mark.parametrize("residency,P", [(0, 0), (1, 1), (1, 4), (1, 8)])
+def test_large_workload_full_size_sampled_walkers(residency, P):
     """L=48, T=0.9, all 4096 walkers in the benchmark's launch configuration,
     under a fixed non-trivial weight: sampled walkers recomputed by the oracle,
     plus the merged histogram against the recorded series (any size)."""
@@ -175,7 +195,8 @@ def test_large_workload_full_size_sampled_walkers(residency):
     L, T, W = s["L"], s["T"], s["n_walkers"]
     V = L ** 3
     lnW = wl.random_lnW(V + 1, seed=11, scale=0.3, slope=-2.9 / T)
-    c = ctx_of([{"L": L, "T": T, "n_walkers": W}], seed=s["seed"], residency=residency)
+    c = ctx_of([{"L": L, "T": T, "n_walkers": W}], seed=s["seed"], residency=residency,
+               lanes_per_walker=P)
     c.set_lnW(0, lnW)
     n = 2
     c.reserve_timeseries(n)
@@ -316,10 +337,18 @@ def test_errors_are_reported_not_raised_as_faults():
     with pytest.raises(muca().MucaError) as e:
         c.get_lnW(5)
     assert e.value.code == muca().ERR_INVALID_ARG
-    bad = oracle.build_table(4, 1.0, 0, 64, np.zeros(65))
-    bad[3, 1, 0] ^= 1  # d = 0 entries must not depend on E_Delta
-    with pytest.raises(muca().MucaError):
-        c.set_table(0, bad)
+    with pytest.raises(muca().MucaError) as e:
+        c.set_table(3, oracle.build_table(4, 1.0, 0, 64, np.zeros(65)))
+    assert e.value.code == muca().ERR_INVALID_ARG
+    with pytest.raises(muca().MucaError) as e:
+        c.run_graph(-1, 5)
+    assert e.value.code == muca().ERR_INVALID_ARG
+    # d = 0 moves do not change E_Delta, so their thresholds cannot depend on it
+    t = oracle.build_table(4, 1.0, 0, 64, np.zeros(65))
+    t[3, 1, 0] ^= 1
+    with pytest.raises(muca().MucaError) as e:
+        c.set_table(0, t)
+    assert e.value.code == muca().ERR_INVALID_ARG
     c.close()
 
 
