@@ -76,6 +76,10 @@ typedef struct {
 #define MUCA_RES_AUTO 0   /* chosen by the autotuner (measured) */
 #define MUCA_RES_GLOBAL 1 /* spins stay in HBM/L2, site-major walker-minor */
 #define MUCA_RES_SMEM 2   /* each block keeps its walkers' lattices in shared memory */
+#define MUCA_RES_SPLIT 3  /* spins in HBM/L2; each block has one warp that runs the
+                             walkers' Metropolis chains and three warps that prepare
+                             and finish the rows around it (L % 4 == 0, 8 <= L <= 48;
+                             other sizes fall back to MUCA_RES_GLOBAL) */
 
 /* debug_flags bits */
 #define MUCA_DEBUG_TALLY_CHECK 1 /* recompute E_J, E_Delta, M after every sweep call */
@@ -84,8 +88,9 @@ typedef struct {
     uint32_t seed;             /* Philox key word 1 */
     int32_t debug_flags;       /* MUCA_DEBUG_* bits */
     int32_t residency;         /* MUCA_RES_* */
-    int32_t walkers_per_block; /* 0 = automatic; else 1 .. 128 with walkers_per_block x
-                                  lanes_per_walker a multiple of 32 and <= 128 */
+    int32_t walkers_per_block; /* 0 = automatic; else 1 .. 32; a block is one warp, so
+                                  walkers_per_block x lanes_per_walker <= 32 (== 32 for
+                                  global residency) */
     int32_t lanes_per_walker;  /* 0 = automatic; else 1, 2, 4 or 8 threads serve one
                                   walker (they share its random numbers) */
 } muca_options;
@@ -206,8 +211,9 @@ int muca_set_state(muca_ctx *ctx, int group, const int8_t *spins);
  * running tallies: MUCA_OK or MUCA_ERR_TALLY_MISMATCH. */
 int muca_check_tallies(muca_ctx *ctx);
 
-/* Kernel configuration chosen for group g: residency (MUCA_RES_GLOBAL or
- * MUCA_RES_SMEM), walkers per block and lanes per walker.  Any may be NULL. */
+/* Kernel configuration chosen for group g: residency (MUCA_RES_GLOBAL,
+ * MUCA_RES_SMEM or MUCA_RES_SPLIT), walkers per block and lanes per walker
+ * (0 for MUCA_RES_SPLIT).  Any output may be NULL. */
 int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walkers_per_block,
                     int32_t *lanes_per_walker);
 

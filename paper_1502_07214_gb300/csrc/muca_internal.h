@@ -7,22 +7,21 @@
 
 namespace muca {
 
-// Packed acceptance table of one group, as the sweep kernel reads it.  One
-// allocation of table_rows(nE) rows of kRow uint32 (one 128-byte line each):
-//   row 0                 the d = 0 moves (s = +-1 -> -+1), which do not depend on
-//                         E_Delta: column (dE_J + 12) / 2, dE_J = -12, -10, .., 12
-//   rows 1 .. kGuard      zero (guard)
-//   rows kGuard+1 + e     E_Delta = e_min + e, e = 0 .. nE-1:
-//                           columns 0 .. 12        d = -1 (s = +-1 -> 0), dE_J + 6
-//                           columns kPlus .. kPlus+12  d = +1 (s = 0 -> +-1), dE_J + 6
-//   last kGuard rows      zero (guard)
-// The guard rows let the kernel prefetch the rows E_Delta +- 2 without bounds
-// checks; they are never compared against (moves that leave the window read 0
-// from the window's own rows).
-constexpr int kRow = 32;
-constexpr int kPlus = 16;
+// Packed acceptance table of one group, as the sweep kernel reads it: one
+// allocation of table_rows(nE) rows of kRow uint32 (160 bytes):
+//   rows 0 .. kGuard-1     zero (guard)
+//   row kGuard + e         E_Delta = e_min + e, e = 0 .. nE-1, every move kind:
+//     column 13 (d + 1) + (d == 0 ? (dE_J + 12) / 2 : dE_J + 6),
+//     d = -1: s = +-1 -> 0, d = 0: s = +-1 -> -+1, d = +1: s = 0 -> +-1
+//   last kGuard rows       zero (guard)
+// The d = 0 columns repeat in every row so that one index formula serves all
+// moves.  The guard rows let the kernel read the rows E_Delta +- 1 and copy
+// windows of rows without bounds checks; they are never compared against
+// (moves that leave the window read 0 from the window's own rows).
+constexpr int kRow = 40;
+constexpr int kBlk = 13;
 constexpr int kGuard = 2;
-inline size_t table_rows(int nE) { return (size_t)nE + 2 * kGuard + 1; }
+inline size_t table_rows(int nE) { return (size_t)nE + 2 * kGuard; }
 
 // Spin layout of a group: int8 spins packed four consecutive sites of a row
 // per 32-bit word, walker-minor: word (row, j) of walker w is at
@@ -38,7 +37,6 @@ struct GroupDev {
     uint32_t *spins;            // [L * L][Lw][Wpad] packed words
     int32_t *tal;               // [3][Wpad]: E_J, E_Delta, M
     unsigned long long *hist;   // [nE]
-    const uint32_t *thr0;       // the d = 0 row of the table allocation
     const uint32_t *thrE;       // the row of E_Delta = e_min in the table allocation
     int32_t *ts;                // [cap][3][W] or nullptr
 };
@@ -69,8 +67,16 @@ cudaError_t launch_sweeps(const GroupDev *groups_dev, const BlockDesc *blocks_de
                           uint64_t sweep0, int n_sweeps, int64_t ts_pos, bool record,
                           cudaStream_t st);
 cudaError_t prepare_smem_kernel(size_t smem_bytes);
+cudaError_t prepare_global_kernel(size_t smem_bytes);
+// Warp-specialised launch (blocks of one chain warp and three helper warps;
+// BlockDesc.S walker slots, a power of 2 in [4, 32]).
+cudaError_t launch_sweeps_ws(const GroupDev *groups_dev, const BlockDesc *blocks_dev, int n_blocks,
+                             size_t smem_bytes, uint32_t seed, uint64_t sweep0, int n_sweeps,
+                             int64_t ts_pos, bool record, cudaStream_t st);
+cudaError_t prepare_ws_kernel(size_t smem_bytes);
+size_t ws_bytes_for(int slots);
 // Bytes of one walker's lattice (padded rows), of a shared-memory tile, and of
-// the per-row staging area of `slots` walkers.
+// the per-row staging area and table windows of `slots` walkers.
 size_t lattice_bytes(int L);
 size_t smem_bytes_for(int L, int walkers);
 size_t stage_bytes_for(int slots);

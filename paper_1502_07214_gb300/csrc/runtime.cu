@@ -60,17 +60,19 @@ struct muca_ctx {
     uint32_t seed = 0;
     int debug = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t side = nullptr;  // second stream for the shared-memory blocks
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // one stream per kernel kind
     cudaStream_t cap = nullptr;   // stream the iteration graph is captured on
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
     uint64_t sweep = 0;
     int64_t ts_cap = 0, ts_len = 0;
     std::string err = "no error";
     int *d_err = nullptr;
     GroupDev *d_groups = nullptr;
-    BlockDesc *d_blocks_g = nullptr, *d_blocks_s = nullptr;
-    int n_blocks_g = 0, n_blocks_s = 0, threads_g = 32, threads_s = 32;
-    size_t smem_g = 0, smem_s = 0;  // dynamic shared memory of the two launches
+    // one launch per kernel kind in use: 0 lanes-per-walker (global lattice),
+    // 1 shared-memory lattice, 2 split warps (global lattice)
+    BlockDesc *d_blocks[3] = {nullptr, nullptr, nullptr};
+    int n_blocks[3] = {0, 0, 0};
+    size_t smem[3] = {0, 0, 0};
 };
 
 namespace {
@@ -140,15 +142,17 @@ void build_packed(Group &g)
 {
     uint32_t *T = g.h_thr;
     std::memset(T, 0, table_rows(g.nE) * kRow * sizeof(uint32_t));
-    for (int k = 0; k < 13; ++k) T[k] = thr_entry(g, 0, 0, 2 * k - 12);
-    uint32_t *E0 = T + (size_t)(1 + kGuard) * kRow;
-    parallel_rows(g.nE, [&g, E0](int b, int e_end) {
+    uint32_t *E0 = T + (size_t)kGuard * kRow;
+    uint32_t d0[kBlk];
+    for (int k = 0; k < kBlk; ++k) d0[k] = thr_entry(g, 0, 0, 2 * k - 12);
+    parallel_rows(g.nE, [&g, E0, &d0](int b, int e_end) {
         for (int e = b; e < e_end; ++e) {
             uint32_t *row = E0 + (size_t)e * kRow;
             for (int dej = -6; dej <= 6; ++dej) {
                 row[dej + 6] = thr_entry(g, e, -1, dej);
-                row[kPlus + dej + 6] = thr_entry(g, e, +1, dej);
+                row[2 * kBlk + dej + 6] = thr_entry(g, e, +1, dej);
             }
+            for (int k = 0; k < kBlk; ++k) row[kBlk + k] = d0[k];
         }
     });
 }
@@ -158,21 +162,21 @@ void build_packed(Group &g)
 int pack_logical(muca_ctx *ctx, Group &g, const uint32_t *lg)
 {
     for (int e = 0; e < g.nE; ++e)
-        for (int k = 0; k < 13; ++k)
+        for (int k = 0; k < kBlk; ++k)
             if (lg[((size_t)e * 3 + 1) * MUCA_NK + 2 * k] != lg[1 * MUCA_NK + 2 * k])
                 return fail(ctx, MUCA_ERR_INVALID_ARG,
                             "set_table: d = 0 entries must not depend on E_Delta (row %d)", e);
     uint32_t *T = g.h_thr;
     std::memset(T, 0, table_rows(g.nE) * kRow * sizeof(uint32_t));
-    for (int k = 0; k < 13; ++k) T[k] = lg[1 * MUCA_NK + 2 * k];
-    uint32_t *E0 = T + (size_t)(1 + kGuard) * kRow;
+    uint32_t *E0 = T + (size_t)kGuard * kRow;
     for (int e = 0; e < g.nE; ++e) {
         const uint32_t *r = lg + (size_t)e * 3 * MUCA_NK;
         uint32_t *row = E0 + (size_t)e * kRow;
         for (int dej = -6; dej <= 6; ++dej) {
             row[dej + 6] = r[0 * MUCA_NK + dej + 12];
-            row[kPlus + dej + 6] = r[2 * MUCA_NK + dej + 12];
+            row[2 * kBlk + dej + 6] = r[2 * MUCA_NK + dej + 12];
         }
+        for (int k = 0; k < kBlk; ++k) row[kBlk + k] = r[1 * MUCA_NK + 2 * k];
     }
     return MUCA_OK;
 }
@@ -205,8 +209,7 @@ GroupDev dev_of(const Group &g)
     d.spins = g.spins;
     d.tal = g.tal;
     d.hist = g.hist;
-    d.thr0 = g.thr;
-    d.thrE = g.thr ? g.thr + (size_t)(1 + kGuard) * kRow : nullptr;
+    d.thrE = g.thr ? g.thr + (size_t)kGuard * kRow : nullptr;
     d.ts = g.ts;
     return d;
 }
@@ -219,79 +222,74 @@ int upload_groups(muca_ctx *ctx)
     return MUCA_OK;
 }
 
-// Block lists of the global-residency and shared-memory-resident launches.
-// A block of group g serves wpb_g walkers with P_g lanes each; a
-// shared-memory block also holds their lattices as a [L*L][Lw][wpb_g] tile.
-// Every block of one launch has the launch's thread count (the largest
-// wpb * P of its groups; surplus threads idle).
+// Kernel kind of a group's configuration.
+int kind_of(const Group &g)
+{
+    return g.residency == MUCA_RES_SMEM ? 1 : g.residency == MUCA_RES_SPLIT ? 2 : 0;
+}
+
+// Block lists of the launches.  A block of group g serves wpb_g walkers:
+//   kind 0: one warp, P_g lanes per walker, staging area and table windows;
+//   kind 1: one warp, the walkers' lattices as a [L*L][Lw][wpb_g] tile too;
+//   kind 2: four warps (chain + helpers), wpb_g a power of 2 in [4, 32].
 int build_blocks(muca_ctx *ctx)
 {
-    std::vector<BlockDesc> bg, bs;
-    int thr_g = 0, thr_s = 0;
-    size_t smem_g = 0, smem_s = 0;
+    std::vector<BlockDesc> b[3];
+    size_t sm[3] = {0, 0, 0};
     for (size_t gi = 0; gi < ctx->g.size(); ++gi) {
         const Group &g = ctx->g[gi];
-        const int threads = g.wpb * g.P;
-        if (g.residency == MUCA_RES_SMEM) {
-            thr_s = std::max(thr_s, threads);
-            smem_s = std::max(smem_s, smem_bytes_for(g.L, g.wpb) + stage_bytes_for(g.wpb));
-        } else {
-            thr_g = std::max(thr_g, threads);
-            smem_g = std::max(smem_g, stage_bytes_for(g.wpb));
+        const int k = kind_of(g);
+        const size_t need = k == 0   ? stage_bytes_for(g.wpb)
+                            : k == 1 ? smem_bytes_for(g.L, g.wpb) + stage_bytes_for(g.wpb)
+                                     : ws_bytes_for(g.wpb);
+        sm[k] = std::max(sm[k], need);
+        for (int w0 = 0; w0 < g.W; w0 += g.wpb)
+            b[k].push_back(BlockDesc{(int)gi, w0, std::min(g.wpb, g.W - w0), g.wpb, g.P});
+    }
+    for (int k = 0; k < 3; ++k) {
+        if (sm[k] > 0 && (int64_t)sm[k] + 1024 > (int64_t)max_smem_per_block())
+            return fail(ctx, MUCA_ERR_INVALID_ARG, "%zu bytes of shared memory per block do not fit",
+                        sm[k]);
+        if (!b[k].empty()) {
+            if (k == 0) CK(prepare_global_kernel(sm[k]));
+            if (k == 1) CK(prepare_smem_kernel(sm[k]));
+            if (k == 2) CK(prepare_ws_kernel(sm[k]));
         }
-        for (int w0 = 0; w0 < g.W; w0 += g.wpb) {
-            BlockDesc b{(int)gi, w0, std::min(g.wpb, g.W - w0), g.wpb, g.P};
-            (g.residency == MUCA_RES_SMEM ? bs : bg).push_back(b);
+        if (ctx->d_blocks[k]) cudaFree(ctx->d_blocks[k]);
+        ctx->d_blocks[k] = nullptr;
+        if (!b[k].empty()) {
+            CK(cudaMalloc(&ctx->d_blocks[k], b[k].size() * sizeof(BlockDesc)));
+            CK(cudaMemcpy(ctx->d_blocks[k], b[k].data(), b[k].size() * sizeof(BlockDesc),
+                          cudaMemcpyHostToDevice));
         }
+        ctx->n_blocks[k] = (int)b[k].size();
+        ctx->smem[k] = sm[k];
     }
-    if (smem_s > 0) {
-        if ((int64_t)smem_s + 1024 > (int64_t)max_smem_per_block())
-            return fail(ctx, MUCA_ERR_INVALID_ARG, "shared-memory tile of %zu bytes does not fit",
-                        smem_s);
-        CK(prepare_smem_kernel(smem_s));
-    }
-    if (ctx->d_blocks_g) cudaFree(ctx->d_blocks_g);
-    if (ctx->d_blocks_s) cudaFree(ctx->d_blocks_s);
-    ctx->d_blocks_g = ctx->d_blocks_s = nullptr;
-    if (!bg.empty()) {
-        CK(cudaMalloc(&ctx->d_blocks_g, bg.size() * sizeof(BlockDesc)));
-        CK(cudaMemcpy(ctx->d_blocks_g, bg.data(), bg.size() * sizeof(BlockDesc),
-                      cudaMemcpyHostToDevice));
-    }
-    if (!bs.empty()) {
-        CK(cudaMalloc(&ctx->d_blocks_s, bs.size() * sizeof(BlockDesc)));
-        CK(cudaMemcpy(ctx->d_blocks_s, bs.data(), bs.size() * sizeof(BlockDesc),
-                      cudaMemcpyHostToDevice));
-    }
-    ctx->n_blocks_g = (int)bg.size();
-    ctx->n_blocks_s = (int)bs.size();
-    ctx->threads_g = thr_g > 0 ? thr_g : 32;
-    ctx->threads_s = thr_s > 0 ? thr_s : 32;
-    ctx->smem_g = smem_g;
-    ctx->smem_s = smem_s;
     return MUCA_OK;
 }
 
-// One launch (or two, on forked streams, when both residencies are in use)
-// sweeping every walker of every group.
+// The launches of one sweep call: on the caller's stream when one kernel kind
+// is in use, otherwise forked over the per-kind streams and joined.
 int launch_all(muca_ctx *ctx, int n_sweeps, bool record, cudaStream_t st)
 {
-    const bool both = ctx->n_blocks_g > 0 && ctx->n_blocks_s > 0;
-    if (both) {
-        CK(cudaEventRecord(ctx->ev_fork, st));
-        CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-    }
-    if (ctx->n_blocks_g > 0)
-        CK(launch_sweeps(ctx->d_groups, ctx->d_blocks_g, ctx->n_blocks_g, ctx->threads_g,
-                         ctx->smem_g, false, ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record,
-                         st));
-    if (ctx->n_blocks_s > 0)
-        CK(launch_sweeps(ctx->d_groups, ctx->d_blocks_s, ctx->n_blocks_s, ctx->threads_s,
-                         ctx->smem_s, true, ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record,
-                         both ? ctx->side : st));
-    if (both) {
-        CK(cudaEventRecord(ctx->ev_join, ctx->side));
-        CK(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+    int used = 0;
+    for (int k = 0; k < 3; ++k) used += ctx->n_blocks[k] > 0;
+    const bool fork = used > 1;
+    if (fork) CK(cudaEventRecord(ctx->ev_fork, st));
+    for (int k = 0; k < 3; ++k) {
+        if (ctx->n_blocks[k] == 0) continue;
+        cudaStream_t s = fork ? ctx->side[k] : st;
+        if (fork) CK(cudaStreamWaitEvent(s, ctx->ev_fork, 0));
+        if (k == 2)
+            CK(launch_sweeps_ws(ctx->d_groups, ctx->d_blocks[k], ctx->n_blocks[k], ctx->smem[k],
+                                ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record, s));
+        else
+            CK(launch_sweeps(ctx->d_groups, ctx->d_blocks[k], ctx->n_blocks[k], 32, ctx->smem[k],
+                             k == 1, ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record, s));
+        if (fork) {
+            CK(cudaEventRecord(ctx->ev_join[k], s));
+            CK(cudaStreamWaitEvent(st, ctx->ev_join[k], 0));
+        }
     }
     return MUCA_OK;
 }
@@ -328,37 +326,54 @@ struct Cand {
     int res, wpb, P;
 };
 
-bool fixed_path(int L) { return L % 4 == 0 && L <= 48 && L != 36 && L != 40 && L != 44; }
+// The unrolled row path: L % 4 == 0 up to 48 (see sweep.cu) and a table at
+// least as long as the per-walker window.
+bool fixed_path(const Group &g)
+{
+    const bool size_ok = g.L % 4 == 0 && g.L <= 48 && g.L != 36 && g.L != 40 && g.L != 44;
+    return size_ok && g.nE + 2 * kGuard >= 32;
+}
 
 // Candidate configurations: (residency, walkers per block, lanes per walker).
-// Fewer walkers per warp spread the chains over more SM sub-partitions and
-// let the extra lanes share the Philox work; the autotuner measures.
+// A sweep block is one warp: walkers_per_block x lanes_per_walker <= 32.
+// Fewer walkers per warp spread the chains over more SM sub-partitions and let
+// the extra lanes share the per-row work; the autotuner measures.
 std::vector<Cand> candidates(const Group &g, int residency, int wpb, int P, int smem_max)
 {
     std::vector<Cand> c;
     const bool want_g = residency == MUCA_RES_AUTO || residency == MUCA_RES_GLOBAL;
     const bool want_s = residency == MUCA_RES_AUTO || residency == MUCA_RES_SMEM;
-    const std::vector<int> Ps = !fixed_path(g.L) ? std::vector<int>{1}
-                                : P > 0          ? std::vector<int>{P}
-                                                 : std::vector<int>{1, 2, 4, 8};
+    const std::vector<int> Ps = !fixed_path(g) ? std::vector<int>{1}
+                                : P > 0        ? std::vector<int>{P}
+                                               : std::vector<int>{1, 2, 4, 8};
     if (want_g)
         for (int p : Ps) {
             if (wpb > 0) {
-                if (wpb * p % 32 == 0 && wpb * p <= 128) c.push_back({MUCA_RES_GLOBAL, wpb, p});
+                if (wpb * p == 32) c.push_back({MUCA_RES_GLOBAL, wpb, p});
             } else {
                 c.push_back({MUCA_RES_GLOBAL, 32 / p, p});
             }
         }
+    const bool want_w = residency == MUCA_RES_AUTO || residency == MUCA_RES_SPLIT;
+    if (want_w && fixed_path(g) && g.L >= 8) {
+        for (int G : {32, 16, 8}) {
+            if (wpb > 0 && wpb != G) continue;
+            if ((int64_t)ws_bytes_for(G) + 1024 <= (int64_t)smem_max)
+                c.push_back({MUCA_RES_SPLIT, G, 0});
+        }
+    } else if (residency == MUCA_RES_SPLIT) {
+        // sizes the split kernel does not cover run on the lanes-per-walker kernel
+        c.push_back({MUCA_RES_GLOBAL, 32, 1});
+    }
     if (want_s) {
-        const int64_t per = (int64_t)lattice_bytes(g.L) + (int64_t)stage_bytes_for(1);
+        const int64_t per = (int64_t)lattice_bytes(g.L) + (int64_t)stage_bytes_for(1) + 16;
         const int fit = (int)std::min<int64_t>(32, (int64_t)(smem_max - 1024) / per);
         for (int p : Ps) {
             if (wpb > 0) {
-                if (wpb <= fit && wpb * p <= 128 && (wpb * p) % 32 == 0)
-                    c.push_back({MUCA_RES_SMEM, wpb, p});
+                if (wpb <= fit && wpb * p <= 32) c.push_back({MUCA_RES_SMEM, wpb, p});
             } else {
                 const int G = std::min(fit, 32 / p);
-                if (G >= 1 && (G * p) % 32 == 0) c.push_back({MUCA_RES_SMEM, G, p});
+                if (G >= 1) c.push_back({MUCA_RES_SMEM, G, p});
             }
         }
     }
@@ -502,12 +517,13 @@ void muca_destroy(muca_ctx *ctx)
     for (auto &g : ctx->g) free_group(g);
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_groups);
-    cudaFree(ctx->d_blocks_g);
-    cudaFree(ctx->d_blocks_s);
-    if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (int k = 0; k < 3; ++k) {
+        if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+        if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
+        cudaFree(ctx->d_blocks[k]);
+    }
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
 }
 
@@ -519,9 +535,9 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
     *out = nullptr;
     if (!groups || n_groups < 1 || !opt)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: need >= 1 group and options");
-    if (opt->residency < MUCA_RES_AUTO || opt->residency > MUCA_RES_SMEM)
+    if (opt->residency < MUCA_RES_AUTO || opt->residency > MUCA_RES_SPLIT)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad residency %d", opt->residency);
-    if (opt->walkers_per_block < 0 || opt->walkers_per_block > 128)
+    if (opt->walkers_per_block < 0 || opt->walkers_per_block > 32)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad walkers_per_block %d",
                     opt->walkers_per_block);
     if (opt->lanes_per_walker != 0 && opt->lanes_per_walker != 1 && opt->lanes_per_walker != 2 &&
@@ -562,10 +578,12 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
         }                                                                                  \
     } while (0)
     {
-        CKI(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        for (int k = 0; k < 3; ++k) {
+            CKI(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
+            CKI(cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming));
+        }
         CKI(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
         CKI(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-        CKI(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
         CKI(cudaMalloc(&ctx->d_err, sizeof(int)));
         CKI(cudaMalloc(&ctx->d_groups, n_groups * sizeof(GroupDev)));
         uint32_t w0 = 0;

@@ -9,19 +9,27 @@
 // GPU design.  Every walker is a strict serial chain: site x+1 sees the
 // E_Delta and the spin that site x left behind.  Throughput is therefore
 // (number of walkers) / (latency of one chain step), and the kernel is built
-// to make that step short and to keep everything else off it.  P lanes of a
-// warp serve one walker (walker slot t / P, lane h = t % P).  A row (fixed
-// y, z) of L sites goes through these phases, staged in shared memory:
-//   1. cp.async (L2 -> shared, bypassing L1) of the NEXT row's old spins and
-//      of its four y/z neighbour rows, completing behind the current row;
+// to make that step short and to keep everything else off it.  The threshold
+// a step reads depends on the walker's current E_Delta, so a dependent load
+// sits on the chain; from L2 that load costs hundreds of cycles, from shared
+// memory a few tens.  Each walker therefore keeps a window of kRing table
+// rows around its E_Delta in shared memory (a ring indexed by row mod kRing),
+// re-centred between rows with cp.async; a group of four sites whose rows
+// might leave the window reads the global table instead (decided by a warp
+// vote, so the warp never diverges on it).
+//
+// P lanes of a warp serve one walker (walker slot t / P, lane h = t % P).
+// A row (fixed y, z) of L sites goes through these phases, staged in shared
+// memory:
+//   1. cp.async (L2 -> shared) of the NEXT row's old spins and of its four y/z
+//      neighbour rows, and of the table rows that re-centre the window;
 //   2. the Philox blocks of the row, split over the P lanes;
-//   3. per-site descriptors, split over the P lanes: for site x the two table
-//      offsets it can need (site x-1 accepted or rejected) relative to the
-//      E_Delta row of the state before site x-1, the row shift dK of its own
-//      move, and its old spin and proposal;
+//   3. per-site descriptors, split over the P lanes: for site x the table
+//      columns it can need (site x-1 accepted or rejected), the row shift of
+//      site x-1's move, and site x's own move;
 //   4. the chain, unrolled over the row: compare u with the threshold in
-//      flight, select the next site's offset, issue its load - nothing else
-//      depends on the previous step - and record the acceptance bit;
+//      flight, select the next site's address, issue its load, record the
+//      acceptance bit - nothing else depends on the previous step;
 //   5. the new spins of the row from the acceptance bits, and the energy
 //      tallies from byte dot products of old and new spins:
 //        dM = sum (N - O), dE_Delta = sum (N^2 - O^2),
@@ -29,9 +37,8 @@
 //      which equals the sum of the per-site energy changes;
 //   6. the next row's old spins and neighbour sums from the prefetched rows
 //      (its y-1 neighbour is the row just finished).
-// The threshold table (L2-resident, rows of 128 bytes) is the only memory the
-// chain touches.  Sizes with L % 4 == 0 up to 48 use this path; any other L
-// uses a plain per-site path with the same results.
+// Sizes with L % 4 == 0 up to 48 use this path; any other L uses a plain
+// per-site path with the same results.
 #include <cstdint>
 
 #include "muca_internal.h"
@@ -89,8 +96,8 @@ __device__ __forceinline__ int8_t *site_ptr(uint32_t *lat, ptrdiff_t st, int Lw,
 }
 
 __device__ void sweep_sites(uint32_t *__restrict__ lat, ptrdiff_t st, int L, int Lw,
-                            const uint32_t *__restrict__ thr0, const uint32_t *__restrict__ thrE,
-                            int e_min, uint32_t key0, uint32_t key1, uint64_t sw, Chain &c)
+                            const uint32_t *__restrict__ thrE, int e_min, uint32_t key0,
+                            uint32_t key1, uint64_t sw, Chain &c)
 {
     const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
     uint32_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
@@ -124,10 +131,8 @@ __device__ void sweep_sites(uint32_t *__restrict__ lat, ptrdiff_t st, int L, int
                 const int sp = proposal(s, word);
                 const int d = sp * sp - s * s;
                 const int dEJ = -(sp - s) * h;
-                const uint32_t t =
-                    d == 0 ? __ldg(thr0 + ((dEJ + 12) >> 1))
-                           : __ldg(thrE + (ptrdiff_t)(c.ED - e_min) * kRow + (d > 0 ? kPlus : 0) +
-                                   dEJ + 6);
+                const int col = kBlk * (d + 1) + (d == 0 ? (dEJ + 12) >> 1 : dEJ + 6);
+                const uint32_t t = __ldg(thrE + (ptrdiff_t)(c.ED - e_min) * kRow + col);
                 if ((word & 0x7FFFFFFFu) < t) {
                     *p = (int8_t)sp;
                     c.EJ += dEJ;
@@ -140,16 +145,22 @@ __device__ void sweep_sites(uint32_t *__restrict__ lat, ptrdiff_t st, int L, int
 }
 
 // ---------------------------------------------------------------------------
-// Staging area of a block in shared memory: for every walker slot (S slots),
-// fields laid out [field][index][slot] so that the lanes of different slots
-// touch consecutive words.
+// Shared memory of a block, per walker slot (S slots):
+//   staging fields laid out [field][index][slot] (lanes of different slots
+//   touch consecutive words);
+//   the table window: kRing rows of kRow words per slot, slot-major, slots
+//   kRingStride words apart (16-byte aligned, padded to spread the banks).
 // ---------------------------------------------------------------------------
 constexpr int kMaxL = 48;
 constexpr int kMaxLw = kMaxL / 4;
 constexpr int kStageWords = 8 * kMaxLw + 4 * kMaxL;  // per slot
+constexpr int kRing = 32;                            // table rows per walker window
+constexpr int kRingStride = kRing * kRow + 4;        // words per slot
+constexpr int kMargin = 8;                           // re-centre when this close to an edge
 
 struct Stage {
-    uint32_t *base;
+    uint32_t *base;  // staging fields
+    uint32_t *ring;  // table windows
     int S;
     // prefetched rows of the next row: f = 0 y-1, 1 y+1, 2 z-1, 3 z+1, 4 itself
     __device__ uint32_t *pf(int f, int j) const { return base + (f * kMaxLw + j) * S; }
@@ -157,9 +168,8 @@ struct Stage {
     __device__ uint32_t *H(int j) const { return base + (6 * kMaxLw + j) * S; }
     __device__ uint32_t *N(int j) const { return base + (7 * kMaxLw + j) * S; }
     __device__ uint32_t *rnd(int x) const { return base + (8 * kMaxLw + x) * S; }
-    __device__ int *GA(int x) const { return (int *)base + (8 * kMaxLw + kMaxL + x) * S; }
-    __device__ int *GR(int x) const { return (int *)base + (8 * kMaxLw + 2 * kMaxL + x) * S; }
-    __device__ uint32_t *AUX(int x) const { return base + (8 * kMaxLw + 3 * kMaxL + x) * S; }
+    __device__ uint32_t *AUX(int x) const { return base + (8 * kMaxLw + kMaxL + x) * S; }
+    __device__ uint32_t *win(int slot) const { return ring + (size_t)slot * kRingStride; }
 };
 
 // Where the block's walkers' lattices live: a [L*L][Lw][stride] word array
@@ -168,6 +178,43 @@ struct BlockLattice {
     uint32_t *base;
     ptrdiff_t stride;
 };
+
+// The table window of one walker: rows [lo, lo + kRing) are (or, after the
+// pending copies complete, will be) in the ring; [vlo, vhi) may be read now.
+struct Window {
+    int lo, vlo, vhi;
+};
+
+// Copy table rows [a, b) into the walker's ring (cp.async, 16-byte chunks,
+// split over the walker's P lanes).
+__device__ __forceinline__ void window_fill(uint32_t *win, const uint32_t *__restrict__ thrE,
+                                            int a, int b, int P, int h)
+{
+    constexpr int kChunks = kRow / 4;
+    const int n = (b - a) * kChunks;
+    for (int c = h; c < n; c += P) {
+        const int row = a + c / kChunks, k = c - (c / kChunks) * kChunks;
+        cp_async16(win + (row & (kRing - 1)) * kRow + 4 * k, thrE + (ptrdiff_t)row * kRow + 4 * k);
+    }
+}
+
+// Re-centre the window on row e if e came within kMargin rows of an edge.
+// Rows stay inside the table allocation [-kGuard, nE + kGuard).
+__device__ __forceinline__ void window_recentre(Window &wd, uint32_t *win,
+                                                const uint32_t *__restrict__ thrE, int e, int nE,
+                                                int P, int h)
+{
+    if (e >= wd.lo + kMargin && e < wd.lo + kRing - kMargin) return;
+    int lo = e - kRing / 2;
+    lo = max(lo, -kGuard);
+    lo = min(lo, nE + kGuard - kRing);
+    if (lo == wd.lo) return;
+    if (lo > wd.lo) window_fill(win, thrE, max(wd.lo + kRing, lo), lo + kRing, P, h);
+    else window_fill(win, thrE, lo, min(wd.lo, lo + kRing), P, h);
+    wd.vlo = max(wd.lo, lo);
+    wd.vhi = min(wd.lo, lo) + kRing;
+    wd.lo = lo;
+}
 
 // Phase 1: copy the five rows around row (y1, z1) of all the block's walkers
 // into the staging area.  In global memory the words of 4 consecutive walkers
@@ -192,7 +239,6 @@ __device__ __forceinline__ void stage_rows(const BlockLattice &bl, const Stage &
             cp_async16(sg.pf(f, j) + 4 * k,
                        bl.base + ((ptrdiff_t)row_of(f) * Lw + j) * bl.stride + 4 * k);
         }
-        cp_async_commit();
     } else {
         for (int c = tid; c < 5 * Lw * nw; c += nthreads) {
             const int f = c / (Lw * nw), rem = c - f * (Lw * nw);
@@ -217,22 +263,89 @@ __device__ __forceinline__ void build_row(const Stage &sg, int slot, int P, int 
     }
 }
 
+// Descriptor of site x (phase 3), one word:
+//   bits 0..5   column if site x-1 was accepted, 6..11 if it was rejected
+//   bits 12..13 row shift of site x-1's move, plus 1
+//   bits 14..15 d = s'^2 - s^2 of site x's move, plus 1
+//   bits 16..17 s' + 1, bits 18..19 s + 1, bit 20 set iff s' > s
+__device__ __forceinline__ int dsc_colA(uint32_t a) { return (int)(a & 63u); }
+__device__ __forceinline__ int dsc_colR(uint32_t a) { return (int)((a >> 6) & 63u); }
+__device__ __forceinline__ int dsc_dprev(uint32_t a) { return (int)((a >> 12) & 3u) - 1; }
+__device__ __forceinline__ int dsc_d(uint32_t a) { return (int)((a >> 14) & 3u) - 1; }
+__device__ __forceinline__ int dsc_sp(uint32_t a) { return (int)((a >> 16) & 3u) - 1; }
+__device__ __forceinline__ int dsc_s(uint32_t a) { return (int)((a >> 18) & 3u) - 1; }
+__device__ __forceinline__ int dsc_k(uint32_t a) { return (a >> 20) & 1u ? 1 : -1; }
+
+// State of the chain of one walker inside a row.
+struct ChainState {
+    int e;       // table row of the current E_Delta
+    uint32_t t;  // threshold in flight for the current site
+    uint32_t u;  // its uniform draw
+    uint32_t a;  // its descriptor
+    int corr;    // column correction of site L-1 (its x+1 is the new site 0)
+};
+
+// One step of the chain for site x (x + 1 < L: also issues the load of site
+// x + 1).  FAST reads the walker's table window, otherwise the global table.
+template <int L, bool FAST>
+__device__ __forceinline__ void chain_step(int x, ChainState &cs, uint32_t (&accb)[(L + 31) / 32],
+                                           const Stage &sg, int slot, const uint32_t *win,
+                                           const uint32_t *__restrict__ thrE)
+{
+    uint32_t a1 = 0u, u1 = 0u;
+    int iA = 0, iR = 0;
+    if (x + 1 < L) {
+        a1 = sg.AUX(x + 1)[slot];
+        u1 = sg.rnd(x + 1)[slot] & 0x7FFFFFFFu;
+        int cA = dsc_colA(a1), cR = dsc_colR(a1);
+        if (x + 1 == L - 1) {
+            cA += cs.corr;
+            cR += cs.corr;
+        }
+        const int eA = cs.e + dsc_dprev(a1);
+        if (FAST) {
+            iA = (eA & (kRing - 1)) * kRow + cA;
+            iR = (cs.e & (kRing - 1)) * kRow + cR;
+        } else {
+            iA = eA * kRow + cA;
+            iR = cs.e * kRow + cR;
+        }
+    }
+    const bool acc = cs.u < cs.t;
+    if (x + 1 < L) cs.t = FAST ? win[acc ? iA : iR] : __ldg(thrE + (acc ? iA : iR));
+    if (acc) {
+        cs.e += dsc_d(cs.a);
+        accb[x >> 5] |= 1u << (x & 31);
+    }
+    if (x == 0) {
+        const int kL = dsc_k(sg.AUX(L - 1)[slot]);
+        cs.corr = acc ? -kL * (dsc_sp(cs.a) - dsc_s(cs.a)) : 0;
+    }
+    cs.a = a1;
+    cs.u = u1;
+}
+
 // The unrolled row path (L % 4 == 0).  Threads of the block run this in lock
 // step: all P lanes of a walker execute the chain on the same data.
 template <int L, bool GLOBAL>
 __device__ __forceinline__ void sweep_rows(const BlockLattice &bl, const Stage &sg,
-                                           const uint32_t *__restrict__ thrE, int off0,
-                                           uint32_t key0, uint32_t key1, uint64_t sw, int &rowoff,
-                                           Chain &c, int slot, int P, int h, int nw, int tid,
-                                           int nthreads, unsigned amask)
+                                           const uint32_t *__restrict__ thrE, int nE,
+                                           uint32_t key0, uint32_t key1, uint64_t sw, int &e,
+                                           Window &wd, Chain &c, int slot, int P, int h, int nw,
+                                           int tid, int nthreads, unsigned amask)
 {
     static_assert(L % 4 == 0 && L <= kMaxL, "row path needs L % 4 == 0, L <= 48");
     constexpr int Lw = L / 4, R = L * L, NB = (L + 31) / 32;
     const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
     uint32_t *const own = bl.base + slot;  // this walker's word 0
+    uint32_t *const win = sg.win(slot);
     // the neighbourhood of row 0
     stage_rows<L, GLOBAL>(bl, sg, 0, 0, nw, tid, nthreads);
-    if (GLOBAL) cp_async_wait_all();
+    window_recentre(wd, win, thrE, e, nE, P, h);
+    cp_async_commit();
+    cp_async_wait_all();
+    wd.vlo = wd.lo;
+    wd.vhi = wd.lo + kRing;
     __syncwarp(amask);
     build_row<L>(sg, slot, P, h, false);
     __syncwarp(amask);
@@ -246,8 +359,10 @@ __device__ __forceinline__ void sweep_rows(const BlockLattice &bl, const Stage &
             z1 = z + 1;
         }
         const bool more = r + 1 < R;
-        // 1. the next row's neighbourhood
+        // 1. the next row's neighbourhood; the table window
         if (more) stage_rows<L, GLOBAL>(bl, sg, y1, z1, nw, tid, nthreads);
+        window_recentre(wd, win, thrE, e, nE, P, h);
+        cp_async_commit();
         // 2. Philox blocks of this row (site i = r L + 4 j is block r Lw + j)
         for (int j = h; j < Lw; j += P) {
             const uint4 v =
@@ -264,67 +379,51 @@ __device__ __forceinline__ void sweep_rows(const BlockLattice &bl, const Stage &
             const int xr = (x + 1 == L) ? 0 : x + 1;  // old value of x = 0 for x = L-1;
             const int right = sbyte(sg.O(xr >> 2)[slot], xr & 3);  // corrected in the chain
             const int base = sbyte(sg.H(x >> 2)[slot], x & 3) + right;
-            const uint32_t word = sg.rnd(x)[slot];
-            const int sp = proposal(s, word);
+            const int sp = proposal(s, sg.rnd(x)[slot]);
             const int d = sp * sp - s * s;
             const int k = sp > s ? 1 : -1;
-            const bool m = (d != 0);  // the threshold sits in the E_Delta row
-            const int c0 = (d > 0 ? kPlus + 6 : 6) - k * base;
-            int ps, psp, pdK;
+            const int c0 = kBlk * (d + 1) + 6 - k * base;
+            int ps, psp;
             if (x == 0) {
                 ps = psp = sbyte(sg.O(Lw - 1)[slot], 3);  // x - 1 of x = 0: old x = L - 1
-                pdK = 0;
             } else {
                 ps = sbyte(sg.O((x - 1) >> 2)[slot], (x - 1) & 3);
                 psp = proposal(ps, sg.rnd(x - 1)[slot]);
-                pdK = (psp * psp - ps * ps) * kRow;
             }
-            sg.GA(x)[slot] = (m ? pdK : off0) + c0 - k * psp;
-            sg.GR(x)[slot] = (m ? 0 : off0) + c0 - k * ps;
-            sg.AUX(x)[slot] = (m ? 1u : 0u) | (k > 0 ? 4u : 0u) | ((uint32_t)(d * kRow & 0xFF) << 8) |
-                              ((uint32_t)(sp & 0xFF) << 16) | ((uint32_t)(s & 0xFF) << 24);
+            const int pd = (x == 0) ? 0 : psp * psp - ps * ps;
+            sg.AUX(x)[slot] = (uint32_t)(c0 - k * psp) | ((uint32_t)(c0 - k * ps) << 6) |
+                              ((uint32_t)(pd + 1) << 12) | ((uint32_t)(d + 1) << 14) |
+                              ((uint32_t)(sp + 1) << 16) | ((uint32_t)(s + 1) << 18) |
+                              (k > 0 ? (1u << 20) : 0u);
         }
         __syncwarp(amask);
-        // 4. the chain
+        // 4. the chain, in groups of four sites
         uint32_t accb[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) accb[b] = 0u;
+        ChainState cs;
+        cs.e = e;
+        cs.corr = 0;
+        cs.a = sg.AUX(0)[slot];
+        cs.u = sg.rnd(0)[slot] & 0x7FFFFFFFu;
         {
-            uint32_t aux = sg.AUX(0)[slot];
-            uint32_t t = __ldg(thrE + ((aux & 1u) ? rowoff : 0) + sg.GR(0)[slot]);
-            uint32_t u = sg.rnd(0)[slot] & 0x7FFFFFFFu;
-            int corr = 0;
+            // the loads a group can issue stay within 4 rows of the group's first row
+            const bool fast = __all_sync(amask, e - 4 >= wd.vlo && e + 4 < wd.vhi);
+            const int col0 = dsc_colR(cs.a);
+            cs.t = fast ? win[(e & (kRing - 1)) * kRow + col0] : __ldg(thrE + e * kRow + col0);
+        }
 #pragma unroll
-            for (int x = 0; x < L; ++x) {
-                const int dK = sbyte(aux, 1);
-                uint32_t aux1 = 0u, u1 = 0u;
-                int IA = 0, IR = 0;
-                if (x + 1 < L) {
-                    aux1 = sg.AUX(x + 1)[slot];
-                    const int mo = (aux1 & 1u) ? rowoff : 0;
-                    IA = mo + sg.GA(x + 1)[slot];
-                    IR = mo + sg.GR(x + 1)[slot];
-                    if (x + 1 == L - 1) {
-                        IA += corr;
-                        IR += corr;
-                    }
-                    u1 = sg.rnd(x + 1)[slot] & 0x7FFFFFFFu;
-                }
-                const bool acc = u < t;
-                if (x + 1 < L) t = __ldg(thrE + (acc ? IA : IR));
-                if (acc) {
-                    rowoff += dK;
-                    accb[x >> 5] |= 1u << (x & 31);
-                }
-                if (x == 0) {
-                    // x + 1 of x = L - 1 is the new value of x = 0
-                    const int kL = (sg.AUX(L - 1)[slot] & 4u) ? 1 : -1;
-                    corr = acc ? -kL * (sbyte(aux, 2) - sbyte(aux, 3)) : 0;
-                }
-                aux = aux1;
-                u = u1;
+        for (int x0 = 0; x0 < L; x0 += 4) {
+            const bool fast = __all_sync(amask, cs.e - 4 >= wd.vlo && cs.e + 4 < wd.vhi);
+            if (fast) {
+#pragma unroll
+                for (int x = x0; x < x0 + 4; ++x) chain_step<L, true>(x, cs, accb, sg, slot, win, thrE);
+            } else {
+#pragma unroll
+                for (int x = x0; x < x0 + 4; ++x) chain_step<L, false>(x, cs, accb, sg, slot, win, thrE);
             }
         }
+        e = cs.e;
         // 5. new spins, their store, the tallies
         for (int j = h; j < Lw; j += P) {
             uint32_t nwd = 0u;
@@ -333,7 +432,7 @@ __device__ __forceinline__ void sweep_rows(const BlockLattice &bl, const Stage &
                 const int x = 4 * j + q;
                 const uint32_t a = sg.AUX(x)[slot];
                 const uint32_t bits = (NB == 1 || x < 32) ? accb[0] : accb[NB - 1];
-                const int sn = ((bits >> (x & 31)) & 1u) ? sbyte(a, 2) : sbyte(a, 3);
+                const int sn = ((bits >> (x & 31)) & 1u) ? dsc_sp(a) : dsc_s(a);
                 nwd |= (uint32_t)(sn & 0xFF) << (8 * q);
             }
             sg.N(j)[slot] = nwd;
@@ -359,12 +458,12 @@ __device__ __forceinline__ void sweep_rows(const BlockLattice &bl, const Stage &
         c.EJ += dJ;
         c.M += dM;
         c.ED += dD;
-        // 6. the next row
-        if (more) {
-            if (GLOBAL) cp_async_wait_all();
-            __syncwarp(amask);
-            build_row<L>(sg, slot, P, h, !wrap);
-        }
+        // 6. the next row; the window copies are complete from here on
+        cp_async_wait_all();
+        wd.vlo = wd.lo;
+        wd.vhi = wd.lo + kRing;
+        __syncwarp(amask);
+        if (more) build_row<L>(sg, slot, P, h, !wrap);
         __syncwarp(amask);
         y = y1;
         z = z1;
@@ -374,8 +473,9 @@ __device__ __forceinline__ void sweep_rows(const BlockLattice &bl, const Stage &
 template <bool RECORD, bool GLOBAL>
 __device__ __forceinline__ void run_block(const GroupDev &g, const BlockDesc &bd,
                                           uint32_t *__restrict__ lat_block, ptrdiff_t st,
-                                          uint32_t *__restrict__ stage, uint32_t seed,
-                                          uint64_t sweep0, int n_sweeps, int64_t ts_pos)
+                                          uint32_t *__restrict__ stage, uint32_t *__restrict__ ring,
+                                          uint32_t seed, uint64_t sweep0, int n_sweeps,
+                                          int64_t ts_pos)
 {
     const int P = bd.P, tid = (int)threadIdx.x, slot = tid / P, h = tid - slot * P;
     const bool active = slot < bd.nw;
@@ -391,17 +491,19 @@ __device__ __forceinline__ void run_block(const GroupDev &g, const BlockDesc &bd
     c.ED = g.tal[g.Wpad + w];
     c.M = g.tal[2 * g.Wpad + w];
     const BlockLattice bl{lat_block, st};
-    const Stage sg{stage, bd.S};
+    const Stage sg{stage, ring, bd.S};
     const int nthreads = bd.nw * P;
-    const int off0 = (int)(g.thr0 - g.thrE);
+    // an empty window: the first re-centre fills it completely
+    Window wd{-(1 << 20), 0, 0};
     for (int k = 0; k < n_sweeps; ++k) {
         const uint64_t sw = sweep0 + (uint64_t)k;
-        int rowoff = (c.ED - g.e_min) * kRow;
-        switch (g.L) {
-#define MUCA_ROWS(LL)                                                                          \
-    case LL:                                                                                   \
-        sweep_rows<LL, GLOBAL>(bl, sg, g.thrE, off0, key0, seed, sw, rowoff, c, slot, P, h,  \
-                               bd.nw, tid, nthreads, amask);                                   \
+        int e = c.ED - g.e_min;
+        // the row path needs a table of at least one window
+        switch (g.nE + 2 * kGuard >= kRing ? g.L : 0) {
+#define MUCA_ROWS(LL)                                                                           \
+    case LL:                                                                                    \
+        sweep_rows<LL, GLOBAL>(bl, sg, g.thrE, g.nE, key0, seed, sw, e, wd, c, slot, P, h,    \
+                               bd.nw, tid, nthreads, amask);                                    \
         break;
             MUCA_ROWS(4)
             MUCA_ROWS(8)
@@ -414,8 +516,7 @@ __device__ __forceinline__ void run_block(const GroupDev &g, const BlockDesc &bd
             MUCA_ROWS(48)
 #undef MUCA_ROWS
             default:
-                sweep_sites(lat_block + slot, st, g.L, g.Lw, g.thr0, g.thrE, g.e_min, key0, seed,
-                            sw, c);
+                sweep_sites(lat_block + slot, st, g.L, g.Lw, g.thrE, g.e_min, key0, seed, sw, c);
                 break;
         }
         if (h == 0) {
@@ -435,25 +536,27 @@ __device__ __forceinline__ void run_block(const GroupDev &g, const BlockDesc &bd
     }
 }
 
-// Thread t of a block serves walker slot t / P as lane t % P.
+// A block is one warp; thread t serves walker slot t / P as lane t % P.
+// Dynamic shared memory: the staging area of S slots, then their table windows.
 template <bool RECORD>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32)
 sweep_global_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restrict__ blocks,
                     uint32_t seed, uint64_t sweep0, int n_sweeps, int64_t ts_pos)
 {
-    extern __shared__ __align__(16) uint32_t s_stage[];
+    extern __shared__ __align__(16) uint32_t s_dyn[];
     const BlockDesc bd = blocks[blockIdx.x];
     const GroupDev g = groups[bd.group];
-    run_block<RECORD, true>(g, bd, g.spins + bd.w0, g.Wpad, s_stage, seed, sweep0, n_sweeps,
+    uint32_t *ring = s_dyn + (size_t)bd.S * kStageWords;
+    run_block<RECORD, true>(g, bd, g.spins + bd.w0, g.Wpad, s_dyn, ring, seed, sweep0, n_sweeps,
                             ts_pos);
 }
 
 // Shared-memory-resident variant: the block's walkers keep their lattices in
 // shared memory as a [L * L][Lw][S] word tile for the whole launch, read from
 // and written back to the global array at the start and the end; the staging
-// area follows the tile.
+// area and the table windows follow the tile.  A block is one warp.
 template <bool RECORD>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32)
 sweep_smem_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restrict__ blocks,
                   uint32_t seed, uint64_t sweep0, int n_sweeps, int64_t ts_pos)
 {
@@ -467,12 +570,369 @@ sweep_smem_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restri
         s_lat[idx] = (c < bd.nw) ? g.spins[(ptrdiff_t)wd * g.Wpad + bd.w0 + c] : 0u;
     }
     __syncthreads();
-    run_block<RECORD, false>(g, bd, s_lat, S, s_lat + (size_t)nwords * S, seed, sweep0, n_sweeps,
-                             ts_pos);
+    // the tile is padded to a 16-byte boundary
+    uint32_t *stage = s_lat + (((size_t)nwords * S + 3) & ~(size_t)3);
+    uint32_t *ring = stage + (size_t)S * kStageWords;
+    run_block<RECORD, false>(g, bd, s_lat, S, stage, ring, seed, sweep0, n_sweeps, ts_pos);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nwords * S; idx += blockDim.x) {
         const int wd = idx / S, c = idx - wd * S;
         if (c < bd.nw) g.spins[(ptrdiff_t)wd * g.Wpad + bd.w0 + c] = s_lat[idx];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-specialised variant (global lattice, L % 4 == 0 up to 48).  A block is
+// kWsWarps warps: warp 0 runs the chains of the block's G walkers (one lane
+// each) and nothing else; warps 1..3 ("helpers") prepare the next row and
+// finish the previous one, so that the per-row work of the phases overlaps
+// the chain instead of adding to it:
+//   helpers, iteration i:  wait until the chain finished row i-2; store its new
+//     spins and add its energy changes; build the old spins and neighbour sums
+//     of row i from the staged rows, draw its Philox words, write its site
+//     descriptors; release row i to the chain; stage the neighbourhood of row
+//     i+1 (cp.async).
+//   chain, row r:  wait for row r; complete the table-window copies issued a
+//     row ago and re-centre the window; run the chain; write the row's new
+//     spins to shared memory; release the descriptor buffer.
+// The only input of row r+1 that depends on row r's outcome is the y-1
+// neighbour: the helpers leave it out of the neighbour sums of non-wrapping
+// rows, and the chain adds -k N_r(x) to the column of site x itself.
+// Buffers: descriptors and random words double-buffered by row parity, old
+// spins / neighbour sums / new spins triple-buffered by row mod 3.  Named
+// barriers: ready[b] (helpers arrive, chain waits), free[b] (chain arrives,
+// helpers wait), and one among the helpers.
+// ---------------------------------------------------------------------------
+constexpr int kWsWarps = 4;
+constexpr int kWsThreads = 32 * kWsWarps;
+constexpr int kWsHelp = kWsThreads - 32;
+constexpr int kBarReady = 1, kBarFree = 3, kBarHelp = 5;
+// shared words per walker slot
+constexpr int kWsWords = kRingStride + 4 * kMaxL + 9 * kMaxLw + 5 * kMaxLw + 2;
+
+__device__ __forceinline__ void bar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+struct WsSmem {
+    uint32_t *base;
+    int G;
+    __device__ uint32_t *win(int slot) const { return base + (size_t)slot * kRingStride; }
+    __device__ uint32_t *rest() const { return base + (size_t)G * kRingStride; }
+    __device__ uint32_t *desc(int b, int x) const { return rest() + ((b * kMaxL) + x) * G; }
+    __device__ uint32_t *rnd(int b, int x) const { return rest() + ((2 + b) * kMaxL + x) * G; }
+    __device__ uint32_t *O(int b, int j) const { return rest() + 4 * kMaxL * G + (b * kMaxLw + j) * G; }
+    __device__ uint32_t *H(int b, int j) const
+    {
+        return rest() + 4 * kMaxL * G + ((3 + b) * kMaxLw + j) * G;
+    }
+    __device__ uint32_t *N(int b, int j) const
+    {
+        return rest() + 4 * kMaxL * G + ((6 + b) * kMaxLw + j) * G;
+    }
+    __device__ uint32_t *pf(int f, int j) const
+    {
+        return rest() + 4 * kMaxL * G + ((9 + f) * kMaxLw + j) * G;
+    }
+    __device__ int *tal(int slot) const
+    {
+        return (int *)(rest() + 4 * kMaxL * G + 14 * kMaxLw * G) + 2 * slot;
+    }
+};
+
+// Helpers: the five rows around row (y1, z1) of the block's walkers into pf.
+template <int L>
+__device__ __forceinline__ void ws_stage(const WsSmem &sm, const uint32_t *lat, ptrdiff_t st,
+                                         int y1, int z1, int ht)
+{
+    constexpr int Lw = L / 4;
+    const int r_ym = z1 * L + (y1 == 0 ? L - 1 : y1 - 1), r_yp = z1 * L + (y1 + 1 == L ? 0 : y1 + 1);
+    const int r_zm = (z1 == 0 ? L - 1 : z1 - 1) * L + y1, r_zp = (z1 + 1 == L ? 0 : z1 + 1) * L + y1;
+    const int r_self = z1 * L + y1;
+    const int lg = __ffs(sm.G >> 2) - 1;  // chunks of 4 walkers per word: G / 4 (a power of 2)
+    const int nch = sm.G >> 2;
+    for (int c = ht; c < 5 * Lw * nch; c += kWsHelp) {
+        const int fj = c >> lg, k = c & (nch - 1);
+        const int f = fj / Lw, j = fj - f * Lw;
+        const int row = f == 0 ? r_ym : f == 1 ? r_yp : f == 2 ? r_zm : f == 3 ? r_zp : r_self;
+        cp_async16(sm.pf(f, j) + 4 * k, lat + ((ptrdiff_t)row * Lw + j) * st + 4 * k);
+    }
+    cp_async_commit();
+}
+
+template <int L, bool RECORD>
+__device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd,
+                                          const WsSmem &sm, uint32_t seed, uint64_t sweep0,
+                                          int n_sweeps, int64_t ts_pos)
+{
+    constexpr int Lw = L / 4, R = L * L, NB = (L + 31) / 32;
+    const int tid = (int)threadIdx.x;
+    const int G = sm.G, nw = bd.nw;
+    uint32_t *const lat = g.spins + bd.w0;  // word (row, j) of slot s: lat[(row Lw + j) Wpad + s]
+    const ptrdiff_t st = g.Wpad;
+    const uint32_t *__restrict__ thrE = g.thrE;
+    if (tid < 32) {
+        // ------------------------------------------------------------ chain warp
+        const int slot = tid;
+        const bool active = slot < nw;
+        const unsigned amask = __ballot_sync(0xFFFFFFFFu, active);
+        const unsigned lead_mask = amask;
+        const int w = bd.w0 + slot;
+        Chain c{0, 0, 0};
+        if (active) {
+            c.EJ = g.tal[w];
+            c.ED = g.tal[g.Wpad + w];
+            c.M = g.tal[2 * g.Wpad + w];
+        }
+        Window wd{-(1 << 20), 0, 0};
+        uint32_t *const win = sm.win(slot < G ? slot : 0);
+        for (int k = 0; k < n_sweeps; ++k) {
+            int e = c.ED - g.e_min;
+            int y = 0;
+#pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+                bar_sync(kBarReady + (r & 1), kWsThreads);
+                cp_async_wait_all();
+                wd.vlo = wd.lo;
+                wd.vhi = wd.lo + kRing;
+                if (active) window_recentre(wd, win, thrE, e, g.nE, 1, 0);
+                cp_async_commit();
+                if (active) {
+                    const int b = r & 1;
+                    const bool ycorr = (y != 0);  // the y-1 row is the one just finished
+                    const int nprev = (r + 2) % 3;
+                    uint32_t accb[NB];
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) accb[q] = 0u;
+                    ChainState cs;
+                    cs.e = e;
+                    cs.corr = 0;
+                    cs.a = sm.desc(b, 0)[slot];
+                    cs.u = sm.rnd(b, 0)[slot] & 0x7FFFFFFFu;
+                    {
+                        const bool fast = __all_sync(amask, e - 4 >= wd.vlo && e + 4 < wd.vhi);
+                        const int col0 = dsc_colR(cs.a) -
+                                         (ycorr ? dsc_k(cs.a) * sbyte(sm.N(nprev, 0)[slot], 0) : 0);
+                        cs.t = fast ? win[(e & (kRing - 1)) * kRow + col0]
+                                    : __ldg(thrE + e * kRow + col0);
+                    }
+#pragma unroll 1
+                    for (int x0 = 0; x0 < L; x0 += 4) {
+                        const bool fast =
+                            __all_sync(amask, cs.e - 4 >= wd.vlo && cs.e + 4 < wd.vhi);
+                        // y-1 neighbours (new) of sites x0+1 .. x0+4
+                        const uint32_t n0 = ycorr ? sm.N(nprev, x0 >> 2)[slot] : 0u;
+                        const uint32_t n1 =
+                            (ycorr && x0 + 4 < L) ? sm.N(nprev, (x0 >> 2) + 1)[slot] : 0u;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int x = x0 + q;
+                            uint32_t a1 = 0u, u1 = 0u;
+                            int iA = 0, iR = 0;
+                            if (x + 1 < L) {
+                                a1 = sm.desc(b, x + 1)[slot];
+                                u1 = sm.rnd(b, x + 1)[slot] & 0x7FFFFFFFu;
+                                const int ny = (q < 3) ? sbyte(n0, q + 1) : sbyte(n1, 0);
+                                int cc = -dsc_k(a1) * ny;
+                                if (x + 1 == L - 1) cc += cs.corr;
+                                const int cA = dsc_colA(a1) + cc, cR = dsc_colR(a1) + cc;
+                                const int eA = cs.e + dsc_dprev(a1);
+                                if (fast) {
+                                    iA = (eA & (kRing - 1)) * kRow + cA;
+                                    iR = (cs.e & (kRing - 1)) * kRow + cR;
+                                } else {
+                                    iA = eA * kRow + cA;
+                                    iR = cs.e * kRow + cR;
+                                }
+                            }
+                            const bool acc = cs.u < cs.t;
+                            if (x + 1 < L)
+                                cs.t = fast ? win[acc ? iA : iR] : __ldg(thrE + (acc ? iA : iR));
+                            if (acc) {
+                                cs.e += dsc_d(cs.a);
+                                if (NB == 1 || x < 32) accb[0] |= 1u << (x & 31);
+                                else accb[NB - 1] |= 1u << (x & 31);
+                            }
+                            if (x == 0) {
+                                const int kL = dsc_k(sm.desc(b, L - 1)[slot]);
+                                cs.corr = acc ? -kL * (dsc_sp(cs.a) - dsc_s(cs.a)) : 0;
+                            }
+                            cs.a = a1;
+                            cs.u = u1;
+                        }
+                    }
+                    e = cs.e;
+                    // the row's new spins
+#pragma unroll 1
+                    for (int j = 0; j < Lw; ++j) {
+                        uint32_t nwd = 0u;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int x = 4 * j + q;
+                            const uint32_t a = sm.desc(b, x)[slot];
+                            const uint32_t bits = (NB == 1 || x < 32) ? accb[0] : accb[NB - 1];
+                            const int sn = ((bits >> (x & 31)) & 1u) ? dsc_sp(a) : dsc_s(a);
+                            nwd |= (uint32_t)(sn & 0xFF) << (8 * q);
+                        }
+                        sm.N(r % 3, j)[slot] = nwd;
+                    }
+                }
+                __syncwarp();
+                bar_arrive(kBarFree + (r & 1), kWsThreads);
+                y = (y + 1 == L) ? 0 : y + 1;
+            }
+            c.ED = e + g.e_min;
+            __syncthreads();  // the helpers' tallies of this sweep are complete
+            if (active) {
+                c.EJ += sm.tal(slot)[0];
+                c.M += sm.tal(slot)[1];
+                sm.tal(slot)[0] = 0;
+                sm.tal(slot)[1] = 0;
+                hist_add(g.hist, c.ED - g.e_min, lead_mask);
+                if (RECORD) {
+                    int32_t *o = g.ts + (ts_pos + k) * 3 * (int64_t)g.W + w;
+                    o[0] = c.EJ;
+                    o[g.W] = c.ED;
+                    o[2 * g.W] = c.M;
+                }
+            }
+            __syncthreads();  // tallies cleared before the helpers add again
+        }
+        if (active) {
+            g.tal[w] = c.EJ;
+            g.tal[g.Wpad + w] = c.ED;
+            g.tal[2 * g.Wpad + w] = c.M;
+        }
+    } else {
+        // ------------------------------------------------------------ helpers
+        const int ht = tid - 32;
+        for (int k = 0; k < n_sweeps; ++k) {
+            const uint64_t sw = sweep0 + (uint64_t)k;
+            const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
+            ws_stage<L>(sm, lat, st, 0, 0, ht);
+#pragma unroll 1
+            for (int i = 0; i < R + 2; ++i) {
+                if (i >= 2) bar_sync(kBarFree + (i & 1), kWsThreads);
+                if (i >= 2) {
+                    // finish row jr = i - 2: store its new spins, add its energy changes
+                    const int jr = i - 2;
+                    const int yj = jr % L;
+                    const bool nonwrap = (yj != 0);
+                    const int bj = jr % 3, bp = (jr + 2) % 3;
+                    for (int it = ht; it < Lw * nw; it += kWsHelp) {
+                        const int j = it / nw, slot = it - j * nw;
+                        const uint32_t N0 = sm.N(bj, j)[slot], O0 = sm.O(bj, j)[slot];
+                        const int j1 = (j + 1 == Lw) ? 0 : j + 1;
+                        const uint32_t n1 = __funnelshift_r(N0, sm.N(bj, j1)[slot], 8);
+                        const uint32_t o1 = __funnelshift_r(O0, sm.O(bj, j1)[slot], 8);
+                        uint32_t Hw = sm.H(bj, j)[slot];
+                        if (nonwrap) Hw = __vadd4(Hw, sm.N(bp, j)[slot]);
+                        int dJ = -__dp4a((int)__vsub4(N0, O0), (int)Hw, 0);
+                        dJ -= __dp4a((int)N0, (int)n1, 0) - __dp4a((int)O0, (int)o1, 0);
+                        const int dM = __dp4a((int)N0, 0x01010101, 0) - __dp4a((int)O0, 0x01010101, 0);
+                        if (dJ) atomicAdd(sm.tal(slot), dJ);
+                        if (dM) atomicAdd(sm.tal(slot) + 1, dM);
+                        lat[((ptrdiff_t)jr * Lw + j) * st + slot] = N0;
+                    }
+                }
+                if (i < R) {
+                    // prepare row i
+                    const int yi = i % L;
+                    const bool wrap = (yi == 0);
+                    const int bo = i % 3, b = i & 1;
+                    cp_async_wait_all();
+                    bar_sync(kBarHelp, kWsHelp);
+                    for (int it = ht; it < Lw * nw; it += kWsHelp) {
+                        const int j = it / nw, slot = it - j * nw;
+                        sm.O(bo, j)[slot] = sm.pf(4, j)[slot];
+                        uint32_t Hw = __vadd4(sm.pf(1, j)[slot],
+                                              __vadd4(sm.pf(2, j)[slot], sm.pf(3, j)[slot]));
+                        if (wrap) Hw = __vadd4(Hw, sm.pf(0, j)[slot]);
+                        sm.H(bo, j)[slot] = Hw;
+                    }
+                    for (int it = ht; it < Lw * nw; it += kWsHelp) {
+                        const int j = it / nw, slot = it - j * nw;
+                        const uint4 v = philox4x32_10(make_uint4((uint32_t)(i * Lw + j), slo, shi, 0u),
+                                                      g.walker0 + (uint32_t)(bd.w0 + slot), seed);
+                        sm.rnd(b, 4 * j)[slot] = v.x;
+                        sm.rnd(b, 4 * j + 1)[slot] = v.y;
+                        sm.rnd(b, 4 * j + 2)[slot] = v.z;
+                        sm.rnd(b, 4 * j + 3)[slot] = v.w;
+                    }
+                    bar_sync(kBarHelp, kWsHelp);
+                    for (int it = ht; it < L * nw; it += kWsHelp) {
+                        const int x = it / nw, slot = it - x * nw;
+                        const int s = sbyte(sm.O(bo, x >> 2)[slot], x & 3);
+                        const int xr = (x + 1 == L) ? 0 : x + 1;  // old x = 0 for x = L - 1,
+                        const int right = sbyte(sm.O(bo, xr >> 2)[slot], xr & 3);  // corrected later
+                        const int base = sbyte(sm.H(bo, x >> 2)[slot], x & 3) + right;
+                        const int sp = proposal(s, sm.rnd(b, x)[slot]);
+                        const int d = sp * sp - s * s;
+                        const int kk = sp > s ? 1 : -1;
+                        const int c0 = kBlk * (d + 1) + 6 - kk * base;
+                        int ps, psp;
+                        if (x == 0) {
+                            ps = psp = sbyte(sm.O(bo, Lw - 1)[slot], 3);
+                        } else {
+                            ps = sbyte(sm.O(bo, (x - 1) >> 2)[slot], (x - 1) & 3);
+                            psp = proposal(ps, sm.rnd(b, x - 1)[slot]);
+                        }
+                        const int pd = (x == 0) ? 0 : psp * psp - ps * ps;
+                        sm.desc(b, x)[slot] =
+                            (uint32_t)(c0 - kk * psp) | ((uint32_t)(c0 - kk * ps) << 6) |
+                            ((uint32_t)(pd + 1) << 12) | ((uint32_t)(d + 1) << 14) |
+                            ((uint32_t)(sp + 1) << 16) | ((uint32_t)(s + 1) << 18) |
+                            (kk > 0 ? (1u << 20) : 0u);
+                    }
+                    bar_arrive(kBarReady + b, kWsThreads);
+                }
+                if (i + 1 < R) {
+                    // the neighbourhood of row i + 1 (all stores of finished rows are done)
+                    bar_sync(kBarHelp, kWsHelp);
+                    const int y1 = (i + 1) % L, z1 = (i + 1) / L;
+                    ws_stage<L>(sm, lat, st, y1, z1, ht);
+                }
+            }
+            __syncthreads();
+            __syncthreads();
+        }
+    }
+}
+
+template <bool RECORD>
+__global__ void __launch_bounds__(kWsThreads)
+sweep_ws_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restrict__ blocks,
+                uint32_t seed, uint64_t sweep0, int n_sweeps, int64_t ts_pos)
+{
+    extern __shared__ __align__(16) uint32_t s_ws[];
+    const BlockDesc bd = blocks[blockIdx.x];
+    const GroupDev g = groups[bd.group];
+    const WsSmem sm{s_ws, bd.S};
+    if (threadIdx.x < (unsigned)bd.S) {
+        sm.tal(threadIdx.x)[0] = 0;
+        sm.tal(threadIdx.x)[1] = 0;
+    }
+    __syncthreads();
+    switch (g.L) {
+#define MUCA_WS(LL)                                                           \
+    case LL: ws_sweeps<LL, RECORD>(g, bd, sm, seed, sweep0, n_sweeps, ts_pos); \
+        break;
+        MUCA_WS(8)
+        MUCA_WS(12)
+        MUCA_WS(16)
+        MUCA_WS(20)
+        MUCA_WS(24)
+        MUCA_WS(28)
+        MUCA_WS(32)
+        MUCA_WS(48)
+#undef MUCA_WS
+        default: break;
     }
 }
 
@@ -556,9 +1016,15 @@ cudaError_t launch_energies(const GroupDev &g, int mode, int *err, cudaStream_t 
 
 size_t lattice_bytes(int L) { return (size_t)L * L * ((L + 3) / 4) * 4; }
 
-size_t stage_bytes_for(int slots) { return (size_t)slots * kStageWords * sizeof(uint32_t); }
+size_t stage_bytes_for(int slots)
+{
+    return (size_t)slots * (kStageWords + kRingStride) * sizeof(uint32_t);
+}
 
-size_t smem_bytes_for(int L, int walkers) { return lattice_bytes(L) * (size_t)walkers; }
+size_t smem_bytes_for(int L, int walkers)
+{
+    return ((lattice_bytes(L) * (size_t)walkers + 15) / 16) * 16;
+}
 
 int max_smem_per_block()
 {
@@ -577,6 +1043,42 @@ cudaError_t prepare_smem_kernel(size_t smem_bytes)
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(sweep_smem_kernel<false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+cudaError_t prepare_global_kernel(size_t smem_bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(sweep_global_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_global_kernel<false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
+size_t ws_bytes_for(int slots) { return (size_t)slots * kWsWords * sizeof(uint32_t); }
+
+cudaError_t prepare_ws_kernel(size_t smem_bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(sweep_ws_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(sweep_ws_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes);
+}
+
+cudaError_t launch_sweeps_ws(const GroupDev *groups_dev, const BlockDesc *blocks_dev, int n_blocks,
+                             size_t smem_bytes, uint32_t seed, uint64_t sweep0, int n_sweeps,
+                             int64_t ts_pos, bool record, cudaStream_t st)
+{
+    if (n_blocks <= 0 || n_sweeps <= 0) return cudaSuccess;
+    if (record)
+        sweep_ws_kernel<true><<<n_blocks, kWsThreads, smem_bytes, st>>>(groups_dev, blocks_dev, seed,
+                                                                        sweep0, n_sweeps, ts_pos);
+    else
+        sweep_ws_kernel<false><<<n_blocks, kWsThreads, smem_bytes, st>>>(
+            groups_dev, blocks_dev, seed, sweep0, n_sweeps, ts_pos);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sweeps(const GroupDev *groups_dev, const BlockDesc *blocks_dev, int n_blocks,

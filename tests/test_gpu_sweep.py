@@ -116,9 +116,9 @@ def compare_group(got, ref, n_iter):
     assert np.array_equal(got["tallies"], ref["tallies"])
 
 
-@pytest.mark.parametrize("residency,wpb,P", [(1, 32, 1), (1, 64, 1), (1, 16, 2), (1, 8, 4),
-                                             (1, 4, 8), (2, 32, 1), (2, 8, 4), (2, 4, 8),
-                                             (0, 0, 0)])
+@pytest.mark.parametrize("residency,wpb,P", [(1, 32, 1), (1, 16, 2), (1, 8, 4), (1, 4, 8),
+                                             (2, 32, 1), (2, 16, 1), (2, 8, 4), (2, 4, 8),
+                                             (3, 32, 0), (3, 16, 0), (3, 8, 0), (0, 0, 0)])
 def test_small_workload_full_run_bit_exact(residency, wpb, P):
     """L=8, T=2.0, 64 walkers, 10 iterations x 200 sweeps, seed 0, in full,
     in every kernel configuration (results never depend on it)."""
@@ -146,10 +146,11 @@ def test_graph_form_equals_plain_form():
         assert np.array_equal(x["lnW"], y["lnW"])
 
 
-def test_mixed_groups_reduced_bit_exact():
+@pytest.mark.parametrize("residency", [0, 3])
+def test_mixed_groups_reduced_bit_exact(residency):
     """The mixed (L, T) batch in one context, few walkers per group (ragged)."""
     groups = wl.mixed_groups(n_walkers=37)
-    got = gpu_run(groups, wl.MIXED["seed"], 2, 3, n_meas=2)
+    got = gpu_run(groups, wl.MIXED["seed"], 2, 3, n_meas=2, residency=residency)
     for g, (spec, w0) in enumerate(zip(groups, walker_offsets(groups))):
         ref = oracle.muca_run(spec["L"], spec["T"], spec["n_walkers"], wl.MIXED["seed"], 2, 3,
                               n_meas=2, walker_id0=w0)
@@ -157,14 +158,14 @@ def test_mixed_groups_reduced_bit_exact():
         assert np.array_equal(got[g]["ts"], ref["ts"].transpose(1, 2, 0))
 
 
-@pytest.mark.parametrize("P", [1, 2, 8])
+@pytest.mark.parametrize("P", [1, 2, 8, 0])
 def test_generic_and_unrolled_sizes_in_one_launch(P):
     """Sizes of the unrolled row path and of the plain per-site path (L % 4 != 0)
     side by side; lanes per walker apply to the unrolled sizes only."""
     groups = [{"L": L, "T": T, "n_walkers": nw}
               for L, T, nw in [(2, 1.0, 7), (3, 2.0, 33), (4, 0.9, 40), (5, 1.4182, 9),
                                (12, 1.0, 65), (20, 2.0, 31)]]
-    got = gpu_run(groups, 23, 2, 4, n_meas=3, residency=1, lanes_per_walker=P)
+    got = gpu_run(groups, 23, 2, 4, n_meas=3, residency=1 if P else 3, lanes_per_walker=P)
     for g, (spec, w0) in enumerate(zip(groups, walker_offsets(groups))):
         ref = oracle.muca_run(spec["L"], spec["T"], spec["n_walkers"], 23, 2, 4, n_meas=3,
                               walker_id0=w0)
@@ -186,7 +187,7 @@ def sample_walkers(W):
     return sorted({0, 1, 31, 32, 33, W // 2, W - 33, W - 1} & set(range(W)))
 
 
-@pytest.mark.parametrize("residency,P", [(0, 0), (1, 1), (1, 4), (1, 8)])
+@pytest.mark.parametrize("residency,P", [(0, 0), (1, 4), (1, 8), (3, 0)])
 def test_large_workload_full_size_sampled_walkers(residency, P):
     """L=48, T=0.9, all 4096 walkers in the benchmark's launch configuration,
     under a fixed non-trivial weight: sampled walkers recomputed by the oracle,
@@ -284,6 +285,39 @@ def test_restricted_window_and_set_state():
     s2, t2 = c.get_state(0)
     assert np.array_equal(s2, g_spins) and np.array_equal(t2, g_tal)
     c.close()
+
+
+@pytest.mark.parametrize("e_min,e_max,res,P", [(300, 320, 1, 1), (250, 350, 1, 4),
+                                              (420, 512, 1, 8), (250, 350, 3, 0),
+                                              (420, 512, 3, 0)])
+def test_restricted_window_unrolled_size(e_min, e_max, res, P):
+    """L=8 with a restricted E_Delta window: a window narrower than the kernel's
+    table window (plain path) and wider ones that reach the top of the range
+    (unrolled path, table window clamped to the window's rows)."""
+    L, T, W = 8, 1.0, 24
+    V = L ** 3
+    rng = np.random.default_rng(e_min)
+    spins = np.zeros((W, V), dtype=np.int8)
+    for w in range(W):
+        n = int(rng.integers(e_min, e_max + 1))
+        idx = rng.choice(V, n, replace=False)
+        spins[w, idx] = rng.choice(np.array([-1, 1], dtype=np.int8), n)
+    c = ctx_of([{"L": L, "T": T, "n_walkers": W, "e_min": e_min, "e_max": e_max}], seed=31,
+               residency=res, lanes_per_walker=P)
+    c.set_state(0, spins)
+    lnW = wl.random_lnW(e_max - e_min + 1, seed=e_max, scale=0.8)
+    c.set_lnW(0, lnW)
+    c.reserve_timeseries(25)
+    c.sweep_iter(25, record=True)
+    g_spins, _ = c.get_state(0)
+    ts = c.get_timeseries(0)
+    c.close()
+    thr = oracle.build_table(L, T, e_min, e_max, lnW)
+    for w in range(W):
+        sp = spins[w].copy()
+        t = oracle.energies(L, sp).astype(np.int32)
+        ref = oracle.sweeps(L, e_min, e_max, thr, 31, w, 0, 25, sp, t, record=True)
+        assert np.array_equal(g_spins[w], sp) and np.array_equal(ts[:, :, w], ref), w
 
 
 def test_ising_limit_on_gpu():
