@@ -128,9 +128,9 @@ def run_reference(args, rank, world):
     cores = os.cpu_count() or 1
     # calibrate: one sweep of one walker per core
     t0 = time.perf_counter()
-    oracle.muca_run(L, T, cores, s["seed"], 1, 1, n_threads=cores, want_spins=False)
-    t1 = time.perf_counter() - t0
-    sweeps = max(1, min(200, int(6.0 / max(t1, 1e-3))))
+    oracle.muca_run(L, T, cores, s["seed"], 1, 20, n_threads=cores, want_spins=False)
+    rate = 20 / max(time.perf_counter() - t0, 1e-3)
+    sweeps = max(20, min(5000, int(8.0 * rate)))  # about 8 s per step
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -163,10 +163,11 @@ def cpu_baseline_sample():
     L, T = s["L"], s["T"]
     V = L ** 3
     cores = os.cpu_count() or 1
+    # calibrate on 20 sweeps, then time a sample of about 15 s
     t0 = time.perf_counter()
-    oracle.muca_run(L, T, cores, s["seed"], 1, 1, n_threads=cores, want_spins=False)
-    t1 = time.perf_counter() - t0
-    sweeps = max(1, min(400, int(12.0 / max(t1, 1e-3))))
+    oracle.muca_run(L, T, cores, s["seed"], 1, 20, n_threads=cores, want_spins=False)
+    rate = 20 / max(time.perf_counter() - t0, 1e-3)
+    sweeps = max(20, min(5000, int(15.0 * rate)))
     t0 = time.perf_counter()
     oracle.muca_run(L, T, cores, s["seed"], 1, sweeps, n_threads=cores, want_spins=False)
     dt = time.perf_counter() - t0
@@ -303,13 +304,14 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": "L=48 T=0.9 4096 walkers: 1000-sweep MUCA iteration "
                                    "(graph) + 250 recorded sweeps + FP32 reweight to 4096 Delta",
                        "L": L, "T": T, "walkers": W, "sweeps_per_step": sweeps + meas,
-                       "residency": {1: "global", 2: "smem"}.get(res, str(res)),
+                       "residency": {1: "global", 2: "smem", 3: "split"}.get(res, str(res)),
                        "walkers_per_block": wpb, "lanes_per_walker": lanes, "seed": s["seed"],
                        "l2": "inputs larger than L2 (lattice 453 MB int8)"},
             "plain": {"value": plain_value, "unit": UNIT, "steps": plain_steps},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": int_peak / 1e12,
                          "unit": "Tops/s", "frac": achieved_ops / int_peak, "traffic": None,
-                         "kernel": "sweep_global_kernel<false>",
+                         "kernel": {1: "sweep_global_kernel<false>", 2: "sweep_smem_kernel<false>",
+                                    3: "sweep_ws_kernel<false>"}.get(res, str(res)),
                          "ops_per_attempt": ops_per_attempt,
                          "peak_source": f"152 SMs x 128 INT32 lanes x median SM clock "
                                         f"{sm_clock:.0f} MHz",
@@ -370,6 +372,37 @@ def reweight_bench(torch, muca):
     return out
 
 
+def run_profile_case(what, cfg):
+    """Short fixed launches for profiler captures (not timed): the sweep kernel
+    of the benchmark workload in a given configuration "residency,walkers per
+    block,lanes per walker" (3 launches of 2 sweeps, no autotuning trials)
+    or the reweighting of the reweight workload (FP32 then FP64)."""
+    import torch
+
+    from paper_1502_07214_gb300 import muca
+
+    torch.cuda.set_device(0)
+    if what == "sweep":
+        s = wl.LARGE
+        res, wpb, lanes = (int(x) for x in cfg.split(","))
+        ctx = muca.Context([{"L": s["L"], "T": s["T"], "n_walkers": s["n_walkers"]}],
+                           seed=s["seed"], residency=res, walkers_per_block=wpb,
+                           lanes_per_walker=lanes)
+        for _ in range(3):
+            ctx.sweep_iter(2)
+        ctx.sync()
+        print("profile case: sweep", ctx.get_config(0))
+        ctx.close()
+    else:
+        r = wl.REWEIGHT
+        ej, ed, m, lnW, dt = wl.synthetic_series()
+        dev = [torch.from_numpy(a.ravel()).cuda() for a in (ej, ed, m)]
+        grid = wl.delta_grid(dt)
+        for p in (32, 64):
+            muca.reweight(*dev, lnW, 0, 1.0 / r["T"], r["L"] ** 3, grid, p)
+        print("profile case: reweight")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,7 +410,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--profile", choices=["sweep", "reweight"],
+                    help="run a short untimed case for a profiler capture and exit")
+    ap.add_argument("--profile-config", default="1,4,8",
+                    help="sweep kernel configuration of --profile sweep")
     args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args.profile, args.profile_config)
+        return
     if args.warmup < 3:
         args.warmup = 3
     world = env_int("WORLD_SIZE", 1)

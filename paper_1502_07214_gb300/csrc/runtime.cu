@@ -372,8 +372,9 @@ std::vector<Cand> candidates(const Group &g, int residency, int wpb, int P, int 
             if (wpb > 0) {
                 if (wpb <= fit && wpb * p <= 32) c.push_back({MUCA_RES_SMEM, wpb, p});
             } else {
+                // fewer than 8 lattices per block leave most of the GPU idle
                 const int G = std::min(fit, 32 / p);
-                if (G >= 1) c.push_back({MUCA_RES_SMEM, G, p});
+                if (G >= 8 || (G >= 1 && G == 32 / p)) c.push_back({MUCA_RES_SMEM, G, p});
             }
         }
     }
