@@ -61,6 +61,8 @@ SIGNATURES = {
     "muca_run_graph": [_P, ctypes.c_int, ctypes.c_int],
     "muca_reweight": [_P, _P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _P, _I32, _I32,
                       _P, _P],
+    "muca_reweight_noalloc": [_P, _P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _P, _I32,
+                              _I32, _P, _P],
     "muca_reserve_timeseries": [_P, _I64],
     "muca_timeseries_device": [_P, ctypes.c_int, _P, _P],
     "muca_get_timeseries": [_P, ctypes.c_int, _P],
@@ -270,9 +272,10 @@ class Context:
 
 
 def reweight(e_j, e_d, m, lnW, e_min, beta, V, delta_grid, precision=64, n_rows=None,
-             row_len=None, row_stride=None, stream=None):
-    """``muca_reweight``: e_j, e_d, m are torch int32 CUDA tensors (or raw device
-    addresses with n_rows/row_len/row_stride given).  Returns numpy [n_grid][5]:
+             row_len=None, row_stride=None, stream=None, no_alloc=False):
+    """``muca_reweight`` (``muca_reweight_noalloc`` with no_alloc=True): e_j, e_d,
+    m are torch int32 CUDA tensors (or raw device addresses with
+    n_rows/row_len/row_stride given).  Returns numpy [n_grid][5]:
     <E_J>, <E_Delta>, C, chi, U4."""
     L = lib()
     ptrs = []
@@ -289,9 +292,10 @@ def reweight(e_j, e_d, m, lnW, e_min, beta, V, delta_grid, precision=64, n_rows=
     lnW = np.ascontiguousarray(lnW, dtype=np.float64)
     grid = np.ascontiguousarray(delta_grid, dtype=np.float64)
     out = np.zeros((len(grid), 5))
-    rc = L.muca_reweight(ptrs[0], ptrs[1], ptrs[2], n_rows, row_len, row_stride, _np_ptr(lnW),
-                         e_min, len(lnW), beta, V, _np_ptr(grid), len(grid), precision,
-                         _np_ptr(out), _stream_ptr(stream))
+    fn = L.muca_reweight_noalloc if no_alloc else L.muca_reweight
+    rc = fn(ptrs[0], ptrs[1], ptrs[2], n_rows, row_len, row_stride, _np_ptr(lnW), e_min,
+            len(lnW), beta, V, _np_ptr(grid), len(grid), precision, _np_ptr(out),
+            _stream_ptr(stream))
     _ck(rc)
     return out
 
