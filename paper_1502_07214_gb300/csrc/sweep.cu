@@ -156,7 +156,7 @@ constexpr int kMaxLw = kMaxL / 4;
 constexpr int kStageWords = 8 * kMaxLw + 4 * kMaxL;  // per slot
 constexpr int kRing = 32;                            // table rows per walker window
 constexpr int kRingStride = kRing * kRow + 4;        // words per slot
-constexpr int kMargin = 8;                           // re-centre when this close to an edge
+constexpr int kMargin = 14;                          // re-centre when this close to an edge
 
 struct Stage {
     uint32_t *base;  // staging fields
@@ -276,53 +276,114 @@ __device__ __forceinline__ int dsc_sp(uint32_t a) { return (int)((a >> 16) & 3u)
 __device__ __forceinline__ int dsc_s(uint32_t a) { return (int)((a >> 18) & 3u) - 1; }
 __device__ __forceinline__ int dsc_k(uint32_t a) { return (a >> 20) & 1u ? 1 : -1; }
 
-// State of the chain of one walker inside a row.
-struct ChainState {
-    int e;       // table row of the current E_Delta
-    uint32_t t;  // threshold in flight for the current site
-    uint32_t u;  // its uniform draw
-    uint32_t a;  // its descriptor
-    int corr;    // column correction of site L-1 (its x+1 is the new site 0)
-};
-
-// One step of the chain for site x (x + 1 < L: also issues the load of site
-// x + 1).  FAST reads the walker's table window, otherwise the global table.
-template <int L, bool FAST>
-__device__ __forceinline__ void chain_step(int x, ChainState &cs, uint32_t (&accb)[(L + 31) / 32],
-                                           const Stage &sg, int slot, const uint32_t *win,
-                                           const uint32_t *__restrict__ thrE)
+// The chain of one walker over one row (phase 4), fully unrolled.  Inputs:
+// the site descriptors and random words of the row (dsc[x * stride],
+// rn[x * stride]); np: the packed new spins of the row's y-1 neighbour, added
+// to the columns when ycorr (the split kernel leaves that neighbour out of the
+// descriptors), else ignored; e: the table row of E_Delta at the row start.
+// Returns the row of E_Delta at the row end and sets the acceptance bits.
+// FAST reads every threshold from the walker's window ring (row e at ring
+// row e mod kRing) without asking whether row e is there; lo_e and hi_e
+// return the lowest and highest row it read, so that the caller can check
+// afterwards that all of them were in the window and otherwise run the row
+// again with row_chain_global.  Nothing that depends on the previous step
+// sits on the chain but the compare, the select of the next address and the
+// load.
+template <int L>
+__device__ __forceinline__ int row_chain_fast(const uint32_t *dsc, const uint32_t *rn, int stride,
+                                              const uint32_t *np, bool ycorr, int e,
+                                              const uint32_t *win, uint32_t (&accb)[(L + 31) / 32],
+                                              int &lo_e, int &hi_e)
 {
-    uint32_t a1 = 0u, u1 = 0u;
-    int iA = 0, iR = 0;
-    if (x + 1 < L) {
-        a1 = sg.AUX(x + 1)[slot];
-        u1 = sg.rnd(x + 1)[slot] & 0x7FFFFFFFu;
-        int cA = dsc_colA(a1), cR = dsc_colR(a1);
-        if (x + 1 == L - 1) {
-            cA += cs.corr;
-            cR += cs.corr;
+    constexpr int Lw = L / 4, NB = (L + 31) / 32;
+    uint32_t nwd[Lw];
+#pragma unroll
+    for (int j = 0; j < Lw; ++j) nwd[j] = ycorr ? np[j * stride] : 0u;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) accb[q] = 0u;
+    const int kL = dsc_k(dsc[(L - 1) * stride]);
+    uint32_t a = dsc[0];
+    uint32_t u = rn[0] & 0x7FFFFFFFu;
+    int ce = e, lo = e, hi = e;
+    uint32_t t = win[(ce & (kRing - 1)) * kRow + dsc_colR(a) - dsc_k(a) * sbyte(nwd[0], 0)];
+    int corr = 0;  // column correction of site L-1: its x+1 is the new site 0
+#pragma unroll
+    for (int x = 0; x < L; ++x) {
+        uint32_t a1 = 0u, u1 = 0u;
+        int iA = 0, iR = 0;
+        if (x + 1 < L) {
+            a1 = dsc[(x + 1) * stride];
+            u1 = rn[(x + 1) * stride] & 0x7FFFFFFFu;
+            int cc = -dsc_k(a1) * sbyte(nwd[(x + 1) >> 2], (x + 1) & 3);
+            if (x + 1 == L - 1) cc += corr;
+            iA = ((ce + dsc_dprev(a1)) & (kRing - 1)) * kRow + dsc_colA(a1) + cc;
+            iR = (ce & (kRing - 1)) * kRow + dsc_colR(a1) + cc;
         }
-        const int eA = cs.e + dsc_dprev(a1);
-        if (FAST) {
-            iA = (eA & (kRing - 1)) * kRow + cA;
-            iR = (cs.e & (kRing - 1)) * kRow + cR;
-        } else {
-            iA = eA * kRow + cA;
-            iR = cs.e * kRow + cR;
+        const bool acc = u < t;
+        if (x + 1 < L) t = win[acc ? iA : iR];
+        if (acc) {
+            ce += dsc_d(a);
+            accb[x >> 5] |= 1u << (x & 31);
         }
+        lo = min(lo, ce);
+        hi = max(hi, ce);
+        if (x == 0) corr = acc ? -kL * (dsc_sp(a) - dsc_s(a)) : 0;
+        a = a1;
+        u = u1;
     }
-    const bool acc = cs.u < cs.t;
-    if (x + 1 < L) cs.t = FAST ? win[acc ? iA : iR] : __ldg(thrE + (acc ? iA : iR));
-    if (acc) {
-        cs.e += dsc_d(cs.a);
-        accb[x >> 5] |= 1u << (x & 31);
+    lo_e = lo;
+    hi_e = hi;
+    return ce;
+}
+
+// The same row, every threshold read from the global table (rows -kGuard ..
+// nE + kGuard - 1 are all there): the path of rows whose E_Delta left the
+// window.  Site by site, not unrolled.
+template <int L>
+__device__ __noinline__ int row_chain_global(const uint32_t *dsc, const uint32_t *rn, int stride,
+                                             const uint32_t *np, bool ycorr, int e,
+                                             const uint32_t *__restrict__ thrE,
+                                             uint32_t (&accb)[(L + 31) / 32])
+{
+    constexpr int NB = (L + 31) / 32;
+    uint32_t b0 = 0u, b1 = 0u;
+    const int kL = dsc_k(dsc[(L - 1) * stride]);
+    bool prev = false;  // site x-1 accepted
+    int corr = 0;
+#pragma unroll 1
+    for (int x = 0; x < L; ++x) {
+        const uint32_t a = dsc[x * stride];
+        const uint32_t u = rn[x * stride] & 0x7FFFFFFFu;
+        int col = prev ? dsc_colA(a) : dsc_colR(a);
+        if (ycorr) col -= dsc_k(a) * sbyte(np[(x >> 2) * stride], x & 3);
+        if (x == L - 1) col += corr;
+        const bool acc = u < __ldg(thrE + (ptrdiff_t)e * kRow + col);
+        if (acc) {
+            e += dsc_d(a);
+            if (x < 32) b0 |= 1u << x;
+            else b1 |= 1u << (x - 32);
+        }
+        if (x == 0) corr = acc ? -kL * (dsc_sp(a) - dsc_s(a)) : 0;
+        prev = acc;
     }
-    if (x == 0) {
-        const int kL = dsc_k(sg.AUX(L - 1)[slot]);
-        cs.corr = acc ? -kL * (dsc_sp(cs.a) - dsc_s(cs.a)) : 0;
-    }
-    cs.a = a1;
-    cs.u = u1;
+    accb[0] = b0;
+    if (NB > 1) accb[NB - 1] = b1;
+    return e;
+}
+
+// Phase 4 of one row: the fast chain, checked against the window [vlo, vhi)
+// that was complete while it ran, and redone from the global table by the
+// walkers that left it.
+template <int L>
+__device__ __forceinline__ int row_chain(const uint32_t *dsc, const uint32_t *rn, int stride,
+                                         const uint32_t *np, bool ycorr, int e, const Window &wd,
+                                         const uint32_t *win, const uint32_t *__restrict__ thrE,
+                                         uint32_t (&accb)[(L + 31) / 32])
+{
+    int lo, hi;
+    const int ce = row_chain_fast<L>(dsc, rn, stride, np, ycorr, e, win, accb, lo, hi);
+    if (lo >= wd.vlo && hi < wd.vhi) return ce;
+    return row_chain_global<L>(dsc, rn, stride, np, ycorr, e, thrE, accb);
 }
 
 // The unrolled row path (L % 4 == 0).  Threads of the block run this in lock
@@ -397,33 +458,10 @@ __device__ __forceinline__ void sweep_rows(const BlockLattice &bl, const Stage &
                               (k > 0 ? (1u << 20) : 0u);
         }
         __syncwarp(amask);
-        // 4. the chain, in groups of four sites
+        // 4. the chain (every lane of the walker runs it on the same data)
         uint32_t accb[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) accb[b] = 0u;
-        ChainState cs;
-        cs.e = e;
-        cs.corr = 0;
-        cs.a = sg.AUX(0)[slot];
-        cs.u = sg.rnd(0)[slot] & 0x7FFFFFFFu;
-        {
-            // the loads a group can issue stay within 4 rows of the group's first row
-            const bool fast = __all_sync(amask, e - 4 >= wd.vlo && e + 4 < wd.vhi);
-            const int col0 = dsc_colR(cs.a);
-            cs.t = fast ? win[(e & (kRing - 1)) * kRow + col0] : __ldg(thrE + e * kRow + col0);
-        }
-#pragma unroll
-        for (int x0 = 0; x0 < L; x0 += 4) {
-            const bool fast = __all_sync(amask, cs.e - 4 >= wd.vlo && cs.e + 4 < wd.vhi);
-            if (fast) {
-#pragma unroll
-                for (int x = x0; x < x0 + 4; ++x) chain_step<L, true>(x, cs, accb, sg, slot, win, thrE);
-            } else {
-#pragma unroll
-                for (int x = x0; x < x0 + 4; ++x) chain_step<L, false>(x, cs, accb, sg, slot, win, thrE);
-            }
-        }
-        e = cs.e;
+        e = row_chain<L>(sg.AUX(0) + slot, sg.rnd(0) + slot, sg.S, nullptr, false, e, wd, win,
+                         thrE, accb);
         // 5. new spins, their store, the tallies
         for (int j = h; j < Lw; j += P) {
             uint32_t nwd = 0u;
@@ -708,66 +746,8 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                     const bool ycorr = (y != 0);  // the y-1 row is the one just finished
                     const int nprev = (r + 2) % 3;
                     uint32_t accb[NB];
-#pragma unroll
-                    for (int q = 0; q < NB; ++q) accb[q] = 0u;
-                    ChainState cs;
-                    cs.e = e;
-                    cs.corr = 0;
-                    cs.a = sm.desc(b, 0)[slot];
-                    cs.u = sm.rnd(b, 0)[slot] & 0x7FFFFFFFu;
-                    {
-                        const bool fast = __all_sync(amask, e - 4 >= wd.vlo && e + 4 < wd.vhi);
-                        const int col0 = dsc_colR(cs.a) -
-                                         (ycorr ? dsc_k(cs.a) * sbyte(sm.N(nprev, 0)[slot], 0) : 0);
-                        cs.t = fast ? win[(e & (kRing - 1)) * kRow + col0]
-                                    : __ldg(thrE + e * kRow + col0);
-                    }
-#pragma unroll 1
-                    for (int x0 = 0; x0 < L; x0 += 4) {
-                        const bool fast =
-                            __all_sync(amask, cs.e - 4 >= wd.vlo && cs.e + 4 < wd.vhi);
-                        // y-1 neighbours (new) of sites x0+1 .. x0+4
-                        const uint32_t n0 = ycorr ? sm.N(nprev, x0 >> 2)[slot] : 0u;
-                        const uint32_t n1 =
-                            (ycorr && x0 + 4 < L) ? sm.N(nprev, (x0 >> 2) + 1)[slot] : 0u;
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int x = x0 + q;
-                            uint32_t a1 = 0u, u1 = 0u;
-                            int iA = 0, iR = 0;
-                            if (x + 1 < L) {
-                                a1 = sm.desc(b, x + 1)[slot];
-                                u1 = sm.rnd(b, x + 1)[slot] & 0x7FFFFFFFu;
-                                const int ny = (q < 3) ? sbyte(n0, q + 1) : sbyte(n1, 0);
-                                int cc = -dsc_k(a1) * ny;
-                                if (x + 1 == L - 1) cc += cs.corr;
-                                const int cA = dsc_colA(a1) + cc, cR = dsc_colR(a1) + cc;
-                                const int eA = cs.e + dsc_dprev(a1);
-                                if (fast) {
-                                    iA = (eA & (kRing - 1)) * kRow + cA;
-                                    iR = (cs.e & (kRing - 1)) * kRow + cR;
-                                } else {
-                                    iA = eA * kRow + cA;
-                                    iR = cs.e * kRow + cR;
-                                }
-                            }
-                            const bool acc = cs.u < cs.t;
-                            if (x + 1 < L)
-                                cs.t = fast ? win[acc ? iA : iR] : __ldg(thrE + (acc ? iA : iR));
-                            if (acc) {
-                                cs.e += dsc_d(cs.a);
-                                if (NB == 1 || x < 32) accb[0] |= 1u << (x & 31);
-                                else accb[NB - 1] |= 1u << (x & 31);
-                            }
-                            if (x == 0) {
-                                const int kL = dsc_k(sm.desc(b, L - 1)[slot]);
-                                cs.corr = acc ? -kL * (dsc_sp(cs.a) - dsc_s(cs.a)) : 0;
-                            }
-                            cs.a = a1;
-                            cs.u = u1;
-                        }
-                    }
-                    e = cs.e;
+                    e = row_chain<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
+                                     sm.N(nprev, 0) + slot, ycorr, e, wd, win, thrE, accb);
                     // the row's new spins
 #pragma unroll 1
                     for (int j = 0; j < Lw; ++j) {
