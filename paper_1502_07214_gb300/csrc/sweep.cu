@@ -198,19 +198,43 @@ __device__ __forceinline__ void window_fill(uint32_t *win, const uint32_t *__res
     }
 }
 
-// Re-centre the window on row e if e came within kMargin rows of an edge.
-// Rows stay inside the table allocation [-kGuard, nE + kGuard).
+// The window position for table row e when the window is at lo: lo while e
+// stays kMargin rows away from both edges, else the position that centres e,
+// kept inside the table allocation [-kGuard, nE + kGuard).
+__device__ __forceinline__ int window_target(int lo, int e, int nE)
+{
+    if (e >= lo + kMargin && e < lo + kRing - kMargin) return lo;
+    int n = e - kRing / 2;
+    n = max(n, -kGuard);
+    return min(n, nE + kGuard - kRing);
+}
+
+// Rows [a, b) that enter the window when it moves from lo to n.
+__device__ __forceinline__ void window_delta(int lo, int n, int &a, int &b)
+{
+    if (n > lo) {
+        a = max(lo + kRing, n);
+        b = n + kRing;
+    } else if (n < lo) {
+        a = n;
+        b = min(lo, n + kRing);
+    } else {
+        a = b = 0;
+    }
+}
+
+// Re-centre the window on row e if e came within kMargin rows of an edge:
+// start the copies of the rows that enter it; [vlo, vhi) becomes the rows in
+// both the old and the new window.
 __device__ __forceinline__ void window_recentre(Window &wd, uint32_t *win,
                                                 const uint32_t *__restrict__ thrE, int e, int nE,
                                                 int P, int h)
 {
-    if (e >= wd.lo + kMargin && e < wd.lo + kRing - kMargin) return;
-    int lo = e - kRing / 2;
-    lo = max(lo, -kGuard);
-    lo = min(lo, nE + kGuard - kRing);
+    const int lo = window_target(wd.lo, e, nE);
     if (lo == wd.lo) return;
-    if (lo > wd.lo) window_fill(win, thrE, max(wd.lo + kRing, lo), lo + kRing, P, h);
-    else window_fill(win, thrE, lo, min(wd.lo, lo + kRing), P, h);
+    int a, b;
+    window_delta(wd.lo, lo, a, b);
+    window_fill(win, thrE, a, b, P, h);
     wd.vlo = max(wd.lo, lo);
     wd.vhi = min(wd.lo, lo) + kRing;
     wd.lo = lo;
@@ -280,32 +304,33 @@ __device__ __forceinline__ int dsc_k(uint32_t a) { return (a >> 20) & 1u ? 1 : -
 // the site descriptors and random words of the row (dsc[x * stride],
 // rn[x * stride]); np: the packed new spins of the row's y-1 neighbour, added
 // to the columns when ycorr (the split kernel leaves that neighbour out of the
-// descriptors), else ignored; e: the table row of E_Delta at the row start.
-// Returns the row of E_Delta at the row end and sets the acceptance bits.
-// FAST reads every threshold from the walker's window ring (row e at ring
-// row e mod kRing) without asking whether row e is there; lo_e and hi_e
-// return the lowest and highest row it read, so that the caller can check
+// descriptors); e: the table row of E_Delta at the row start.  Returns the
+// row of E_Delta at the row end and the row's new spins, packed (nn).
+// It reads every threshold from the walker's window ring (row e at ring row
+// e mod kRing) without asking whether row e is there; lo_e and hi_e return
+// the lowest and highest row it read, so that the caller can check
 // afterwards that all of them were in the window and otherwise run the row
 // again with row_chain_global.  Nothing that depends on the previous step
 // sits on the chain but the compare, the select of the next address and the
 // load.
 template <int L>
 __device__ __forceinline__ int row_chain_fast(const uint32_t *dsc, const uint32_t *rn, int stride,
-                                              const uint32_t *np, bool ycorr, int e,
-                                              const uint32_t *win, uint32_t (&accb)[(L + 31) / 32],
+                                              const uint32_t (&np)[L / 4], bool ycorr, int e,
+                                              const uint32_t *win, uint32_t (&nn)[L / 4],
                                               int &lo_e, int &hi_e)
 {
-    constexpr int Lw = L / 4, NB = (L + 31) / 32;
-    uint32_t nwd[Lw];
+    constexpr int Lw = L / 4;
+    uint32_t ny[Lw];
 #pragma unroll
-    for (int j = 0; j < Lw; ++j) nwd[j] = ycorr ? np[j * stride] : 0u;
-#pragma unroll
-    for (int q = 0; q < NB; ++q) accb[q] = 0u;
+    for (int j = 0; j < Lw; ++j) {
+        ny[j] = ycorr ? np[j] : 0u;
+        nn[j] = 0u;
+    }
     const int kL = dsc_k(dsc[(L - 1) * stride]);
     uint32_t a = dsc[0];
     uint32_t u = rn[0] & 0x7FFFFFFFu;
     int ce = e, lo = e, hi = e;
-    uint32_t t = win[(ce & (kRing - 1)) * kRow + dsc_colR(a) - dsc_k(a) * sbyte(nwd[0], 0)];
+    uint32_t t = win[(ce & (kRing - 1)) * kRow + dsc_colR(a) - dsc_k(a) * sbyte(ny[0], 0)];
     int corr = 0;  // column correction of site L-1: its x+1 is the new site 0
 #pragma unroll
     for (int x = 0; x < L; ++x) {
@@ -314,19 +339,17 @@ __device__ __forceinline__ int row_chain_fast(const uint32_t *dsc, const uint32_
         if (x + 1 < L) {
             a1 = dsc[(x + 1) * stride];
             u1 = rn[(x + 1) * stride] & 0x7FFFFFFFu;
-            int cc = -dsc_k(a1) * sbyte(nwd[(x + 1) >> 2], (x + 1) & 3);
+            int cc = -dsc_k(a1) * sbyte(ny[(x + 1) >> 2], (x + 1) & 3);
             if (x + 1 == L - 1) cc += corr;
             iA = ((ce + dsc_dprev(a1)) & (kRing - 1)) * kRow + dsc_colA(a1) + cc;
             iR = (ce & (kRing - 1)) * kRow + dsc_colR(a1) + cc;
         }
         const bool acc = u < t;
         if (x + 1 < L) t = win[acc ? iA : iR];
-        if (acc) {
-            ce += dsc_d(a);
-            accb[x >> 5] |= 1u << (x & 31);
-        }
+        if (acc) ce += dsc_d(a);
         lo = min(lo, ce);
         hi = max(hi, ce);
+        nn[x >> 2] |= (uint32_t)((acc ? dsc_sp(a) : dsc_s(a)) & 0xFF) << (8 * (x & 3));
         if (x == 0) corr = acc ? -kL * (dsc_sp(a) - dsc_s(a)) : 0;
         a = a1;
         u = u1;
@@ -338,52 +361,35 @@ __device__ __forceinline__ int row_chain_fast(const uint32_t *dsc, const uint32_
 
 // The same row, every threshold read from the global table (rows -kGuard ..
 // nE + kGuard - 1 are all there): the path of rows whose E_Delta left the
-// window.  Site by site, not unrolled.
+// window.  Site by site, not unrolled; np is nullptr when the row has no y-1
+// correction.  Writes the row's packed new spins to nout[j * stride].
 template <int L>
 __device__ __noinline__ int row_chain_global(const uint32_t *dsc, const uint32_t *rn, int stride,
-                                             const uint32_t *np, bool ycorr, int e,
-                                             const uint32_t *__restrict__ thrE,
-                                             uint32_t (&accb)[(L + 31) / 32])
+                                             const uint32_t *np, int e,
+                                             const uint32_t *__restrict__ thrE, uint32_t *nout)
 {
-    constexpr int NB = (L + 31) / 32;
-    uint32_t b0 = 0u, b1 = 0u;
     const int kL = dsc_k(dsc[(L - 1) * stride]);
     bool prev = false;  // site x-1 accepted
     int corr = 0;
+    uint32_t word = 0u;
 #pragma unroll 1
     for (int x = 0; x < L; ++x) {
         const uint32_t a = dsc[x * stride];
         const uint32_t u = rn[x * stride] & 0x7FFFFFFFu;
         int col = prev ? dsc_colA(a) : dsc_colR(a);
-        if (ycorr) col -= dsc_k(a) * sbyte(np[(x >> 2) * stride], x & 3);
+        if (np) col -= dsc_k(a) * sbyte(np[(x >> 2) * stride], x & 3);
         if (x == L - 1) col += corr;
         const bool acc = u < __ldg(thrE + (ptrdiff_t)e * kRow + col);
-        if (acc) {
-            e += dsc_d(a);
-            if (x < 32) b0 |= 1u << x;
-            else b1 |= 1u << (x - 32);
+        if (acc) e += dsc_d(a);
+        word |= (uint32_t)((acc ? dsc_sp(a) : dsc_s(a)) & 0xFF) << (8 * (x & 3));
+        if ((x & 3) == 3) {
+            nout[(x >> 2) * stride] = word;
+            word = 0u;
         }
         if (x == 0) corr = acc ? -kL * (dsc_sp(a) - dsc_s(a)) : 0;
         prev = acc;
     }
-    accb[0] = b0;
-    if (NB > 1) accb[NB - 1] = b1;
     return e;
-}
-
-// Phase 4 of one row: the fast chain, checked against the window [vlo, vhi)
-// that was complete while it ran, and redone from the global table by the
-// walkers that left it.
-template <int L>
-__device__ __forceinline__ int row_chain(const uint32_t *dsc, const uint32_t *rn, int stride,
-                                         const uint32_t *np, bool ycorr, int e, const Window &wd,
-                                         const uint32_t *win, const uint32_t *__restrict__ thrE,
-                                         uint32_t (&accb)[(L + 31) / 32])
-{
-    int lo, hi;
-    const int ce = row_chain_fast<L>(dsc, rn, stride, np, ycorr, e, win, accb, lo, hi);
-    if (lo >= wd.vlo && hi < wd.vhi) return ce;
-    return row_chain_global<L>(dsc, rn, stride, np, ycorr, e, thrE, accb);
 }
 
 // The unrolled row path (L % 4 == 0).  Threads of the block run this in lock
@@ -396,7 +402,7 @@ __device__ __forceinline__ void sweep_rows(const BlockLattice &bl, const Stage &
                                            int tid, int nthreads, unsigned amask)
 {
     static_assert(L % 4 == 0 && L <= kMaxL, "row path needs L % 4 == 0, L <= 48");
-    constexpr int Lw = L / 4, R = L * L, NB = (L + 31) / 32;
+    constexpr int Lw = L / 4, R = L * L;
     const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
     uint32_t *const own = bl.base + slot;  // this walker's word 0
     uint32_t *const win = sg.win(slot);
@@ -458,23 +464,32 @@ __device__ __forceinline__ void sweep_rows(const BlockLattice &bl, const Stage &
                               (k > 0 ? (1u << 20) : 0u);
         }
         __syncwarp(amask);
-        // 4. the chain (every lane of the walker runs it on the same data)
-        uint32_t accb[NB];
-        e = row_chain<L>(sg.AUX(0) + slot, sg.rnd(0) + slot, sg.S, nullptr, false, e, wd, win,
-                         thrE, accb);
-        // 5. new spins, their store, the tallies
-        for (int j = h; j < Lw; j += P) {
-            uint32_t nwd = 0u;
+        // 4. the chain (every lane of the walker runs it on the same data),
+        //    checked against the window that was complete while it ran
+        uint32_t nn[Lw], np0[Lw];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int x = 4 * j + q;
-                const uint32_t a = sg.AUX(x)[slot];
-                const uint32_t bits = (NB == 1 || x < 32) ? accb[0] : accb[NB - 1];
-                const int sn = ((bits >> (x & 31)) & 1u) ? dsc_sp(a) : dsc_s(a);
-                nwd |= (uint32_t)(sn & 0xFF) << (8 * q);
+        for (int j = 0; j < Lw; ++j) np0[j] = 0u;
+        {
+            int lo, hi;
+            const int ce =
+                row_chain_fast<L>(sg.AUX(0) + slot, sg.rnd(0) + slot, sg.S, np0, false, e, win, nn,
+                                  lo, hi);
+            if (lo >= wd.vlo && hi < wd.vhi) {
+                e = ce;
+            } else {
+                e = row_chain_global<L>(sg.AUX(0) + slot, sg.rnd(0) + slot, sg.S, nullptr, e, thrE,
+                                        sg.N(0) + slot);
+#pragma unroll
+                for (int j = 0; j < Lw; ++j) nn[j] = sg.N(j)[slot];
             }
-            sg.N(j)[slot] = nwd;
-            own[((ptrdiff_t)r * Lw + j) * bl.stride] = nwd;
+        }
+        // 5. new spins, their store, the tallies
+#pragma unroll
+        for (int j = 0; j < Lw; ++j) {
+            if (j % P == h) {
+                sg.N(j)[slot] = nn[j];
+                own[((ptrdiff_t)r * Lw + j) * bl.stride] = nn[j];
+            }
         }
         __syncwarp(amask);
         int dJ = 0, dM = 0, dD = 0;
@@ -622,31 +637,41 @@ sweep_smem_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restri
 // ---------------------------------------------------------------------------
 // Warp-specialised variant (global lattice, L % 4 == 0 up to 48).  A block is
 // kWsWarps warps: warp 0 runs the chains of the block's G walkers (one lane
-// each) and nothing else; warps 1..3 ("helpers") prepare the next row and
-// finish the previous one, so that the per-row work of the phases overlaps
-// the chain instead of adding to it:
+// each) and nothing else; warps 1..3 ("helpers") prepare the next row, finish
+// the previous one and keep the chains' table windows filled, so that the
+// per-row work overlaps the chain instead of adding to it:
 //   helpers, iteration i:  wait until the chain finished row i-2; store its new
-//     spins and add its energy changes; build the old spins and neighbour sums
-//     of row i from the staged rows, draw its Philox words, write its site
-//     descriptors; release row i to the chain; stage the neighbourhood of row
-//     i+1 (cp.async).
-//   chain, row r:  wait for row r; complete the table-window copies issued a
-//     row ago and re-centre the window; run the chain; write the row's new
-//     spins to shared memory; release the descriptor buffer.
+//     spins and accumulate its energy changes; copy the table rows the chain
+//     asked for at the end of row i-2 into its window; build the old spins and
+//     neighbour sums of row i from the staged rows, draw its Philox words and
+//     proposals, write its site descriptors; release row i to the chain;
+//     stage the neighbourhood of row i+1 (cp.async).
+//   chain, row r:  wait for row r; run the chain from the window; keep the
+//     row's new spins in registers (the y-1 neighbours of row r+1) and write
+//     them to shared memory; choose the window position for the rows to come;
+//     release the row's buffers.
 // The only input of row r+1 that depends on row r's outcome is the y-1
 // neighbour: the helpers leave it out of the neighbour sums of non-wrapping
 // rows, and the chain adds -k N_r(x) to the column of site x itself.
-// Buffers: descriptors and random words double-buffered by row parity, old
-// spins / neighbour sums / new spins triple-buffered by row mod 3.  Named
-// barriers: ready[b] (helpers arrive, chain waits), free[b] (chain arrives,
-// helpers wait), and one among the helpers.
+// Window protocol: the rows asked for at the end of row r are copied by the
+// helpers while the chain runs row r+1 and are complete when row r+2 starts
+// (the helpers wait for their copies before they release a row), so row r+1
+// may trust only rows that are in both the previous and the new window.
+// Buffers: descriptors, random words and window requests double-buffered by
+// row parity; old spins, neighbour sums and new spins triple-buffered by row
+// mod 3.  Named barriers: ready[b] (helpers arrive, chain waits), free[b]
+// (chain arrives, helpers wait), and one among the helpers.  Helper thread ht
+// serves walker slot ht mod G and the words j = ht / G, ht / G + 96 / G, ...
+// of each row, so that its share of the energy changes belongs to one walker
+// and is summed in registers over the sweep.
 // ---------------------------------------------------------------------------
 constexpr int kWsWarps = 4;
 constexpr int kWsThreads = 32 * kWsWarps;
 constexpr int kWsHelp = kWsThreads - 32;
 constexpr int kBarReady = 1, kBarFree = 3, kBarHelp = 5;
-// shared words per walker slot
-constexpr int kWsWords = kRingStride + 4 * kMaxL + 9 * kMaxLw + 5 * kMaxLw + 2;
+// shared words per walker slot: window, descriptors and random words, the
+// packed-word buffers (O, H, N x3, staged rows x5, proposals), requests, tallies
+constexpr int kWsWords = kRingStride + 4 * kMaxL + 15 * kMaxLw + 6;
 
 __device__ __forceinline__ void bar_sync(int id, int n)
 {
@@ -665,23 +690,18 @@ struct WsSmem {
     __device__ uint32_t *rest() const { return base + (size_t)G * kRingStride; }
     __device__ uint32_t *desc(int b, int x) const { return rest() + ((b * kMaxL) + x) * G; }
     __device__ uint32_t *rnd(int b, int x) const { return rest() + ((2 + b) * kMaxL + x) * G; }
-    __device__ uint32_t *O(int b, int j) const { return rest() + 4 * kMaxL * G + (b * kMaxLw + j) * G; }
-    __device__ uint32_t *H(int b, int j) const
+    __device__ uint32_t *words(int k, int j) const
     {
-        return rest() + 4 * kMaxL * G + ((3 + b) * kMaxLw + j) * G;
+        return rest() + 4 * kMaxL * G + (k * kMaxLw + j) * G;
     }
-    __device__ uint32_t *N(int b, int j) const
-    {
-        return rest() + 4 * kMaxL * G + ((6 + b) * kMaxLw + j) * G;
-    }
-    __device__ uint32_t *pf(int f, int j) const
-    {
-        return rest() + 4 * kMaxL * G + ((9 + f) * kMaxLw + j) * G;
-    }
-    __device__ int *tal(int slot) const
-    {
-        return (int *)(rest() + 4 * kMaxL * G + 14 * kMaxLw * G) + 2 * slot;
-    }
+    __device__ uint32_t *O(int b, int j) const { return words(b, j); }
+    __device__ uint32_t *H(int b, int j) const { return words(3 + b, j); }
+    __device__ uint32_t *N(int b, int j) const { return words(6 + b, j); }
+    __device__ uint32_t *pf(int f, int j) const { return words(9 + f, j); }
+    __device__ uint32_t *SP(int j) const { return words(14, j); }
+    __device__ int *ints() const { return (int *)(rest() + 4 * kMaxL * G + 15 * kMaxLw * G); }
+    __device__ int *req(int b, int slot) const { return ints() + 2 * (b * G + slot); }
+    __device__ int *tal(int slot) const { return ints() + 4 * G + 2 * slot; }
 };
 
 // Helpers: the five rows around row (y1, z1) of the block's walkers into pf.
@@ -709,7 +729,7 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                                           const WsSmem &sm, uint32_t seed, uint64_t sweep0,
                                           int n_sweeps, int64_t ts_pos)
 {
-    constexpr int Lw = L / 4, R = L * L, NB = (L + 31) / 32;
+    constexpr int Lw = L / 4, R = L * L;
     const int tid = (int)threadIdx.x;
     const int G = sm.G, nw = bd.nw;
     uint32_t *const lat = g.spins + bd.w0;  // word (row, j) of slot s: lat[(row Lw + j) Wpad + s]
@@ -720,48 +740,62 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
         const int slot = tid;
         const bool active = slot < nw;
         const unsigned amask = __ballot_sync(0xFFFFFFFFu, active);
-        const unsigned lead_mask = amask;
         const int w = bd.w0 + slot;
         Chain c{0, 0, 0};
+        uint32_t *const win = sm.win(slot < G ? slot : 0);
+        // lo_a: the window once every copy asked for so far is complete;
+        // lo_b: the window before the last request
+        int lo_a = 0, lo_b = 0;
         if (active) {
             c.EJ = g.tal[w];
             c.ED = g.tal[g.Wpad + w];
             c.M = g.tal[2 * g.Wpad + w];
+            lo_a = window_target(-(1 << 20), c.ED - g.e_min, g.nE);
+            window_fill(win, thrE, lo_a, lo_a + kRing, 1, 0);
         }
-        Window wd{-(1 << 20), 0, 0};
-        uint32_t *const win = sm.win(slot < G ? slot : 0);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
         for (int k = 0; k < n_sweeps; ++k) {
             int e = c.ED - g.e_min;
+            lo_b = lo_a;  // the requests of the last sweep are complete when row 0 starts
+            uint32_t np[Lw];
+#pragma unroll
+            for (int j = 0; j < Lw; ++j) np[j] = 0u;
             int y = 0;
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 bar_sync(kBarReady + (r & 1), kWsThreads);
-                cp_async_wait_all();
-                wd.vlo = wd.lo;
-                wd.vhi = wd.lo + kRing;
-                if (active) window_recentre(wd, win, thrE, e, g.nE, 1, 0);
-                cp_async_commit();
                 if (active) {
                     const int b = r & 1;
                     const bool ycorr = (y != 0);  // the y-1 row is the one just finished
-                    const int nprev = (r + 2) % 3;
-                    uint32_t accb[NB];
-                    e = row_chain<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
-                                     sm.N(nprev, 0) + slot, ycorr, e, wd, win, thrE, accb);
-                    // the row's new spins
-#pragma unroll 1
-                    for (int j = 0; j < Lw; ++j) {
-                        uint32_t nwd = 0u;
+                    const int vlo = max(lo_a, lo_b), vhi = min(lo_a, lo_b) + kRing;
+                    uint32_t nn[Lw];
+                    int lo, hi;
+                    const int ce = row_chain_fast<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
+                                                     np, ycorr, e, win, nn, lo, hi);
+                    uint32_t *const nout = sm.N(r % 3, 0) + slot;
+                    if (lo >= vlo && hi < vhi) {
+                        e = ce;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int x = 4 * j + q;
-                            const uint32_t a = sm.desc(b, x)[slot];
-                            const uint32_t bits = (NB == 1 || x < 32) ? accb[0] : accb[NB - 1];
-                            const int sn = ((bits >> (x & 31)) & 1u) ? dsc_sp(a) : dsc_s(a);
-                            nwd |= (uint32_t)(sn & 0xFF) << (8 * q);
-                        }
-                        sm.N(r % 3, j)[slot] = nwd;
+                        for (int j = 0; j < Lw; ++j) nout[j * G] = nn[j];
+                    } else {
+                        e = row_chain_global<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
+                                                ycorr ? sm.N((r + 2) % 3, 0) + slot : nullptr, e,
+                                                thrE, nout);
+#pragma unroll
+                        for (int j = 0; j < Lw; ++j) nn[j] = nout[j * G];
                     }
+#pragma unroll
+                    for (int j = 0; j < Lw; ++j) np[j] = nn[j];
+                    // the window for the rows to come
+                    const int lo_c = window_target(lo_a, e, g.nE);
+                    int ra, rb;
+                    window_delta(lo_a, lo_c, ra, rb);
+                    sm.req(b, slot)[0] = ra;
+                    sm.req(b, slot)[1] = rb;
+                    lo_b = lo_a;
+                    lo_a = lo_c;
                 }
                 __syncwarp();
                 bar_arrive(kBarFree + (r & 1), kWsThreads);
@@ -774,7 +808,7 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                 c.M += sm.tal(slot)[1];
                 sm.tal(slot)[0] = 0;
                 sm.tal(slot)[1] = 0;
-                hist_add(g.hist, c.ED - g.e_min, lead_mask);
+                hist_add(g.hist, c.ED - g.e_min, amask);
                 if (RECORD) {
                     int32_t *o = g.ts + (ts_pos + k) * 3 * (int64_t)g.W + w;
                     o[0] = c.EJ;
@@ -792,96 +826,130 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
     } else {
         // ------------------------------------------------------------ helpers
         const int ht = tid - 32;
+        const int lgG = __ffs(G) - 1;
+        const int hs = ht & (G - 1);       // walker slot
+        const int hj0 = ht >> lgG;         // first word of the slot's rows
+        const int hstep = kWsHelp >> lgG;  // helpers per slot
+        const bool hact = hs < nw;
+        const uint32_t key0 = g.walker0 + (uint32_t)(bd.w0 + hs);
+        uint32_t *const hwin = sm.win(hs);
         for (int k = 0; k < n_sweeps; ++k) {
             const uint64_t sw = sweep0 + (uint64_t)k;
             const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
+            int dJ = 0, dM = 0;
             ws_stage<L>(sm, lat, st, 0, 0, ht);
 #pragma unroll 1
             for (int i = 0; i < R + 2; ++i) {
-                if (i >= 2) bar_sync(kBarFree + (i & 1), kWsThreads);
                 if (i >= 2) {
+                    bar_sync(kBarFree + (i & 1), kWsThreads);
                     // finish row jr = i - 2: store its new spins, add its energy changes
                     const int jr = i - 2;
-                    const int yj = jr % L;
-                    const bool nonwrap = (yj != 0);
+                    const bool nonwrap = (jr % L != 0);
                     const int bj = jr % 3, bp = (jr + 2) % 3;
-                    for (int it = ht; it < Lw * nw; it += kWsHelp) {
-                        const int j = it / nw, slot = it - j * nw;
-                        const uint32_t N0 = sm.N(bj, j)[slot], O0 = sm.O(bj, j)[slot];
-                        const int j1 = (j + 1 == Lw) ? 0 : j + 1;
-                        const uint32_t n1 = __funnelshift_r(N0, sm.N(bj, j1)[slot], 8);
-                        const uint32_t o1 = __funnelshift_r(O0, sm.O(bj, j1)[slot], 8);
-                        uint32_t Hw = sm.H(bj, j)[slot];
-                        if (nonwrap) Hw = __vadd4(Hw, sm.N(bp, j)[slot]);
-                        int dJ = -__dp4a((int)__vsub4(N0, O0), (int)Hw, 0);
-                        dJ -= __dp4a((int)N0, (int)n1, 0) - __dp4a((int)O0, (int)o1, 0);
-                        const int dM = __dp4a((int)N0, 0x01010101, 0) - __dp4a((int)O0, 0x01010101, 0);
-                        if (dJ) atomicAdd(sm.tal(slot), dJ);
-                        if (dM) atomicAdd(sm.tal(slot) + 1, dM);
-                        lat[((ptrdiff_t)jr * Lw + j) * st + slot] = N0;
+                    if (hact) {
+                        for (int j = hj0; j < Lw; j += hstep) {
+                            const uint32_t N0 = sm.N(bj, j)[hs], O0 = sm.O(bj, j)[hs];
+                            const int j1 = (j + 1 == Lw) ? 0 : j + 1;
+                            const uint32_t n1 = __funnelshift_r(N0, sm.N(bj, j1)[hs], 8);
+                            const uint32_t o1 = __funnelshift_r(O0, sm.O(bj, j1)[hs], 8);
+                            uint32_t Hw = sm.H(bj, j)[hs];
+                            if (nonwrap) Hw = __vadd4(Hw, sm.N(bp, j)[hs]);
+                            dJ -= __dp4a((int)__vsub4(N0, O0), (int)Hw, 0);
+                            dJ -= __dp4a((int)N0, (int)n1, 0) - __dp4a((int)O0, (int)o1, 0);
+                            dM += __dp4a((int)N0, 0x01010101, 0) - __dp4a((int)O0, 0x01010101, 0);
+                            lat[((ptrdiff_t)jr * Lw + j) * st + hs] = N0;
+                        }
+                        // the table rows the chain asked for at the end of row jr
+                        const int ra = sm.req(jr & 1, hs)[0], rb = sm.req(jr & 1, hs)[1];
+                        constexpr int kChunks = kRow / 4;
+                        for (int q = hj0; q < (rb - ra) * kChunks; q += hstep) {
+                            const int row = ra + q / kChunks, part = q - (q / kChunks) * kChunks;
+                            cp_async16(hwin + (row & (kRing - 1)) * kRow + 4 * part,
+                                       thrE + (ptrdiff_t)row * kRow + 4 * part);
+                        }
                     }
+                    cp_async_commit();
                 }
                 if (i < R) {
                     // prepare row i
-                    const int yi = i % L;
-                    const bool wrap = (yi == 0);
+                    const bool wrap = (i % L == 0);
                     const int bo = i % 3, b = i & 1;
                     cp_async_wait_all();
                     bar_sync(kBarHelp, kWsHelp);
-                    for (int it = ht; it < Lw * nw; it += kWsHelp) {
-                        const int j = it / nw, slot = it - j * nw;
-                        sm.O(bo, j)[slot] = sm.pf(4, j)[slot];
-                        uint32_t Hw = __vadd4(sm.pf(1, j)[slot],
-                                              __vadd4(sm.pf(2, j)[slot], sm.pf(3, j)[slot]));
-                        if (wrap) Hw = __vadd4(Hw, sm.pf(0, j)[slot]);
-                        sm.H(bo, j)[slot] = Hw;
-                    }
-                    for (int it = ht; it < Lw * nw; it += kWsHelp) {
-                        const int j = it / nw, slot = it - j * nw;
-                        const uint4 v = philox4x32_10(make_uint4((uint32_t)(i * Lw + j), slo, shi, 0u),
-                                                      g.walker0 + (uint32_t)(bd.w0 + slot), seed);
-                        sm.rnd(b, 4 * j)[slot] = v.x;
-                        sm.rnd(b, 4 * j + 1)[slot] = v.y;
-                        sm.rnd(b, 4 * j + 2)[slot] = v.z;
-                        sm.rnd(b, 4 * j + 3)[slot] = v.w;
+                    if (hact) {
+                        // old spins, neighbour sums, Philox words, proposals
+                        for (int j = hj0; j < Lw; j += hstep) {
+                            const uint32_t o = sm.pf(4, j)[hs];
+                            uint32_t Hw =
+                                __vadd4(sm.pf(1, j)[hs], __vadd4(sm.pf(2, j)[hs], sm.pf(3, j)[hs]));
+                            if (wrap) Hw = __vadd4(Hw, sm.pf(0, j)[hs]);
+                            sm.O(bo, j)[hs] = o;
+                            sm.H(bo, j)[hs] = Hw;
+                            const uint4 v = philox4x32_10(
+                                make_uint4((uint32_t)(i * Lw + j), slo, shi, 0u), key0, seed);
+                            sm.rnd(b, 4 * j)[hs] = v.x;
+                            sm.rnd(b, 4 * j + 1)[hs] = v.y;
+                            sm.rnd(b, 4 * j + 2)[hs] = v.z;
+                            sm.rnd(b, 4 * j + 3)[hs] = v.w;
+                            const uint32_t spw =
+                                ((uint32_t)proposal(sbyte(o, 0), v.x) & 0xFFu) |
+                                (((uint32_t)proposal(sbyte(o, 1), v.y) & 0xFFu) << 8) |
+                                (((uint32_t)proposal(sbyte(o, 2), v.z) & 0xFFu) << 16) |
+                                (((uint32_t)proposal(sbyte(o, 3), v.w) & 0xFFu) << 24);
+                            sm.SP(j)[hs] = spw;
+                        }
                     }
                     bar_sync(kBarHelp, kWsHelp);
-                    for (int it = ht; it < L * nw; it += kWsHelp) {
-                        const int x = it / nw, slot = it - x * nw;
-                        const int s = sbyte(sm.O(bo, x >> 2)[slot], x & 3);
-                        const int xr = (x + 1 == L) ? 0 : x + 1;  // old x = 0 for x = L - 1,
-                        const int right = sbyte(sm.O(bo, xr >> 2)[slot], xr & 3);  // corrected later
-                        const int base = sbyte(sm.H(bo, x >> 2)[slot], x & 3) + right;
-                        const int sp = proposal(s, sm.rnd(b, x)[slot]);
-                        const int d = sp * sp - s * s;
-                        const int kk = sp > s ? 1 : -1;
-                        const int c0 = kBlk * (d + 1) + 6 - kk * base;
-                        int ps, psp;
-                        if (x == 0) {
-                            ps = psp = sbyte(sm.O(bo, Lw - 1)[slot], 3);
-                        } else {
-                            ps = sbyte(sm.O(bo, (x - 1) >> 2)[slot], (x - 1) & 3);
-                            psp = proposal(ps, sm.rnd(b, x - 1)[slot]);
+                    if (hact) {
+                        // descriptors of the four sites of each word
+                        for (int j = hj0; j < Lw; j += hstep) {
+                            const int jl = (j == 0) ? Lw - 1 : j - 1, jn = (j + 1 == Lw) ? 0 : j + 1;
+                            const uint32_t o = sm.O(bo, j)[hs], spw = sm.SP(j)[hs];
+                            const uint32_t ol = sm.O(bo, jl)[hs], spl = sm.SP(jl)[hs];
+                            const uint32_t on = sm.O(bo, jn)[hs], Hw = sm.H(bo, j)[hs];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int s = sbyte(o, q), sp = sbyte(spw, q);
+                                // right neighbour: for x = L-1 the old site 0, corrected in the chain
+                                const int right = (q < 3) ? sbyte(o, q + 1) : sbyte(on, 0);
+                                const int base = sbyte(Hw, q) + right;
+                                const int d = sp * sp - s * s;
+                                const int kk = sp > s ? 1 : -1;
+                                const int c0 = kBlk * (d + 1) + 6 - kk * base;
+                                // left neighbour: site x-1 (for x = 0 the old site L-1)
+                                int ps, psp;
+                                if (q > 0) {
+                                    ps = sbyte(o, q - 1);
+                                    psp = sbyte(spw, q - 1);
+                                } else {
+                                    ps = sbyte(ol, 3);
+                                    psp = (j == 0) ? ps : sbyte(spl, 3);
+                                }
+                                const int pd = psp * psp - ps * ps;
+                                sm.desc(b, 4 * j + q)[hs] =
+                                    (uint32_t)(c0 - kk * psp) | ((uint32_t)(c0 - kk * ps) << 6) |
+                                    ((uint32_t)(pd + 1) << 12) | ((uint32_t)(d + 1) << 14) |
+                                    ((uint32_t)(sp + 1) << 16) | ((uint32_t)(s + 1) << 18) |
+                                    (kk > 0 ? (1u << 20) : 0u);
+                            }
                         }
-                        const int pd = (x == 0) ? 0 : psp * psp - ps * ps;
-                        sm.desc(b, x)[slot] =
-                            (uint32_t)(c0 - kk * psp) | ((uint32_t)(c0 - kk * ps) << 6) |
-                            ((uint32_t)(pd + 1) << 12) | ((uint32_t)(d + 1) << 14) |
-                            ((uint32_t)(sp + 1) << 16) | ((uint32_t)(s + 1) << 18) |
-                            (kk > 0 ? (1u << 20) : 0u);
                     }
                     bar_arrive(kBarReady + b, kWsThreads);
                 }
                 if (i + 1 < R) {
                     // the neighbourhood of row i + 1 (all stores of finished rows are done)
                     bar_sync(kBarHelp, kWsHelp);
-                    const int y1 = (i + 1) % L, z1 = (i + 1) / L;
-                    ws_stage<L>(sm, lat, st, y1, z1, ht);
+                    ws_stage<L>(sm, lat, st, (i + 1) % L, (i + 1) / L, ht);
                 }
+            }
+            if (hact) {
+                if (dJ) atomicAdd(sm.tal(hs), dJ);
+                if (dM) atomicAdd(sm.tal(hs) + 1, dM);
             }
             __syncthreads();
             __syncthreads();
         }
+        cp_async_wait_all();
     }
 }
 
