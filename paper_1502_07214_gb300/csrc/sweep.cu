@@ -669,9 +669,10 @@ constexpr int kWsWarps = 4;
 constexpr int kWsThreads = 32 * kWsWarps;
 constexpr int kWsHelp = kWsThreads - 32;
 constexpr int kBarReady = 1, kBarFree = 3, kBarHelp = 5;
-// shared words per walker slot: window, descriptors and random words, the
-// packed-word buffers (O, H, N x3, staged rows x5, proposals), requests, tallies
-constexpr int kWsWords = kRingStride + 4 * kMaxL + 15 * kMaxLw + 6;
+// shared words per walker slot: window, descriptors and random words x2, the
+// packed-word buffers (O, H, N x3, staged rows x5, proposals x2), acceptance
+// bits x2, window requests x2, tallies
+constexpr int kWsWords = kRingStride + 4 * kMaxL + 16 * kMaxLw + 4 + 4 + 2;
 
 __device__ __forceinline__ void bar_sync(int id, int n)
 {
@@ -698,10 +699,12 @@ struct WsSmem {
     __device__ uint32_t *H(int b, int j) const { return words(3 + b, j); }
     __device__ uint32_t *N(int b, int j) const { return words(6 + b, j); }
     __device__ uint32_t *pf(int f, int j) const { return words(9 + f, j); }
-    __device__ uint32_t *SP(int j) const { return words(14, j); }
-    __device__ int *ints() const { return (int *)(rest() + 4 * kMaxL * G + 15 * kMaxLw * G); }
-    __device__ int *req(int b, int slot) const { return ints() + 2 * (b * G + slot); }
-    __device__ int *tal(int slot) const { return ints() + 4 * G + 2 * slot; }
+    __device__ uint32_t *SP(int b, int j) const { return words(14 + b, j); }
+    __device__ uint32_t *ints() const { return rest() + 4 * kMaxL * G + 16 * kMaxLw * G; }
+    // acceptance bits of a row: word q (sites 32 q ..) of slot s
+    __device__ uint32_t *ACC(int b, int q, int slot) const { return ints() + (2 * b + q) * G + slot; }
+    __device__ int *req(int b, int slot) const { return (int *)ints() + 4 * G + 2 * (b * G + slot); }
+    __device__ int *tal(int slot) const { return (int *)ints() + 8 * G + 2 * slot; }
 };
 
 // Helpers: the five rows around row (y1, z1) of the block's walkers into pf.
@@ -722,6 +725,109 @@ __device__ __forceinline__ void ws_stage(const WsSmem &sm, const uint32_t *lat, 
         cp_async16(sm.pf(f, j) + 4 * k, lat + ((ptrdiff_t)row * Lw + j) * st + 4 * k);
     }
     cp_async_commit();
+}
+
+// Site descriptor of the split kernel (written by the helpers), one word:
+//   bits 0..5   column if site x-1 was accepted, 6..11 if it was rejected,
+//               both with the old spin of the y-1 neighbour in the sum
+//   bits 12..13 d = s'^2 - s^2 of site x's move, plus 1
+//   bits 14..16 q + 2: the column change when the y-1 neighbour (row r-1,
+//               same x) was accepted, -k (s'_y-1 - s_y-1); 0 on rows y = 0
+//   bits 17..19 (site L-1 only) Q + 2: its column change when site 0 of the
+//               same row was accepted
+// Random words are stored with bit 31 cleared (the chain's u).
+__device__ __forceinline__ int dw_colA(uint32_t a) { return (int)(a & 63u); }
+__device__ __forceinline__ int dw_colR(uint32_t a) { return (int)((a >> 6) & 63u); }
+__device__ __forceinline__ int dw_d(uint32_t a) { return (int)((a >> 12) & 3u) - 1; }
+__device__ __forceinline__ int dw_q(uint32_t a) { return (int)((a >> 14) & 7u) - 2; }
+__device__ __forceinline__ int dw_Q(uint32_t a) { return (int)((a >> 17) & 7u) - 2; }
+
+// The chain of the split kernel over one row, fully unrolled, from the
+// window (as row_chain_fast).  pacc: the acceptance bits of the y-1 row
+// (zero when it gives no correction); returns E_Delta's row at the row end
+// and the row's acceptance bits; lo_e / hi_e: the rows it read.
+template <int L>
+__device__ __forceinline__ int ws_chain_fast(const uint32_t *dsc, const uint32_t *rn, int stride,
+                                             const uint32_t (&pacc)[(L + 31) / 32], int e,
+                                             const uint32_t *win, uint32_t (&accb)[(L + 31) / 32],
+                                             int &lo_e, int &hi_e)
+{
+    constexpr int NB = (L + 31) / 32;
+    uint32_t A[L], U[L];
+#pragma unroll
+    for (int x = 0; x < L; ++x) {
+        A[x] = dsc[x * stride];
+        U[x] = rn[x * stride];
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) accb[q] = 0u;
+    auto ycc = [&](int x) { return ((pacc[x >> 5] >> (x & 31)) & 1u) ? dw_q(A[x]) : 0; };
+    int ce = e, lo = e, hi = e;
+    uint32_t t = win[(ce & (kRing - 1)) * kRow + dw_colR(A[0]) + ycc(0)];
+    int corr = 0;  // column change of site L-1: its x+1 is the new site 0
+#pragma unroll
+    for (int x = 0; x < L; ++x) {
+        int iA = 0, iR = 0;
+        if (x + 1 < L) {
+            int cc = ycc(x + 1);
+            if (x + 1 == L - 1) cc += corr;
+            iA = ((ce + dw_d(A[x])) & (kRing - 1)) * kRow + dw_colA(A[x + 1]) + cc;
+            iR = (ce & (kRing - 1)) * kRow + dw_colR(A[x + 1]) + cc;
+        }
+        const bool acc = U[x] < t;
+        if (x + 1 < L) t = win[acc ? iA : iR];
+        if (acc) {
+            ce += dw_d(A[x]);
+            accb[x >> 5] |= 1u << (x & 31);
+        }
+        lo = min(lo, ce);
+        hi = max(hi, ce);
+        if (x == 0) corr = acc ? dw_Q(A[L - 1]) : 0;
+    }
+    lo_e = lo;
+    hi_e = hi;
+    return ce;
+}
+
+// The same row from the global table, site by site (rows whose E_Delta left
+// the window).  pacc points to the y-1 row's acceptance bits (word q at
+// pacc[q * G]) or is nullptr; the row's bits go to accb[q * G].
+template <int L>
+__device__ __noinline__ int ws_chain_global(const uint32_t *dsc, const uint32_t *rn, int stride,
+                                            const uint32_t *pacc, int e,
+                                            const uint32_t *__restrict__ thrE, uint32_t *accb,
+                                            int G)
+{
+    bool prev = false;  // site x-1 accepted
+    int corr = 0;
+    uint32_t bits = 0u;
+#pragma unroll 1
+    for (int x = 0; x < L; ++x) {
+        const uint32_t a = dsc[x * stride];
+        int col = prev ? dw_colA(a) : dw_colR(a);
+        if (pacc && ((pacc[(x >> 5) * G] >> (x & 31)) & 1u)) col += dw_q(a);
+        if (x == L - 1) col += corr;
+        const bool acc = rn[x * stride] < __ldg(thrE + (ptrdiff_t)e * kRow + col);
+        if (acc) {
+            e += dw_d(a);
+            bits |= 1u << (x & 31);
+        }
+        if ((x & 31) == 31 || x == L - 1) {
+            accb[(x >> 5) * G] = bits;
+            bits = 0u;
+        }
+        if (x == 0) corr = acc ? dw_Q(dsc[(L - 1) * stride]) : 0;
+        prev = acc;
+    }
+    return e;
+}
+
+// Bytes of word j of a row's new spins: the proposal where the site's
+// acceptance bit is set, else the old spin.
+__device__ __forceinline__ uint32_t new_word(uint32_t old, uint32_t prop, uint32_t bits4)
+{
+    const uint32_t m = ((bits4 * 0x00204081u) & 0x01010101u) * 0xFFu;
+    return (prop & m) | (old & ~m);
 }
 
 template <int L, bool RECORD>
@@ -759,35 +865,33 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
         for (int k = 0; k < n_sweeps; ++k) {
             int e = c.ED - g.e_min;
             lo_b = lo_a;  // the requests of the last sweep are complete when row 0 starts
-            uint32_t np[Lw];
+            constexpr int NB = (L + 31) / 32;
+            uint32_t pacc[NB];  // acceptance bits of the previous row
 #pragma unroll
-            for (int j = 0; j < Lw; ++j) np[j] = 0u;
-            int y = 0;
+            for (int q = 0; q < NB; ++q) pacc[q] = 0u;
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 bar_sync(kBarReady + (r & 1), kWsThreads);
                 if (active) {
                     const int b = r & 1;
-                    const bool ycorr = (y != 0);  // the y-1 row is the one just finished
                     const int vlo = max(lo_a, lo_b), vhi = min(lo_a, lo_b) + kRing;
-                    uint32_t nn[Lw];
+                    uint32_t accb[NB];
                     int lo, hi;
-                    const int ce = row_chain_fast<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
-                                                     np, ycorr, e, win, nn, lo, hi);
-                    uint32_t *const nout = sm.N(r % 3, 0) + slot;
+                    const int ce = ws_chain_fast<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
+                                                    pacc, e, win, accb, lo, hi);
                     if (lo >= vlo && hi < vhi) {
                         e = ce;
 #pragma unroll
-                        for (int j = 0; j < Lw; ++j) nout[j * G] = nn[j];
+                        for (int q = 0; q < NB; ++q) sm.ACC(b, q, slot)[0] = accb[q];
                     } else {
-                        e = row_chain_global<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
-                                                ycorr ? sm.N((r + 2) % 3, 0) + slot : nullptr, e,
-                                                thrE, nout);
+                        e = ws_chain_global<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
+                                               sm.ACC(b ^ 1, 0, slot), e, thrE, sm.ACC(b, 0, slot),
+                                               G);
 #pragma unroll
-                        for (int j = 0; j < Lw; ++j) nn[j] = nout[j * G];
+                        for (int q = 0; q < NB; ++q) accb[q] = sm.ACC(b, q, slot)[0];
                     }
 #pragma unroll
-                    for (int j = 0; j < Lw; ++j) np[j] = nn[j];
+                    for (int q = 0; q < NB; ++q) pacc[q] = accb[q];
                     // the window for the rows to come
                     const int lo_c = window_target(lo_a, e, g.nE);
                     int ra, rb;
@@ -799,7 +903,6 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                 }
                 __syncwarp();
                 bar_arrive(kBarFree + (r & 1), kWsThreads);
-                y = (y + 1 == L) ? 0 : y + 1;
             }
             c.ED = e + g.e_min;
             __syncthreads();  // the helpers' tallies of this sweep are complete
@@ -845,12 +948,19 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                     // finish row jr = i - 2: store its new spins, add its energy changes
                     const int jr = i - 2;
                     const bool nonwrap = (jr % L != 0);
-                    const int bj = jr % 3, bp = (jr + 2) % 3;
+                    const int bj = jr % 3, bp = (jr + 2) % 3, ba = jr & 1;
                     if (hact) {
+                        // new spins of word jj of row jr from its acceptance bits
+                        auto nword = [&](int jj) {
+                            const uint32_t bits4 =
+                                (sm.ACC(ba, (4 * jj) >> 5, hs)[0] >> ((4 * jj) & 31)) & 15u;
+                            return new_word(sm.O(bj, jj)[hs], sm.SP(ba, jj)[hs], bits4);
+                        };
                         for (int j = hj0; j < Lw; j += hstep) {
-                            const uint32_t N0 = sm.N(bj, j)[hs], O0 = sm.O(bj, j)[hs];
+                            const uint32_t N0 = nword(j), O0 = sm.O(bj, j)[hs];
+                            sm.N(bj, j)[hs] = N0;
                             const int j1 = (j + 1 == Lw) ? 0 : j + 1;
-                            const uint32_t n1 = __funnelshift_r(N0, sm.N(bj, j1)[hs], 8);
+                            const uint32_t n1 = __funnelshift_r(N0, nword(j1), 8);
                             const uint32_t o1 = __funnelshift_r(O0, sm.O(bj, j1)[hs], 8);
                             uint32_t Hw = sm.H(bj, j)[hs];
                             if (nonwrap) Hw = __vadd4(Hw, sm.N(bp, j)[hs]);
@@ -887,26 +997,35 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                             sm.H(bo, j)[hs] = Hw;
                             const uint4 v = philox4x32_10(
                                 make_uint4((uint32_t)(i * Lw + j), slo, shi, 0u), key0, seed);
-                            sm.rnd(b, 4 * j)[hs] = v.x;
-                            sm.rnd(b, 4 * j + 1)[hs] = v.y;
-                            sm.rnd(b, 4 * j + 2)[hs] = v.z;
-                            sm.rnd(b, 4 * j + 3)[hs] = v.w;
+                            sm.rnd(b, 4 * j)[hs] = v.x & 0x7FFFFFFFu;
+                            sm.rnd(b, 4 * j + 1)[hs] = v.y & 0x7FFFFFFFu;
+                            sm.rnd(b, 4 * j + 2)[hs] = v.z & 0x7FFFFFFFu;
+                            sm.rnd(b, 4 * j + 3)[hs] = v.w & 0x7FFFFFFFu;
                             const uint32_t spw =
                                 ((uint32_t)proposal(sbyte(o, 0), v.x) & 0xFFu) |
                                 (((uint32_t)proposal(sbyte(o, 1), v.y) & 0xFFu) << 8) |
                                 (((uint32_t)proposal(sbyte(o, 2), v.z) & 0xFFu) << 16) |
                                 (((uint32_t)proposal(sbyte(o, 3), v.w) & 0xFFu) << 24);
-                            sm.SP(j)[hs] = spw;
+                            sm.SP(b, j)[hs] = spw;
                         }
                     }
                     bar_sync(kBarHelp, kWsHelp);
                     if (hact) {
                         // descriptors of the four sites of each word
+                        const int bq = (i + 2) % 3;  // row i-1: its old spins
+                        const int s0 = sbyte(sm.O(bo, 0)[hs], 0), sp0 = sbyte(sm.SP(b, 0)[hs], 0);
                         for (int j = hj0; j < Lw; j += hstep) {
                             const int jl = (j == 0) ? Lw - 1 : j - 1, jn = (j + 1 == Lw) ? 0 : j + 1;
-                            const uint32_t o = sm.O(bo, j)[hs], spw = sm.SP(j)[hs];
-                            const uint32_t ol = sm.O(bo, jl)[hs], spl = sm.SP(jl)[hs];
-                            const uint32_t on = sm.O(bo, jn)[hs], Hw = sm.H(bo, j)[hs];
+                            const uint32_t o = sm.O(bo, j)[hs], spw = sm.SP(b, j)[hs];
+                            const uint32_t ol = sm.O(bo, jl)[hs], spl = sm.SP(b, jl)[hs];
+                            const uint32_t on = sm.O(bo, jn)[hs];
+                            // neighbour sums with the old y-1 row; its changes: yo -> yp
+                            uint32_t Hw = sm.H(bo, j)[hs], yo = 0u, yp = 0u;
+                            if (!wrap) {
+                                yo = sm.O(bq, j)[hs];
+                                yp = sm.SP(b ^ 1, j)[hs];
+                                Hw = __vadd4(Hw, yo);
+                            }
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
                                 const int s = sbyte(o, q), sp = sbyte(spw, q);
@@ -925,12 +1044,12 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                                     ps = sbyte(ol, 3);
                                     psp = (j == 0) ? ps : sbyte(spl, 3);
                                 }
-                                const int pd = psp * psp - ps * ps;
+                                const int qy = -kk * (sbyte(yp, q) - sbyte(yo, q));
+                                const int qL = (4 * j + q == L - 1) ? -kk * (sp0 - s0) : 0;
                                 sm.desc(b, 4 * j + q)[hs] =
                                     (uint32_t)(c0 - kk * psp) | ((uint32_t)(c0 - kk * ps) << 6) |
-                                    ((uint32_t)(pd + 1) << 12) | ((uint32_t)(d + 1) << 14) |
-                                    ((uint32_t)(sp + 1) << 16) | ((uint32_t)(s + 1) << 18) |
-                                    (kk > 0 ? (1u << 20) : 0u);
+                                    ((uint32_t)(d + 1) << 12) | ((uint32_t)(qy + 2) << 14) |
+                                    ((uint32_t)(qL + 2) << 17);
                             }
                         }
                     }
