@@ -435,7 +435,17 @@ static int tune_group(muca_ctx *ctx, size_t gi, int residency, int wpb, int P)
     CK(cudaMalloc(&dg, sizeof(GroupDev)));
     ctx->d_groups = dg;
     int rc = upload_groups(ctx);
-    const int trial_sweeps = std::max(1, std::min(8, (int)(4096 * 4 / std::max(1, g.V))));
+    // Trials start from a relaxed copy: the sweeps right after a random start
+    // move E_Delta much faster than a running simulation does.
+    const int relax_sweeps = std::max(4, std::min(64, (1 << 22) / std::max(1, g.V)));
+    const int trial_sweeps = std::max(2, std::min(8, (1 << 18) / std::max(1, g.V)));
+    if (rc == MUCA_OK) {
+        ctx->g[0].residency = cands[0].res;
+        ctx->g[0].wpb = cands[0].wpb;
+        ctx->g[0].P = cands[0].P;
+        rc = build_blocks(ctx);
+    }
+    if (rc == MUCA_OK) rc = launch_all(ctx, relax_sweeps, false, ctx->stream);
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);

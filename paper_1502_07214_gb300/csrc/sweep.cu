@@ -637,37 +637,44 @@ sweep_smem_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restri
 // ---------------------------------------------------------------------------
 // Warp-specialised variant (global lattice, L % 4 == 0 up to 48).  A block is
 // kWsWarps warps: warp 0 runs the chains of the block's G walkers (one lane
-// each) and nothing else; warps 1..3 ("helpers") prepare the next row, finish
+// each) and nothing else; the other warps ("helpers") prepare the next row, finish
 // the previous one and keep the chains' table windows filled, so that the
 // per-row work overlaps the chain instead of adding to it:
-//   helpers, iteration i:  wait until the chain finished row i-2; store its new
-//     spins and accumulate its energy changes; copy the table rows the chain
-//     asked for at the end of row i-2 into its window; build the old spins and
-//     neighbour sums of row i from the staged rows, draw its Philox words and
-//     proposals, write its site descriptors; release row i to the chain;
-//     stage the neighbourhood of row i+1 (cp.async).
-//   chain, row r:  wait for row r; run the chain from the window; keep the
-//     row's new spins in registers (the y-1 neighbours of row r+1) and write
-//     them to shared memory; choose the window position for the rows to come;
-//     release the row's buffers.
+//   helpers, iteration i:  wait until the chain finished row i-2; form its new
+//     spins from its acceptance bits, store them and accumulate its energy
+//     changes; copy the table rows the chain asked for at the end of row i-2
+//     into its window; build the old spins and neighbour sums of row i from
+//     the staged rows, draw its Philox words and proposals, write its site
+//     descriptors; release row i to the chain; stage the neighbourhood of row
+//     i+1 (cp.async).
+//   chain, row r:  wait for row r; run the chain from the window; write the
+//     row's acceptance bits; choose the window position for the rows to
+//     come; release the row's buffers.
 // The only input of row r+1 that depends on row r's outcome is the y-1
-// neighbour: the helpers leave it out of the neighbour sums of non-wrapping
-// rows, and the chain adds -k N_r(x) to the column of site x itself.
+// neighbour.  The helpers form the columns of row r+1 with its old spins and
+// store, per site, the column change if it was accepted; the chain applies it
+// from the acceptance bits of row r, which it keeps in registers.  Likewise
+// for site L-1, whose x+1 neighbour is site 0 of the same row.
 // Window protocol: the rows asked for at the end of row r are copied by the
 // helpers while the chain runs row r+1 and are complete when row r+2 starts
 // (the helpers wait for their copies before they release a row), so row r+1
 // may trust only rows that are in both the previous and the new window.
-// Buffers: descriptors, random words and window requests double-buffered by
-// row parity; old spins, neighbour sums and new spins triple-buffered by row
-// mod 3.  Named barriers: ready[b] (helpers arrive, chain waits), free[b]
+// Buffers: descriptors, random words, proposals, acceptance bits and window
+// requests double-buffered by row parity; old spins, neighbour sums and new
+// spins triple-buffered by row mod 3.  Named barriers: ready[b] (helpers arrive, chain waits), free[b]
 // (chain arrives, helpers wait), and one among the helpers.  Helper thread ht
-// serves walker slot ht mod G and the words j = ht / G, ht / G + 96 / G, ...
+// serves walker slot ht mod G and the words j = ht / G, ht / G + kWsHelp / G, ...
 // of each row, so that its share of the energy changes belongs to one walker
 // and is summed in registers over the sweep.
 // ---------------------------------------------------------------------------
-constexpr int kWsWarps = 4;
+constexpr int kWsWarps = 8;
 constexpr int kWsThreads = 32 * kWsWarps;
-constexpr int kWsHelp = kWsThreads - 32;
+// Warp w of a block issues from scheduler w mod 4 of its SM.  Warp kWsIdle
+// shares the chain warp's scheduler and only waits at the sweep barriers, so
+// that no helper instruction competes with the chain for issue slots.
+constexpr int kWsIdle = 4;
+constexpr int kWsHelp = kWsThreads - 64;  // helper threads
+constexpr int kWsSync = 32 + kWsHelp;     // threads of the ready / free barriers
 constexpr int kBarReady = 1, kBarFree = 3, kBarHelp = 5;
 // shared words per walker slot: window, descriptors and random words x2, the
 // packed-word buffers (O, H, N x3, staged rows x5, proposals x2), acceptance
@@ -871,7 +878,7 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
             for (int q = 0; q < NB; ++q) pacc[q] = 0u;
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
-                bar_sync(kBarReady + (r & 1), kWsThreads);
+                bar_sync(kBarReady + (r & 1), kWsSync);
                 if (active) {
                     const int b = r & 1;
                     const int vlo = max(lo_a, lo_b), vhi = min(lo_a, lo_b) + kRing;
@@ -902,7 +909,7 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                     lo_a = lo_c;
                 }
                 __syncwarp();
-                bar_arrive(kBarFree + (r & 1), kWsThreads);
+                bar_arrive(kBarFree + (r & 1), kWsSync);
             }
             c.ED = e + g.e_min;
             __syncthreads();  // the helpers' tallies of this sweep are complete
@@ -926,9 +933,14 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
             g.tal[g.Wpad + w] = c.ED;
             g.tal[2 * g.Wpad + w] = c.M;
         }
+    } else if ((tid >> 5) == kWsIdle) {
+        for (int k = 0; k < n_sweeps; ++k) {
+            __syncthreads();
+            __syncthreads();
+        }
     } else {
         // ------------------------------------------------------------ helpers
-        const int ht = tid - 32;
+        const int ht = tid - ((tid >> 5) > kWsIdle ? 64 : 32);
         const int lgG = __ffs(G) - 1;
         const int hs = ht & (G - 1);       // walker slot
         const int hj0 = ht >> lgG;         // first word of the slot's rows
@@ -944,7 +956,7 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
 #pragma unroll 1
             for (int i = 0; i < R + 2; ++i) {
                 if (i >= 2) {
-                    bar_sync(kBarFree + (i & 1), kWsThreads);
+                    bar_sync(kBarFree + (i & 1), kWsSync);
                     // finish row jr = i - 2: store its new spins, add its energy changes
                     const int jr = i - 2;
                     const bool nonwrap = (jr % L != 0);
@@ -1053,7 +1065,7 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                             }
                         }
                     }
-                    bar_arrive(kBarReady + b, kWsThreads);
+                    bar_arrive(kBarReady + b, kWsSync);
                 }
                 if (i + 1 < R) {
                     // the neighbourhood of row i + 1 (all stores of finished rows are done)
@@ -1073,7 +1085,7 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
 }
 
 template <bool RECORD>
-__global__ void __launch_bounds__(kWsThreads)
+__global__ void __launch_bounds__(kWsThreads, 1)
 sweep_ws_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restrict__ blocks,
                 uint32_t seed, uint64_t sweep0, int n_sweeps, int64_t ts_pos)
 {
