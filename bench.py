@@ -375,8 +375,9 @@ def reweight_bench(torch, muca):
 def run_profile_case(what, cfg):
     """Short fixed launches for profiler captures (not timed): the sweep kernel
     of the benchmark workload in a given configuration "residency,walkers per
-    block,lanes per walker" (3 launches of 2 sweeps, no autotuning trials)
-    or the reweighting of the reweight workload (FP32 then FP64)."""
+    block,lanes per walker" (one launch of 100 sweeps that relaxes the random
+    start, then 2 launches of 2 sweeps; no autotuning trials) or the
+    reweighting of the reweight workload (FP32 then FP64)."""
     import torch
 
     from paper_1502_07214_gb300 import muca
@@ -388,7 +389,8 @@ def run_profile_case(what, cfg):
         ctx = muca.Context([{"L": s["L"], "T": s["T"], "n_walkers": s["n_walkers"]}],
                            seed=s["seed"], residency=res, walkers_per_block=wpb,
                            lanes_per_walker=lanes)
-        for _ in range(3):
+        ctx.sweep_iter(100)
+        for _ in range(2):
             ctx.sweep_iter(2)
         ctx.sync()
         print("profile case: sweep", ctx.get_config(0))
