@@ -49,6 +49,20 @@ def env_int(k, d):
         return d
 
 
+# DRAM bytes (read + write) per sweep of the benchmark workload, from one ncu
+# capture of the kernel in this configuration (profiles/sweep_ws_L48_4096w.md):
+# 926.8 MB read + 849.0 MB written over a launch of 2 sweeps.  Valid only for
+# the kernel source the counters were taken on.
+TRAFFIC_PER_SWEEP = {3: (926.833152e6 + 849.035776e6) / 2}
+
+
+def traffic_per_launch(res, sweeps):
+    """DRAM traffic of one launch of `sweeps` sweeps, scaled from the ncu
+    capture (traffic grows in proportion to the sweeps), or None."""
+    b = TRAFFIC_PER_SWEEP.get(res)
+    return None if b is None else b * sweeps
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -278,7 +292,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - q0
     e2e_value = attempts_step * e2e_steps * world / e2e_s
     nE = V + 1
-    h2d = nE * 32 * 4 + 16 * 4  # table upload of the merge
+    h2d = (nE + 4) * 40 * 4  # table upload of the merge (table rows incl. guards x 40 words)
     d2h = nE * 8 + meas * 3 * W * 4 + nE * 8 + grid.size * 5 * 8  # hist, series, lnW, results
 
     # reweighting sub-benchmark (FP32 vs FP64), rank 0 only
@@ -309,7 +323,8 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (lattice 453 MB int8)"},
             "plain": {"value": plain_value, "unit": UNIT, "steps": plain_steps},
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": int_peak / 1e12,
-                         "unit": "Tops/s", "frac": achieved_ops / int_peak, "traffic": None,
+                         "unit": "Tops/s", "frac": achieved_ops / int_peak,
+                         "traffic": traffic_per_launch(res, sweeps),
                          "kernel": {1: "sweep_global_kernel<false>", 2: "sweep_smem_kernel<false>",
                                     3: "sweep_ws_kernel<false>"}.get(res, str(res)),
                          "ops_per_attempt": ops_per_attempt,
