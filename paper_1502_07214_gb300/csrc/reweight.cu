@@ -37,8 +37,9 @@ struct Bins {
     unsigned long long *sej;   // sum E_J (two's complement)
     unsigned long long *sam;   // sum |M|
     unsigned long long *sm2;   // sum M^2
-    unsigned long long *sm4lo; // sum M^4, low 64 bits
-    unsigned long long *sm4hi; // sum M^4, high 64 bits
+    unsigned long long *sm4lo; // sum M^4 = sm4hi 2^shift + sm4lo
+    unsigned long long *sm4hi;
+    int shift;                 // 64 (two-word sum with carry) or 36 (two limb sums)
 };
 
 // Per-bin statistics consumed by stage B.
@@ -54,6 +55,11 @@ struct BinStats {
     F *lwlo; // FP32 only: lnW - hi
 };
 
+// LIMBS: M^4 (< 2^72) is split into 36-bit limbs summed separately, so that
+// every add is a fire-and-forget reduction; exact while a bin holds fewer than
+// 2^28 samples, which the host guarantees by the call's sample count.
+// Otherwise the low word's returned old value gives the carry into the high one.
+template <bool LIMBS>
 __global__ void bin_kernel(const int32_t *__restrict__ ej, const int32_t *__restrict__ ed,
                            const int32_t *__restrict__ m, int64_t n_rows, int row_len,
                            int64_t row_stride, int e_min, int nE, Bins b, int *err)
@@ -77,9 +83,16 @@ __global__ void bin_kernel(const int32_t *__restrict__ ej, const int32_t *__rest
             atomicAdd(b.sej + e, (unsigned long long)j);
             atomicAdd(b.sam + e, am);
             atomicAdd(b.sm2 + e, m2);
-            const unsigned long long old = atomicAdd(b.sm4lo + e, m4lo);
-            const unsigned long long carry = (old + m4lo < old) ? 1ull : 0ull;
-            if (m4hi + carry) atomicAdd(b.sm4hi + e, m4hi + carry);
+            if (LIMBS) {
+                const unsigned long long lo = m4lo & ((1ull << 36) - 1);
+                const unsigned long long hi = (m4lo >> 36) | (m4hi << 28);
+                atomicAdd(b.sm4lo + e, lo);
+                if (hi) atomicAdd(b.sm4hi + e, hi);
+            } else {
+                const unsigned long long old = atomicAdd(b.sm4lo + e, m4lo);
+                const unsigned long long carry = (old + m4lo < old) ? 1ull : 0ull;
+                if (m4hi + carry) atomicAdd(b.sm4hi + e, m4hi + carry);
+            }
         }
     }
 }
@@ -118,7 +131,9 @@ __global__ void stats_kernel_f64(Bins b, int nE, int V, const double *__restrict
     s.cm[e] = (double)sam / dn / dV;
     s.vb[e] = u128_to_double((unsigned long long)(v >> 64), (unsigned long long)v) / dn / dV / dV;
     s.q2[e] = (double)sm2 / dV / dV;
-    s.q4[e] = u128_to_double(b.sm4hi[e], b.sm4lo[e]) / dV / dV / dV / dV;
+    const unsigned __int128 q4 = ((unsigned __int128)b.sm4hi[e] << b.shift) + b.sm4lo[e];
+    s.q4[e] = u128_to_double((unsigned long long)(q4 >> 64), (unsigned long long)q4) / dV / dV /
+              dV / dV;
 }
 
 __global__ void stats_kernel_f32(Bins b, int nE, int V, const float *__restrict__ lw_hi,
@@ -144,7 +159,9 @@ __global__ void stats_kernel_f32(Bins b, int nE, int V, const float *__restrict_
     s.cm[e] = (float)sam / fn / fV;
     s.vb[e] = u128_to_float((unsigned long long)(v >> 64), (unsigned long long)v) / fn / fV / fV;
     s.q2[e] = (float)sm2 / fV / fV;
-    s.q4[e] = u128_to_float(b.sm4hi[e], b.sm4lo[e]) / fV / fV / fV / fV;
+    const unsigned __int128 q4 = ((unsigned __int128)b.sm4hi[e] << b.shift) + b.sm4lo[e];
+    s.q4[e] = u128_to_float((unsigned long long)(q4 >> 64), (unsigned long long)q4) / fV / fV /
+              fV / fV;
 }
 
 // ---------------------------------------------------------------- reductions
@@ -337,67 +354,109 @@ __device__ __forceinline__ F2 expo32(float chi, float clo, int E, float lwh, flo
     return {s, lo};
 }
 
+// One block serves kGridD consecutive Delta points, so that every bin's
+// statistics are read once per kGridD points; per point, the arithmetic and the
+// order of every sum are those of a block serving that point alone.
+constexpr int kGridD = 4;
+
+template <int D>
 __global__ void __launch_bounds__(256)
 grid_kernel_f32(BinStats<float> s, int nE, int e_min, float beta, int V,
-                const float *__restrict__ c_hi, const float *__restrict__ c_lo,
+                const float *__restrict__ c_hi, const float *__restrict__ c_lo, int n_grid,
                 double *__restrict__ out)
 {
     __shared__ float sh[64];
-    const int k = blockIdx.x;
-    const float ch = c_hi[k], cl = c_lo[k];
-    float amax = -INFINITY;
+    const int k0 = blockIdx.x * D;
+    float ch[D], cl[D], amax[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const int k = min(k0 + d, n_grid - 1);
+        ch[d] = c_hi[k];
+        cl[d] = c_lo[k];
+        amax[d] = -INFINITY;
+    }
     for (int e = threadIdx.x; e < nE; e += blockDim.x)
         if (s.n[e] > 0.f) {
-            const F2 a = expo32(ch, cl, e_min + e, s.lw[e], s.lwlo[e]);
-            amax = fmaxf(amax, a.hi);
-        }
-    amax = block_max(amax, sh);
-    KSum<float> acc[6];
+            const float lh = s.lw[e], ll = s.lwlo[e];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) acc[i].init();
+            for (int d = 0; d < D; ++d)
+                amax[d] = fmaxf(amax[d], expo32(ch[d], cl[d], e_min + e, lh, ll).hi);
+        }
+#pragma unroll
+    for (int d = 0; d < D; ++d) amax[d] = block_max(amax[d], sh);
+    KSum<float> acc[D][6];
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[d][i].init();
     for (int e = threadIdx.x; e < nE; e += blockDim.x) {
         const float n = s.n[e];
         if (n <= 0.f) continue;
-        const F2 a = expo32(ch, cl, e_min + e, s.lw[e], s.lwlo[e]);
-        const float d = (a.hi - amax) + a.lo;
-        if (d < -104.f) continue;
-        const float w = expf(d);
-        const float wn = w * n;
-        acc[0].add(wn);
-        acc[1].add(wn * (float)(e_min + e));
-        acc[2].add(wn * s.mej[e]);
-        acc[3].add(wn * s.cm[e]);
-        acc[4].add(w * s.q2[e]);
-        acc[5].add(w * s.q4[e]);
+        const float lh = s.lw[e], ll = s.lwlo[e], mej = s.mej[e], cm = s.cm[e], q2 = s.q2[e],
+                    q4 = s.q4[e];
+        const float fe = (float)(e_min + e);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const F2 a = expo32(ch[d], cl[d], e_min + e, lh, ll);
+            const float x = (a.hi - amax[d]) + a.lo;
+            if (x < -104.f) continue;
+            const float w = expf(x);
+            const float wn = w * n;
+            acc[d][0].add(wn);
+            acc[d][1].add(wn * fe);
+            acc[d][2].add(wn * mej);
+            acc[d][3].add(wn * cm);
+            acc[d][4].add(w * q2);
+            acc[d][5].add(w * q4);
+        }
     }
-    float S[6];
-    block_sum<float, 6>(acc, S, sh);
-    const float Z = S[0], mE = S[1] / Z, mJ = S[2] / Z, mu = S[3] / Z;
-    KSum<float> acc2[2];
-    acc2[0].init();
-    acc2[1].init();
+    float Z[D], mE[D], mJ[D], mu[D], m2[D], m4[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        float S[6];
+        block_sum<float, 6>(acc[d], S, sh);
+        Z[d] = S[0];
+        mE[d] = S[1] / Z[d];
+        mJ[d] = S[2] / Z[d];
+        mu[d] = S[3] / Z[d];
+        m2[d] = S[4] / Z[d];
+        m4[d] = S[5] / Z[d];
+    }
+    KSum<float> acc2[D][2];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        acc2[d][0].init();
+        acc2[d][1].init();
+    }
     for (int e = threadIdx.x; e < nE; e += blockDim.x) {
         const float n = s.n[e];
         if (n <= 0.f) continue;
-        const F2 a = expo32(ch, cl, e_min + e, s.lw[e], s.lwlo[e]);
-        const float d = (a.hi - amax) + a.lo;
-        if (d < -104.f) continue;
-        const float w = expf(d);
-        const float wn = w * n;
-        acc2[0].add(wn * ((s.mej[e] - mJ) * ((float)(e_min + e) - mE)));
-        const float dm = s.cm[e] - mu;
-        acc2[1].add(w * s.vb[e] + wn * (dm * dm));
+        const float lh = s.lw[e], ll = s.lwlo[e], mej = s.mej[e], cm = s.cm[e], vb = s.vb[e];
+        const float fe = (float)(e_min + e);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const F2 a = expo32(ch[d], cl[d], e_min + e, lh, ll);
+            const float x = (a.hi - amax[d]) + a.lo;
+            if (x < -104.f) continue;
+            const float w = expf(x);
+            const float wn = w * n;
+            acc2[d][0].add(wn * ((mej - mJ[d]) * (fe - mE[d])));
+            const float dm = cm - mu[d];
+            acc2[d][1].add(w * vb + wn * (dm * dm));
+        }
     }
-    float S2[2];
-    block_sum<float, 2>(acc2, S2, sh);
-    if (threadIdx.x == 0) {
-        double *o = out + 5 * (int64_t)k;
-        o[0] = mJ;
-        o[1] = mE;
-        o[2] = -beta * (S2[0] / Z);
-        o[3] = beta * (float)V * (S2[1] / Z);
-        const float m2 = S[4] / Z, m4 = S[5] / Z;
-        o[4] = 1.f - m4 / (3.f * m2 * m2);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        float S2[2];
+        block_sum<float, 2>(acc2[d], S2, sh);
+        if (threadIdx.x == 0 && k0 + d < n_grid) {
+            double *o = out + 5 * (int64_t)(k0 + d);
+            o[0] = mJ[d];
+            o[1] = mE[d];
+            o[2] = -beta * (S2[0] / Z[d]);
+            o[3] = beta * (float)V * (S2[1] / Z[d]);
+            o[4] = 1.f - m4[d] / (3.f * m2[d] * m2[d]);
+        }
     }
 }
 
@@ -441,6 +500,9 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
     b.sm2 = b.sam + n_e;
     b.sm4lo = b.sm2 + n_e;
     b.sm4hi = b.sm4lo + n_e;
+    b.shift = ((unsigned __int128)n_rows * (uint64_t)std::max(row_len, 0) < ((unsigned __int128)1 << 28))
+                  ? 36
+                  : 64;
     char *ps = p + L.bins;
     char *pg = ps + L.stats;
     double *d_out = (double *)(pg + L.grid);
@@ -457,8 +519,12 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
     if (n_rows > 0 && row_len > 0) {
         dim3 grid((unsigned)std::min<int64_t>((row_len + 255) / 256, 1024),
                   (unsigned)std::min<int64_t>(n_rows, 4096));
-        bin_kernel<<<grid, 256, 0, st>>>(e_j, e_d, m, n_rows, row_len, row_stride, e_min, n_e, b,
-                                         d_err);
+        if (b.shift == 36)
+            bin_kernel<true><<<grid, 256, 0, st>>>(e_j, e_d, m, n_rows, row_len, row_stride,
+                                                   e_min, n_e, b, d_err);
+        else
+            bin_kernel<false><<<grid, 256, 0, st>>>(e_j, e_d, m, n_rows, row_len, row_stride,
+                                                    e_min, n_e, b, d_err);
         RCK(cudaGetLastError());
     }
     const int sb = (n_e + 255) / 256;
@@ -517,8 +583,8 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
         stats_kernel_f32<<<sb, 256, 0, st>>>(b, n_e, V, d_lh, d_ll, s);
         RCK(cudaGetLastError());
         if (n_grid > 0)
-            grid_kernel_f32<<<n_grid, 256, 0, st>>>(s, n_e, e_min, (float)beta, V, d_ch, d_cl,
-                                                    d_out);
+            grid_kernel_f32<kGridD><<<(n_grid + kGridD - 1) / kGridD, 256, 0, st>>>(
+                s, n_e, e_min, (float)beta, V, d_ch, d_cl, n_grid, d_out);
         RCK(cudaGetLastError());
         RCK(cudaStreamSynchronize(st));
     }
