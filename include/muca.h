@@ -158,8 +158,11 @@ int muca_run_graph(muca_ctx *ctx, int n_iters, int sweeps_per_iter);
  *                 chi = beta V (<m^2> - <|m|>^2), U4 = 1 - <m^4> / (3 <m^2>^2),
  *                 m = M / V
  *   stream        cudaStream_t for the work (NULL = legacy default stream)
- * Allocates its scratch with cudaMallocAsync on the stream; synchronises the
- * stream before returning. */
+ * Working memory (per-bin sums, and up to 8 bytes per sample for at most 2^26
+ * samples at a time) comes from a device memory pool that the library creates
+ * on the device at the first call and keeps until the process exits; the pool
+ * keeps what it has held, so it holds the largest call's working memory.
+ * Synchronises the stream before returning. */
 int muca_reweight(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n_rows,
                   int32_t row_len, int64_t row_stride, const double *lnW, int32_t e_min,
                   int32_t n_e, double beta, int32_t V, const double *delta_grid, int32_t n_grid,

@@ -91,10 +91,15 @@ int reweight_check_args(const int32_t *e_j, const int32_t *e_d, const int32_t *m
                         double beta, int32_t V, const double *delta_grid, int32_t n_grid,
                         int32_t precision, double *out);
 size_t reweight_scratch_bytes(int32_t n_e, int32_t n_grid, int32_t precision);
+// records / records_bytes: an optional second device region (at most
+// reweight_record_bytes(n_e, samples) bytes are used) that lets stage A sum
+// the samples in shared memory per bucket of bins; without it (nullptr, 0)
+// every sample adds to the global bin sums directly.
+size_t reweight_record_bytes(int32_t n_e, int64_t n_samples);
 int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n_rows,
                         int32_t row_len, int64_t row_stride, const double *lnW, int32_t e_min,
                         int32_t n_e, double beta, int32_t V, const double *delta_grid,
                         int32_t n_grid, int32_t precision, double *out, cudaStream_t st,
-                        char *scratch);
+                        char *scratch, char *records = nullptr, size_t records_bytes = 0);
 
 }  // namespace muca

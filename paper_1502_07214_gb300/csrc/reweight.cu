@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -94,6 +95,168 @@ __global__ void bin_kernel(const int32_t *__restrict__ ej, const int32_t *__rest
                 if (m4hi + carry) atomicAdd(b.sm4hi + e, m4hi + carry);
             }
         }
+    }
+}
+
+// ------------------------------------------------- stage A through buckets
+// The same integer bin sums, formed without one global atomic per sample:
+// samples are counted per bucket of kBkt consecutive bins, scattered into
+// bucket order as 8-byte records, and each bucket's records are summed in
+// shared memory before one global add per bin and block.  A record holds the
+// bin offset, E_J (|E_J| < 2^20) and |M| (<= 2^18, so M^4 < 2^72); a sample
+// outside those ranges is added straight to the global sums instead and
+// leaves a null record.
+constexpr int kBktBits = 11;
+constexpr int kBkt = 1 << kBktBits;
+constexpr unsigned kNullRec = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void direct_add(const Bins &b, int e, long long j, unsigned long long am)
+{
+    const unsigned long long m2 = am * am;
+    const unsigned long long m4lo = m2 * m2, m4hi = __umul64hi(m2, m2);
+    atomicAdd(b.cnt + e, 1ull);
+    atomicAdd(b.sej + e, (unsigned long long)j);
+    atomicAdd(b.sam + e, am);
+    atomicAdd(b.sm2 + e, m2);
+    const unsigned long long old = atomicAdd(b.sm4lo + e, m4lo);
+    const unsigned long long carry = (old + m4lo < old) ? 1ull : 0ull;
+    if (m4hi + carry) atomicAdd(b.sm4hi + e, m4hi + carry);
+}
+
+// Samples per bucket; flags a sample outside [e_min, e_min + nE).
+__global__ void bucket_count_kernel(const int32_t *__restrict__ ed, int64_t n_rows, int row_len,
+                                    int64_t row_stride, int e_min, int nE, int nbk,
+                                    unsigned *cnt, int *err)
+{
+    extern __shared__ unsigned sc[];
+    for (int i = threadIdx.x; i < nbk; i += blockDim.x) sc[i] = 0u;
+    __syncthreads();
+    for (int64_t r = blockIdx.y; r < n_rows; r += gridDim.y)
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < row_len;
+             c += gridDim.x * blockDim.x) {
+            const int e = __ldg(ed + r * row_stride + c) - e_min;
+            if (e < 0 || e >= nE) atomicOr(err, 1);
+            else atomicAdd(&sc[e >> kBktBits], 1u);
+        }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbk; i += blockDim.x)
+        if (sc[i]) atomicAdd(cnt + i, sc[i]);
+}
+
+// Records into bucket order: bucket k occupies [start_k, start_k + cnt_k),
+// start the prefix sums of cnt; cur[k] hands out the blocks' places in it.
+__global__ void __launch_bounds__(1024)
+bucket_scatter_kernel(const int32_t *__restrict__ ej, const int32_t *__restrict__ ed,
+                      const int32_t *__restrict__ m, int64_t n_rows, int row_len,
+                      int64_t row_stride, int e_min, int nE, int nbk,
+                      const unsigned *__restrict__ cnt, unsigned *cur, uint2 *rec, Bins b)
+{
+    extern __shared__ unsigned s2[];
+    unsigned *start = s2, *lc = s2 + nbk, *base = s2 + 2 * nbk;
+    if (threadIdx.x == 0) {
+        unsigned acc = 0u;
+        for (int i = 0; i < nbk; ++i) {
+            start[i] = acc;
+            acc += cnt[i];
+        }
+    }
+    for (int64_t r = blockIdx.y; r < n_rows; r += gridDim.y)
+        for (int c0 = blockIdx.x * blockDim.x; c0 < row_len; c0 += gridDim.x * blockDim.x) {
+            for (int i = threadIdx.x; i < nbk; i += blockDim.x) lc[i] = 0u;
+            __syncthreads();
+            const int c = c0 + threadIdx.x;
+            int e = -1, bk = 0;
+            unsigned rank = 0u;
+            if (c < row_len) {
+                const int64_t o = r * row_stride + c;
+                e = __ldg(ed + o) - e_min;
+                if (e >= 0 && e < nE) {
+                    bk = e >> kBktBits;
+                    rank = atomicAdd(&lc[bk], 1u);
+                } else {
+                    e = -1;
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nbk; i += blockDim.x)
+                if (lc[i]) base[i] = atomicAdd(cur + i, lc[i]);
+            __syncthreads();
+            if (e >= 0) {
+                const int64_t o = r * row_stride + c;
+                const int j = __ldg(ej + o), mm = __ldg(m + o);
+                const unsigned am = mm < 0 ? 0u - (unsigned)mm : (unsigned)mm;
+                uint2 rr;
+                if (j > -(1 << 20) && j < (1 << 20) && am <= (1u << 18)) {
+                    rr.x = (unsigned)(e & (kBkt - 1)) | ((unsigned)(j + (1 << 20)) << kBktBits);
+                    rr.y = am;
+                } else {
+                    direct_add(b, e, j, am);
+                    rr.x = 0u;
+                    rr.y = kNullRec;
+                }
+                rec[start[bk] + base[bk] + rank] = rr;
+            }
+            __syncthreads();
+        }
+}
+
+// Sums of bucket blockIdx.y's records in shared memory (M^4 as 36-bit limbs,
+// exact for the at most 2^26 records of a pass), then one global add per bin.
+constexpr int kHistThreads = 512;
+constexpr size_t kHistSmem = (size_t)kBkt * (5 * sizeof(unsigned long long) + sizeof(unsigned));
+
+__global__ void __launch_bounds__(kHistThreads)
+bucket_hist_kernel(const uint2 *__restrict__ rec, const unsigned *__restrict__ cnt, Bins b)
+{
+    extern __shared__ __align__(16) unsigned long long h64[];
+    unsigned long long *sej = h64, *sam = h64 + kBkt, *sm2 = h64 + 2 * kBkt, *l4 = h64 + 3 * kBkt,
+                       *h4 = h64 + 4 * kBkt;
+    unsigned *sc = (unsigned *)(h64 + 5 * kBkt);
+    __shared__ unsigned s_start, s_n;
+    const int bk = blockIdx.y;
+    if (threadIdx.x == 0) {
+        unsigned acc = 0u;
+        for (int i = 0; i < bk; ++i) acc += cnt[i];
+        s_start = acc;
+        s_n = cnt[bk];
+    }
+    __syncthreads();
+    const unsigned start = s_start, n = s_n;
+    if ((unsigned long long)blockIdx.x * blockDim.x >= n) return;
+    for (int i = threadIdx.x; i < kBkt; i += blockDim.x) {
+        sej[i] = sam[i] = sm2[i] = l4[i] = h4[i] = 0ull;
+        sc[i] = 0u;
+    }
+    __syncthreads();
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint2 r = rec[start + i];
+        if (r.y == kNullRec) continue;
+        const int eo = (int)(r.x & (kBkt - 1));
+        const long long j = (long long)(r.x >> kBktBits) - (1 << 20);
+        const unsigned long long am = r.y, m2 = am * am;
+        const unsigned long long m4lo = m2 * m2, m4hi = __umul64hi(m2, m2);
+        atomicAdd(&sc[eo], 1u);
+        atomicAdd(&sej[eo], (unsigned long long)j);
+        atomicAdd(&sam[eo], am);
+        atomicAdd(&sm2[eo], m2);
+        atomicAdd(&l4[eo], m4lo & ((1ull << 36) - 1));
+        const unsigned long long hi = (m4lo >> 36) | (m4hi << 28);
+        if (hi) atomicAdd(&h4[eo], hi);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBkt; i += blockDim.x) {
+        const unsigned k = sc[i];
+        if (!k) continue;
+        const int e = bk * kBkt + i;
+        atomicAdd(b.cnt + e, (unsigned long long)k);
+        atomicAdd(b.sej + e, sej[i]);
+        atomicAdd(b.sam + e, sam[i]);
+        atomicAdd(b.sm2 + e, sm2[i]);
+        const unsigned __int128 q = ((unsigned __int128)h4[i] << 36) + l4[i];
+        const unsigned long long lo = (unsigned long long)q, hi = (unsigned long long)(q >> 64);
+        const unsigned long long old = atomicAdd(b.sm4lo + e, lo);
+        const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+        if (hi + carry) atomicAdd(b.sm4hi + e, hi + carry);
     }
 }
 
@@ -479,9 +642,23 @@ Scratch scratch_layout(int nE, int n_grid, int precision)
     return s;
 }
 
+// Bytes of the bucket counters at the start of a record buffer (256-byte aligned).
+size_t bucket_counter_bytes(int nE)
+{
+    const size_t nbk = ((size_t)nE + kBkt - 1) >> kBktBits;
+    return (2 * nbk * sizeof(unsigned) + 255) & ~(size_t)255;
+}
+
 }  // namespace
 
 namespace muca {
+
+size_t reweight_record_bytes(int32_t n_e, int64_t n_samples)
+{
+    const int64_t cap = std::min<int64_t>(n_samples, (int64_t)1 << 26);
+    return bucket_counter_bytes(n_e) + (size_t)std::max<int64_t>(cap, 0) * sizeof(uint2);
+}
+
 
 // The whole reweighting on a caller-provided scratch region of
 // scratch_layout(...).total bytes (device memory).
@@ -489,7 +666,7 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
                         int32_t row_len, int64_t row_stride, const double *lnW, int32_t e_min,
                         int32_t n_e, double beta, int32_t V, const double *delta_grid,
                         int32_t n_grid, int32_t precision, double *out, cudaStream_t st,
-                        char *scratch)
+                        char *scratch, char *records, size_t records_bytes)
 {
     const Scratch L = scratch_layout(n_e, n_grid, precision);
     char *p = scratch;
@@ -516,7 +693,41 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
     } while (0)
     RCK(cudaMemsetAsync(p, 0, L.bins, st));
     RCK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-    if (n_rows > 0 && row_len > 0) {
+    const int nbk = (n_e + kBkt - 1) >> kBktBits;
+    const size_t rec_cap =
+        records ? (records_bytes - std::min(records_bytes, bucket_counter_bytes(n_e))) / sizeof(uint2)
+                : 0;
+    if (n_rows > 0 && row_len > 0 && (size_t)row_len <= rec_cap) {
+        // stage A through buckets, a pass of at most rec_cap samples at a time
+        unsigned *d_cnt = (unsigned *)records, *d_cur = d_cnt + nbk;
+        uint2 *d_rec = (uint2 *)(records + bucket_counter_bytes(n_e));
+        b.shift = 64;
+        int dev = 0, nsm = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        RCK(cudaFuncSetAttribute(bucket_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHistSmem));
+        const int64_t rows_pass = std::min<int64_t>(n_rows, (int64_t)(rec_cap / (size_t)row_len));
+        for (int64_t r0 = 0; r0 < n_rows; r0 += rows_pass) {
+            const int64_t nr = std::min(rows_pass, n_rows - r0);
+            const int64_t off = r0 * row_stride;
+            RCK(cudaMemsetAsync(d_cnt, 0, 2 * (size_t)nbk * sizeof(unsigned), st));
+            dim3 g1((unsigned)std::min<int64_t>((row_len + 255) / 256, 1024),
+                    (unsigned)std::min<int64_t>(nr, 4096));
+            bucket_count_kernel<<<g1, 256, nbk * sizeof(unsigned), st>>>(
+                e_d + off, nr, row_len, row_stride, e_min, n_e, nbk, d_cnt, d_err);
+            RCK(cudaGetLastError());
+            dim3 g2((unsigned)std::min<int64_t>((row_len + 1023) / 1024, 1024),
+                    (unsigned)std::min<int64_t>(nr, 4096));
+            bucket_scatter_kernel<<<g2, 1024, 3 * nbk * sizeof(unsigned), st>>>(
+                e_j + off, e_d + off, m + off, nr, row_len, row_stride, e_min, n_e, nbk, d_cnt,
+                d_cur, d_rec, b);
+            RCK(cudaGetLastError());
+            dim3 g3((unsigned)std::max(1, (2 * nsm + nbk - 1) / nbk), (unsigned)nbk);
+            bucket_hist_kernel<<<g3, kHistThreads, kHistSmem, st>>>(d_rec, d_cnt, b);
+            RCK(cudaGetLastError());
+        }
+    } else if (n_rows > 0 && row_len > 0) {
         dim3 grid((unsigned)std::min<int64_t>((row_len + 255) / 256, 1024),
                   (unsigned)std::min<int64_t>(n_rows, 4096));
         if (b.shift == 36)
@@ -629,6 +840,41 @@ int reweight_check_args(const int32_t *e_j, const int32_t *e_d, const int32_t *m
 
 }  // namespace muca
 
+// Device memory pool of the reweighting on the current device, created on
+// first use.  It keeps what it has once held (release threshold: all), so that
+// repeated calls do not map and unmap their working memory each time.
+static int reweight_pool(cudaMemPool_t *out)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = -1;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess)
+        return rw_fail(MUCA_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
+    if (dev < 0 || dev >= 64) return rw_fail(MUCA_ERR_NOT_SUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        ce = cudaMemPoolCreate(&p, &props);
+        if (ce != cudaSuccess)
+            return rw_fail(MUCA_ERR_CUDA, std::string("cudaMemPoolCreate: ") + cudaGetErrorString(ce));
+        uint64_t keep = ~0ull;
+        ce = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (ce != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return rw_fail(MUCA_ERR_CUDA, std::string("cudaMemPoolSetAttribute: ") +
+                                              cudaGetErrorString(ce));
+        }
+        pools[dev] = p;
+    }
+    *out = pools[dev];
+    return MUCA_OK;
+}
+
 extern "C" int muca_reweight(const int32_t *e_j, const int32_t *e_d, const int32_t *m,
                              int64_t n_rows, int32_t row_len, int64_t row_stride,
                              const double *lnW, int32_t e_min, int32_t n_e, double beta, int32_t V,
@@ -640,13 +886,18 @@ extern "C" int muca_reweight(const int32_t *e_j, const int32_t *e_d, const int32
     if (rc != MUCA_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = muca::reweight_scratch_bytes(n_e, n_grid, precision);
+    const size_t rbytes = muca::reweight_record_bytes(n_e, n_rows * (int64_t)row_len);
+    cudaMemPool_t pool = nullptr;
+    rc = reweight_pool(&pool);
+    if (rc != MUCA_OK) return rc;
     void *scratch = nullptr;
-    cudaError_t ce = cudaMallocAsync(&scratch, bytes, st);
+    cudaError_t ce = cudaMallocFromPoolAsync(&scratch, bytes + rbytes, pool, st);
     if (ce != cudaSuccess)
         return rw_fail(ce == cudaErrorMemoryAllocation ? MUCA_ERR_OOM : MUCA_ERR_CUDA,
                        std::string("cudaMallocAsync: ") + cudaGetErrorString(ce));
     rc = muca::reweight_on_scratch(e_j, e_d, m, n_rows, row_len, row_stride, lnW, e_min, n_e, beta,
-                                   V, delta_grid, n_grid, precision, out, st, (char *)scratch);
+                                   V, delta_grid, n_grid, precision, out, st, (char *)scratch,
+                                   (char *)scratch + bytes, rbytes);
     cudaFreeAsync(scratch, st);
     cudaStreamSynchronize(st);
     return rc;
