@@ -38,9 +38,8 @@ struct Bins {
     unsigned long long *sej;   // sum E_J (two's complement)
     unsigned long long *sam;   // sum |M|
     unsigned long long *sm2;   // sum M^2
-    unsigned long long *sm4lo; // sum M^4 = sm4hi 2^shift + sm4lo
-    unsigned long long *sm4hi;
-    int shift;                 // 64 (two-word sum with carry) or 36 (two limb sums)
+    unsigned long long *sm4lo; // sum M^4, low 64 bits
+    unsigned long long *sm4hi; // sum M^4, high 64 bits
 };
 
 // Per-bin statistics consumed by stage B.
@@ -56,11 +55,9 @@ struct BinStats {
     F *lwlo; // FP32 only: lnW - hi
 };
 
-// LIMBS: M^4 (< 2^72) is split into 36-bit limbs summed separately, so that
-// every add is a fire-and-forget reduction; exact while a bin holds fewer than
-// 2^28 samples, which the host guarantees by the call's sample count.
-// Otherwise the low word's returned old value gives the carry into the high one.
-template <bool LIMBS>
+// Stage A, one sample at a time: every sum of every sample is a 64-bit
+// atomic add into the global bin sums; M^4 is a 128-bit sum whose low word's
+// returned old value gives the carry into the high word.
 __global__ void bin_kernel(const int32_t *__restrict__ ej, const int32_t *__restrict__ ed,
                            const int32_t *__restrict__ m, int64_t n_rows, int row_len,
                            int64_t row_stride, int e_min, int nE, Bins b, int *err)
@@ -84,16 +81,9 @@ __global__ void bin_kernel(const int32_t *__restrict__ ej, const int32_t *__rest
             atomicAdd(b.sej + e, (unsigned long long)j);
             atomicAdd(b.sam + e, am);
             atomicAdd(b.sm2 + e, m2);
-            if (LIMBS) {
-                const unsigned long long lo = m4lo & ((1ull << 36) - 1);
-                const unsigned long long hi = (m4lo >> 36) | (m4hi << 28);
-                atomicAdd(b.sm4lo + e, lo);
-                if (hi) atomicAdd(b.sm4hi + e, hi);
-            } else {
-                const unsigned long long old = atomicAdd(b.sm4lo + e, m4lo);
-                const unsigned long long carry = (old + m4lo < old) ? 1ull : 0ull;
-                if (m4hi + carry) atomicAdd(b.sm4hi + e, m4hi + carry);
-            }
+            const unsigned long long old = atomicAdd(b.sm4lo + e, m4lo);
+            const unsigned long long carry = (old + m4lo < old) ? 1ull : 0ull;
+            if (m4hi + carry) atomicAdd(b.sm4hi + e, m4hi + carry);
         }
     }
 }
@@ -294,9 +284,7 @@ __global__ void stats_kernel_f64(Bins b, int nE, int V, const double *__restrict
     s.cm[e] = (double)sam / dn / dV;
     s.vb[e] = u128_to_double((unsigned long long)(v >> 64), (unsigned long long)v) / dn / dV / dV;
     s.q2[e] = (double)sm2 / dV / dV;
-    const unsigned __int128 q4 = ((unsigned __int128)b.sm4hi[e] << b.shift) + b.sm4lo[e];
-    s.q4[e] = u128_to_double((unsigned long long)(q4 >> 64), (unsigned long long)q4) / dV / dV /
-              dV / dV;
+    s.q4[e] = u128_to_double(b.sm4hi[e], b.sm4lo[e]) / dV / dV / dV / dV;
 }
 
 __global__ void stats_kernel_f32(Bins b, int nE, int V, const float *__restrict__ lw_hi,
@@ -322,9 +310,7 @@ __global__ void stats_kernel_f32(Bins b, int nE, int V, const float *__restrict_
     s.cm[e] = (float)sam / fn / fV;
     s.vb[e] = u128_to_float((unsigned long long)(v >> 64), (unsigned long long)v) / fn / fV / fV;
     s.q2[e] = (float)sm2 / fV / fV;
-    const unsigned __int128 q4 = ((unsigned __int128)b.sm4hi[e] << b.shift) + b.sm4lo[e];
-    s.q4[e] = u128_to_float((unsigned long long)(q4 >> 64), (unsigned long long)q4) / fV / fV /
-              fV / fV;
+    s.q4[e] = u128_to_float(b.sm4hi[e], b.sm4lo[e]) / fV / fV / fV / fV;
 }
 
 // ---------------------------------------------------------------- reductions
@@ -677,9 +663,6 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
     b.sm2 = b.sam + n_e;
     b.sm4lo = b.sm2 + n_e;
     b.sm4hi = b.sm4lo + n_e;
-    b.shift = ((unsigned __int128)n_rows * (uint64_t)std::max(row_len, 0) < ((unsigned __int128)1 << 28))
-                  ? 36
-                  : 64;
     char *ps = p + L.bins;
     char *pg = ps + L.stats;
     double *d_out = (double *)(pg + L.grid);
@@ -701,7 +684,6 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
         // stage A through buckets, a pass of at most rec_cap samples at a time
         unsigned *d_cnt = (unsigned *)records, *d_cur = d_cnt + nbk;
         uint2 *d_rec = (uint2 *)(records + bucket_counter_bytes(n_e));
-        b.shift = 64;
         int dev = 0, nsm = 152;
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -730,12 +712,8 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
     } else if (n_rows > 0 && row_len > 0) {
         dim3 grid((unsigned)std::min<int64_t>((row_len + 255) / 256, 1024),
                   (unsigned)std::min<int64_t>(n_rows, 4096));
-        if (b.shift == 36)
-            bin_kernel<true><<<grid, 256, 0, st>>>(e_j, e_d, m, n_rows, row_len, row_stride,
-                                                   e_min, n_e, b, d_err);
-        else
-            bin_kernel<false><<<grid, 256, 0, st>>>(e_j, e_d, m, n_rows, row_len, row_stride,
-                                                    e_min, n_e, b, d_err);
+        bin_kernel<<<grid, 256, 0, st>>>(e_j, e_d, m, n_rows, row_len, row_stride, e_min, n_e, b,
+                                         d_err);
         RCK(cudaGetLastError());
     }
     const int sb = (n_e + 255) / 256;

@@ -145,3 +145,32 @@ def test_full_size_reweight_sampled_grid_points():
         err = np.abs(got[ks] - ref) / sc
         assert (err <= TOL[p]).all(), (p, dict(zip(NAMES, err.max(axis=0))))
     assert np.isfinite(got64).all() and np.isfinite(got32).all()
+
+
+def test_bucketed_sums_equal_direct_sums():
+    """``muca_reweight`` forms the per-bin integer sums through buckets of bins
+    (records summed in shared memory); ``muca_reweight_noalloc`` adds every
+    sample to the global sums.  Both sums are exact, so the results must be
+    bit-identical: here with samples whose E_J or |M| are too large for a
+    record, and with more samples (2^26 + 65536) than one bucketed pass takes."""
+    V, n_e = 4999, 5000
+    n_rows, row_len = 16400, 4096
+    n = n_rows * row_len
+    g = torch.Generator(device="cuda").manual_seed(11)
+    e_d = torch.randint(0, n_e, (n,), device="cuda", dtype=torch.int32, generator=g)
+    e_j = torch.randint(-3 * V, 3 * V + 1, (n,), device="cuda", dtype=torch.int32, generator=g)
+    m = torch.randint(-V, V + 1, (n,), device="cuda", dtype=torch.int32, generator=g)
+    big = torch.randint(0, n, (4096,), device="cuda", generator=g)
+    e_j[big[:2048]] = torch.randint(1 << 20, 1 << 26, (2048,), device="cuda", dtype=torch.int32,
+                                    generator=g)
+    m[big[2048:]] = -torch.randint((1 << 18) + 1, 1 << 22, (2048,), device="cuda",
+                                   dtype=torch.int32, generator=g)
+    lnW = wl.random_lnW(n_e, seed=4, scale=3.0, slope=-0.4)
+    grid = np.linspace(0.2, 0.6, 13)
+    for p in (64, 32):
+        a = muca().reweight(e_j, e_d, m, lnW, 0, 0.7, V, grid, p, n_rows=n_rows,
+                            row_len=row_len, row_stride=row_len)
+        b = muca().reweight(e_j, e_d, m, lnW, 0, 0.7, V, grid, p, n_rows=n_rows,
+                            row_len=row_len, row_stride=row_len, no_alloc=True)
+        assert np.isfinite(a).all()
+        assert np.array_equal(a, b), p
