@@ -296,9 +296,10 @@ def run_ours(args, rank, world, local_rank):
     d2h = nE * 8 + meas * 3 * W * 4 + nE * 8 + grid.size * 5 * 8  # hist, series, lnW, results
 
     # reweighting sub-benchmark (FP32 vs FP64), rank 0 only
-    rw = None
+    rw = mixed = None
     if rank == 0:
         rw = reweight_bench(torch, muca)
+        mixed = mixed_bench(torch, muca, stream)
 
     if rank == 0:
         pk, pk_kind = peaks()
@@ -339,6 +340,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": args.steps * (launches_per_sweep_call * 2 + 3),
             "clocks": clk,
             "reweight": rw,
+            "batched_mixed": mixed,
         }
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline_sample()
@@ -353,6 +355,55 @@ def run_ours(args, rank, world, local_rank):
 # the six-neighbour sum (5), proposal and energy change (6), table index and
 # compare (4), conditional update of the spin and the three tallies (5).
 ALGO_INT_OPS = 40
+
+
+def mixed_bench(torch, muca, stream, n_it=2):
+    """The batching workload: 24 (L, T) groups of 512 walkers, L = 8..32.  Batched:
+    one context, one sweep launch per iteration over all groups, the iteration
+    loop captured as a CUDA graph.  Plain: one context per (L, T) group, run one
+    after the other, one sweep launch per iteration plus a host-driven merge.
+    Attempts/s over the same number of 300-sweep iterations; contexts (and their
+    autotuning) are set up outside the timed regions."""
+    mx = wl.MIXED
+    groups = wl.mixed_groups()
+    sweeps = mx["sweeps"]
+    attempts = sum(g["n_walkers"] * g["L"] ** 3 for g in groups) * sweeps * n_it
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    ctx = muca.Context(groups, seed=mx["seed"])
+    ctx.run_graph(1, sweeps)  # warm-up (graph capture)
+    ms_b = timed(lambda: ctx.run_graph(n_it, sweeps))
+    cfgs = sorted({ctx.get_config(i) for i in range(len(groups))})
+    ctx.close()
+    ms_p = 0.0
+    for i, g in enumerate(groups):
+        c = muca.Context([g], seed=mx["seed"] + 1 + i)
+        c.sweep_iter(sweeps)
+        c.merge_update()
+
+        def run():
+            for _ in range(n_it):
+                c.sweep_iter(sweeps)
+                c.merge_update()
+
+        ms_p += timed(run)
+        c.close()
+    vb, vp = attempts / (ms_b / 1e3), attempts / (ms_p / 1e3)
+    return {"workload": "24 groups: L in {8,12,16,20,24,32} x T in {2.0,1.4182,1.0,0.9}, "
+                        f"512 walkers each, {n_it} iterations x {sweeps} sweeps",
+            "unit": UNIT, "batched": vb, "plain_per_config": vp, "batched_over_plain": vb / vp,
+            "batched_ms": ms_b, "plain_ms": ms_p,
+            "batched_configs": [{"residency": {1: "global", 2: "smem", 3: "split"}.get(c[0], str(c[0])),
+                                 "walkers_per_block": c[1], "lanes_per_walker": c[2]}
+                                for c in cfgs]}
 
 
 def reweight_bench(torch, muca):

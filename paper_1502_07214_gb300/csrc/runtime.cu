@@ -246,6 +246,13 @@ int build_blocks(muca_ctx *ctx)
         for (int w0 = 0; w0 < g.W; w0 += g.wpb)
             b[k].push_back(BlockDesc{(int)gi, w0, std::min(g.wpb, g.W - w0), g.wpb, g.P});
     }
+    // Longest blocks first: when a launch needs more than one wave of blocks,
+    // the blocks of the largest lattices (work per sweep: walkers x sites)
+    // start first instead of forming the tail.
+    for (int k = 0; k < 3; ++k)
+        std::stable_sort(b[k].begin(), b[k].end(), [&](const BlockDesc &x, const BlockDesc &y) {
+            return (int64_t)x.nw * ctx->g[x.group].V > (int64_t)y.nw * ctx->g[y.group].V;
+        });
     for (int k = 0; k < 3; ++k) {
         if (sm[k] > 0 && (int64_t)sm[k] + 1024 > (int64_t)max_smem_per_block())
             return fail(ctx, MUCA_ERR_INVALID_ARG, "%zu bytes of shared memory per block do not fit",
@@ -492,6 +499,94 @@ static int tune_group(muca_ctx *ctx, size_t gi, int residency, int wpb, int P)
     return MUCA_OK;
 }
 
+// Joint choice for a context of several groups.  All groups' blocks of one
+// kernel kind share a launch, and a launch gives every block the largest
+// shared-memory size among them, so choices made one group at a time can
+// leave an SM holding one block where it could hold two.  Times the whole
+// batch with the per-group choices and with one common walkers-per-block for
+// the split-kernel groups, on a relaxed copy of the state, and keeps the
+// fastest.  The state is restored afterwards.
+static int tune_batch(muca_ctx *ctx)
+{
+    const size_t n = ctx->g.size();
+    std::vector<size_t> split;
+    for (size_t i = 0; i < n; ++i)
+        if (ctx->g[i].residency == MUCA_RES_SPLIT) split.push_back(i);
+    if (split.size() < 2) return MUCA_OK;
+    struct Backup {
+        uint32_t *s = nullptr;
+        int32_t *t = nullptr;
+        unsigned long long *h = nullptr;
+        size_t sb = 0, tb = 0, hb = 0;
+    };
+    std::vector<Backup> bk(n);
+    int rc = MUCA_OK;
+    for (size_t i = 0; i < n && rc == MUCA_OK; ++i) {
+        const Group &g = ctx->g[i];
+        Backup &b = bk[i];
+        b.sb = (size_t)g.L * g.L * g.Lw * g.Wpad * sizeof(uint32_t);
+        b.tb = (size_t)3 * g.Wpad * sizeof(int32_t);
+        b.hb = (size_t)g.nE * sizeof(unsigned long long);
+        if (cudaMalloc(&b.s, b.sb) != cudaSuccess || cudaMalloc(&b.t, b.tb) != cudaSuccess ||
+            cudaMalloc(&b.h, b.hb) != cudaSuccess ||
+            cudaMemcpyAsync(b.s, g.spins, b.sb, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(b.t, g.tal, b.tb, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(b.h, g.hist, b.hb, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+            rc = fail(ctx, MUCA_ERR_CUDA, "batch tuning: backup of the state failed");
+    }
+    std::vector<int> tuned(n);
+    for (size_t i = 0; i < n; ++i) tuned[i] = ctx->g[i].wpb;
+    const int smem_max = max_smem_per_block();
+    auto apply = [&](int G) {
+        for (size_t i : split) ctx->g[i].wpb = G ? G : tuned[i];
+    };
+    int best_G = 0;
+    if (rc == MUCA_OK) {
+        apply(0);
+        rc = build_blocks(ctx);
+        if (rc == MUCA_OK) rc = launch_all(ctx, 32, false, ctx->stream);  // relax the copy
+    }
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int G : {0, 32, 16, 8}) {
+        if (rc != MUCA_OK) break;
+        if (G && (int64_t)ws_bytes_for(G) + 1024 > (int64_t)smem_max) continue;
+        apply(G);
+        rc = build_blocks(ctx);
+        if (rc == MUCA_OK) rc = launch_all(ctx, 1, false, ctx->stream);
+        cudaEventRecord(a, ctx->stream);
+        if (rc == MUCA_OK) rc = launch_all(ctx, 4, false, ctx->stream);
+        cudaEventRecord(b, ctx->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) rc = MUCA_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rc == MUCA_OK && ms < best) {
+            best = ms;
+            best_G = G;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    apply(best_G);
+    for (size_t i = 0; i < n; ++i) {
+        const Group &g = ctx->g[i];
+        const Backup &k = bk[i];
+        if (k.s) cudaMemcpyAsync(g.spins, k.s, k.sb, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (k.t) cudaMemcpyAsync(g.tal, k.t, k.tb, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (k.h) cudaMemcpyAsync(g.hist, k.h, k.hb, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && rc == MUCA_OK)
+        rc = fail(ctx, MUCA_ERR_CUDA, "batch tuning: restoring the state failed");
+    for (Backup &k : bk) {
+        cudaFree(k.s);
+        cudaFree(k.t);
+        cudaFree(k.h);
+    }
+    return rc;
+}
+
 static void free_group(Group &g)
 {
     cudaFree(g.spins);
@@ -648,6 +743,11 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
             if ((rc = tune_group(ctx, i, opt->residency, opt->walkers_per_block,
                                  opt->lanes_per_walker)) != MUCA_OK)
                 goto bad;
+        if (n_groups > 1 && opt->residency == MUCA_RES_AUTO && opt->walkers_per_block == 0) {
+            bool all_in = true;
+            for (int i = 0; i < n_groups; ++i) all_in = all_in && ctx->g[i].in_window;
+            if (all_in && (rc = tune_batch(ctx)) != MUCA_OK) goto bad;
+        }
         if ((rc = build_blocks(ctx)) != MUCA_OK) goto bad;
         CKI(cudaStreamSynchronize(ctx->stream));
     }
