@@ -133,6 +133,8 @@ __global__ void bucket_count_kernel(const int32_t *__restrict__ ed, int64_t n_ro
         if (sc[i]) atomicAdd(cnt + i, sc[i]);
 }
 
+constexpr int kScatterPer = 4;
+
 // Records into bucket order: bucket k occupies [start_k, start_k + cnt_k),
 // start the prefix sums of cnt; cur[k] hands out the blocks' places in it.
 __global__ void __launch_bounds__(1024)
@@ -150,41 +152,49 @@ bucket_scatter_kernel(const int32_t *__restrict__ ej, const int32_t *__restrict_
             acc += cnt[i];
         }
     }
+    // a tile is kScatterPer samples per thread of one row
+    const int tile = kScatterPer * blockDim.x;
     for (int64_t r = blockIdx.y; r < n_rows; r += gridDim.y)
-        for (int c0 = blockIdx.x * blockDim.x; c0 < row_len; c0 += gridDim.x * blockDim.x) {
+        for (int c0 = blockIdx.x * tile; c0 < row_len; c0 += gridDim.x * tile) {
             for (int i = threadIdx.x; i < nbk; i += blockDim.x) lc[i] = 0u;
             __syncthreads();
-            const int c = c0 + threadIdx.x;
-            int e = -1, bk = 0;
-            unsigned rank = 0u;
-            if (c < row_len) {
-                const int64_t o = r * row_stride + c;
-                e = __ldg(ed + o) - e_min;
-                if (e >= 0 && e < nE) {
-                    bk = e >> kBktBits;
-                    rank = atomicAdd(&lc[bk], 1u);
-                } else {
-                    e = -1;
+            int e[kScatterPer], bk[kScatterPer];
+            unsigned rank[kScatterPer];
+#pragma unroll
+            for (int q = 0; q < kScatterPer; ++q) {
+                const int c = c0 + q * blockDim.x + threadIdx.x;
+                e[q] = -1;
+                bk[q] = 0;
+                rank[q] = 0u;
+                if (c < row_len) {
+                    const int ee = __ldg(ed + r * row_stride + c) - e_min;
+                    if (ee >= 0 && ee < nE) {
+                        e[q] = ee;
+                        bk[q] = ee >> kBktBits;
+                        rank[q] = atomicAdd(&lc[bk[q]], 1u);
+                    }
                 }
             }
             __syncthreads();
             for (int i = threadIdx.x; i < nbk; i += blockDim.x)
                 if (lc[i]) base[i] = atomicAdd(cur + i, lc[i]);
             __syncthreads();
-            if (e >= 0) {
-                const int64_t o = r * row_stride + c;
+#pragma unroll
+            for (int q = 0; q < kScatterPer; ++q) {
+                if (e[q] < 0) continue;
+                const int64_t o = r * row_stride + c0 + q * blockDim.x + threadIdx.x;
                 const int j = __ldg(ej + o), mm = __ldg(m + o);
                 const unsigned am = mm < 0 ? 0u - (unsigned)mm : (unsigned)mm;
                 uint2 rr;
                 if (j > -(1 << 20) && j < (1 << 20) && am <= (1u << 18)) {
-                    rr.x = (unsigned)(e & (kBkt - 1)) | ((unsigned)(j + (1 << 20)) << kBktBits);
+                    rr.x = (unsigned)(e[q] & (kBkt - 1)) | ((unsigned)(j + (1 << 20)) << kBktBits);
                     rr.y = am;
                 } else {
-                    direct_add(b, e, j, am);
+                    direct_add(b, e[q], j, am);
                     rr.x = 0u;
                     rr.y = kNullRec;
                 }
-                rec[start[bk] + base[bk] + rank] = rr;
+                rec[start[bk[q]] + base[bk[q]] + rank[q]] = rr;
             }
             __syncthreads();
         }
@@ -699,7 +709,8 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
             bucket_count_kernel<<<g1, 256, nbk * sizeof(unsigned), st>>>(
                 e_d + off, nr, row_len, row_stride, e_min, n_e, nbk, d_cnt, d_err);
             RCK(cudaGetLastError());
-            dim3 g2((unsigned)std::min<int64_t>((row_len + 1023) / 1024, 1024),
+            dim3 g2((unsigned)std::min<int64_t>((row_len + 1024 * kScatterPer - 1) /
+                                                    (1024 * kScatterPer), 1024),
                     (unsigned)std::min<int64_t>(nr, 4096));
             bucket_scatter_kernel<<<g2, 1024, 3 * nbk * sizeof(unsigned), st>>>(
                 e_j + off, e_d + off, m + off, nr, row_len, row_stride, e_min, n_e, nbk, d_cnt,
