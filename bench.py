@@ -140,11 +140,12 @@ def run_reference(args, rank, world):
     L, T = s["L"], s["T"]
     V = L ** 3
     cores = os.cpu_count() or 1
-    # calibrate: one sweep of one walker per core
-    t0 = time.perf_counter()
+    # calibrate on 60 sweeps of one walker per core, after 20 warm-up sweeps
     oracle.muca_run(L, T, cores, s["seed"], 1, 20, n_threads=cores, want_spins=False)
-    rate = 20 / max(time.perf_counter() - t0, 1e-3)
-    sweeps = max(20, min(5000, int(8.0 * rate)))  # about 8 s per step
+    t0 = time.perf_counter()
+    oracle.muca_run(L, T, cores, s["seed"], 1, 60, n_threads=cores, want_spins=False)
+    rate = 60 / max(time.perf_counter() - t0, 1e-3)
+    sweeps = max(20, min(20000, int(8.0 * rate)))  # about 8 s per step
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -177,11 +178,13 @@ def cpu_baseline_sample():
     L, T = s["L"], s["T"]
     V = L ** 3
     cores = os.cpu_count() or 1
-    # calibrate on 20 sweeps, then time a sample of about 15 s
-    t0 = time.perf_counter()
+    # calibrate on 60 sweeps after 20 (the first sweeps run slower), then time a
+    # sample of about 15 s
     oracle.muca_run(L, T, cores, s["seed"], 1, 20, n_threads=cores, want_spins=False)
-    rate = 20 / max(time.perf_counter() - t0, 1e-3)
-    sweeps = max(20, min(5000, int(15.0 * rate)))
+    t0 = time.perf_counter()
+    oracle.muca_run(L, T, cores, s["seed"], 1, 60, n_threads=cores, want_spins=False)
+    rate = 60 / max(time.perf_counter() - t0, 1e-3)
+    sweeps = max(20, min(20000, int(15.0 * rate)))
     t0 = time.perf_counter()
     oracle.muca_run(L, T, cores, s["seed"], 1, sweeps, n_threads=cores, want_spins=False)
     dt = time.perf_counter() - t0
