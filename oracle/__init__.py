@@ -36,8 +36,10 @@ def lib():
                                   P, P, P, P, P, i32, i32]
         L.or_reweight.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
         L.or_reweight_q.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
+        L.or_find_peak.argtypes = [P, P, i64, i32, P, i32, i32, dbl, dbl, dbl, i32, i32, i32, P]
         for f in ("or_init_spins", "or_energies", "or_build_table", "or_sweeps",
-                  "or_update_lnW", "or_muca_run", "or_reweight", "or_reweight_q"):
+                  "or_update_lnW", "or_muca_run", "or_reweight", "or_reweight_q",
+                  "or_find_peak"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -148,3 +150,19 @@ def reweight(e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads=None):
 def reweight_q(e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads=None):
     """binary128 reweighting (rounded to FP64 on output)."""
     return _rw(lib().or_reweight_q, e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads)
+
+
+def find_peak(e_j, e_d, lnW, e_min, beta, lo, hi, n_iter=60, n_jack=0, n_threads=None):
+    """Delta*_L and C*_L by bisection on dC/dDelta (Sec. III) for the full series
+    and the n_jack leave-one-block-out subsets.  e_j, e_d are [n_rows][row_len]
+    (one row per sweep).  Returns an array [1 + n_jack][2] of (Delta*, C*)."""
+    ej = np.ascontiguousarray(e_j, dtype=np.int32)
+    ed = np.ascontiguousarray(e_d, dtype=np.int32)
+    if ed.ndim == 1:
+        ej, ed = ej[None, :], ed[None, :]
+    lw = np.ascontiguousarray(lnW, dtype=np.float64)
+    out = np.zeros((1 + n_jack, 2))
+    nt = n_threads or min(os.cpu_count() or 1, 1 + n_jack)
+    _ck(lib().or_find_peak(_p(ej), _p(ed), ed.shape[0], ed.shape[1], _p(lw), e_min, len(lw),
+                           beta, lo, hi, n_iter, n_jack, nt, _p(out)), "or_find_peak")
+    return out

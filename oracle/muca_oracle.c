@@ -631,3 +631,154 @@ int or_reweight_q(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int6
     free(tid);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Pseudo-transition point (Sec. III): Delta*_L is the field where C(Delta)   */
+/* of Eq. 6 is largest, found as the zero crossing of its derivative by       */
+/* bisection with time-series reweighting (Eq. 3), for the full series and    */
+/* for w subsets that each leave out 1/w of the measurements (jackknife);     */
+/* C*_L = C(Delta*_L).  Differentiating a reweighted mean,                    */
+/*   d<O>/dDelta = -beta (<O E_Delta> - <O><E_Delta>),                         */
+/* applied to Eq. 6 gives                                                      */
+/*   dC/dDelta = beta^2 <(E_J - <E_J>)(E_Delta - <E_Delta>)^2>.                */
+/* Readings: the series is n_rows rows of row_len samples (one row per sweep),*/
+/* subset b leaves out rows [b n_rows / w, (b+1) n_rows / w); the interval     */
+/* [lo, hi] must bracket the maximum (dC/dDelta > 0 at lo, < 0 at hi); each   */
+/* of n_iter steps keeps the half whose ends still bracket it                  */
+/* (mid = lo + (hi - lo) / 2; dC/dDelta(mid) > 0 moves lo, else hi), and the   */
+/* result is the midpoint of the last interval.                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const int32_t *e_j, *e_d;
+    int64_t n_rows;
+    int32_t row_len;
+    int64_t skip0, skip1; /* rows left out */
+    const double *lnW;
+    int e_min;
+    double beta;
+} pk_set;
+
+/* <E_J>, <E_Delta>, the covariance and the third mixed moment at Delta,
+ * centred exponents (reading R9) and centred sums (reading R10). */
+static void pk_moments(const pk_set *p, double delta, double *cov, double *third)
+{
+    const double c = p->beta * delta;
+    double amax = -INFINITY;
+    int32_t estar = 0;
+    for (int64_t r = 0; r < p->n_rows; ++r) {
+        if (r >= p->skip0 && r < p->skip1) continue;
+        for (int32_t k = 0; k < p->row_len; ++k) {
+            const int32_t e = p->e_d[r * p->row_len + k];
+            const double a = -(c * (double)e) - p->lnW[e - p->e_min];
+            if (a > amax) {
+                amax = a;
+                estar = e;
+            }
+        }
+    }
+    const double lstar = p->lnW[estar - p->e_min];
+    nsum z = {0, 0}, sj = {0, 0}, sd = {0, 0};
+    for (int64_t r = 0; r < p->n_rows; ++r) {
+        if (r >= p->skip0 && r < p->skip1) continue;
+        for (int32_t k = 0; k < p->row_len; ++k) {
+            const int64_t s = r * p->row_len + k;
+            const int32_t e = p->e_d[s];
+            const double w = exp(-(c * (double)(e - estar)) - (p->lnW[e - p->e_min] - lstar));
+            nsum_add(&z, w);
+            nsum_add(&sj, w * (double)p->e_j[s]);
+            nsum_add(&sd, w * (double)e);
+        }
+    }
+    const double Z = nsum_get(&z), mj = nsum_get(&sj) / Z, md = nsum_get(&sd) / Z;
+    nsum s2 = {0, 0}, s3 = {0, 0};
+    for (int64_t r = 0; r < p->n_rows; ++r) {
+        if (r >= p->skip0 && r < p->skip1) continue;
+        for (int32_t k = 0; k < p->row_len; ++k) {
+            const int64_t s = r * p->row_len + k;
+            const int32_t e = p->e_d[s];
+            const double w = exp(-(c * (double)(e - estar)) - (p->lnW[e - p->e_min] - lstar));
+            const double dj = (double)p->e_j[s] - mj, dd = (double)e - md;
+            nsum_add(&s2, w * (dj * dd));
+            nsum_add(&s3, w * (dj * dd * dd));
+        }
+    }
+    *cov = nsum_get(&s2) / Z;
+    *third = nsum_get(&s3) / Z;
+}
+
+typedef struct {
+    pk_set set;
+    double lo, hi;
+    int n_iter;
+    double *out; /* Delta*, C* */
+    int rc;
+} pk_job;
+
+static void *pk_job_run(void *arg)
+{
+    pk_job *j = (pk_job *)arg;
+    double cov, t_lo, t_hi;
+    pk_moments(&j->set, j->lo, &cov, &t_lo);
+    pk_moments(&j->set, j->hi, &cov, &t_hi);
+    if (!(t_lo > 0.0 && t_hi < 0.0)) {
+        j->rc = OR_ERR_ARG;
+        return NULL;
+    }
+    double lo = j->lo, hi = j->hi;
+    for (int i = 0; i < j->n_iter; ++i) {
+        const double mid = lo + 0.5 * (hi - lo);
+        double t;
+        pk_moments(&j->set, mid, &cov, &t);
+        if (t > 0.0) lo = mid;
+        else hi = mid;
+    }
+    const double ds = lo + 0.5 * (hi - lo);
+    double t;
+    pk_moments(&j->set, ds, &cov, &t);
+    j->out[0] = ds;
+    j->out[1] = -j->set.beta * cov;
+    j->rc = OR_OK;
+    return NULL;
+}
+
+int or_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_rows, int32_t row_len,
+                 const double *lnW, int e_min, int nE, double beta, double lo, double hi,
+                 int n_iter, int n_jack, int n_threads, double *out)
+{
+    if (!e_j || !e_d || !lnW || !out || n_rows < 1 || row_len < 1 || nE < 1 || !(beta > 0.0) ||
+        !(lo < hi) || n_iter < 0 || n_jack < 0 || n_jack == 1 || n_jack > n_rows)
+        return OR_ERR_ARG;
+    for (int64_t s = 0; s < n_rows * (int64_t)row_len; ++s)
+        if (e_d[s] < e_min || e_d[s] >= e_min + nE) return OR_ERR_WINDOW;
+    const int n_sets = 1 + n_jack;
+    pk_job *jobs = (pk_job *)calloc((size_t)n_sets, sizeof(pk_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)n_sets, sizeof(pthread_t));
+    if (!jobs || !tid) {
+        free(jobs);
+        free(tid);
+        return OR_ERR_NOMEM;
+    }
+    for (int b = 0; b < n_sets; ++b) {
+        pk_set st = {e_j, e_d, n_rows, row_len, 0, 0, lnW, e_min, beta};
+        if (b > 0) {
+            st.skip0 = (int64_t)(b - 1) * n_rows / n_jack;
+            st.skip1 = (int64_t)b * n_rows / n_jack;
+        }
+        pk_job j = {st, lo, hi, n_iter, out + 2 * b, OR_OK};
+        jobs[b] = j;
+    }
+    /* data sets in parallel, at most n_threads at a time */
+    if (n_threads < 1) n_threads = 1;
+    for (int b0 = 0; b0 < n_sets; b0 += n_threads) {
+        const int b1 = b0 + n_threads < n_sets ? b0 + n_threads : n_sets;
+        for (int b = b0 + 1; b < b1; ++b) pthread_create(&tid[b], NULL, pk_job_run, &jobs[b]);
+        pk_job_run(&jobs[b0]);
+        for (int b = b0 + 1; b < b1; ++b) pthread_join(tid[b], NULL);
+    }
+    int rc = OR_OK;
+    for (int b = 0; b < n_sets; ++b)
+        if (jobs[b].rc != OR_OK) rc = jobs[b].rc;
+    free(jobs);
+    free(tid);
+    return rc;
+}

@@ -90,6 +90,17 @@ int or_reweight_q(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int6
                   const double *lnW, int e_min, int nE, double beta, int V,
                   const double *grid, int n_grid, int n_threads, double *out);
 
+/* Pseudo-transition point (Sec. III): Delta*_L (the maximum of C, Eq. 6)
+ * by n_iter bisection steps on the zero of dC/dDelta inside [lo, hi], and
+ * C*_L, for the full series (n_rows x row_len samples, row-major) and for the
+ * n_jack subsets (0 or >= 2) that each leave out one block of n_rows / n_jack
+ * consecutive rows.  out[2 b], out[2 b + 1] = Delta*, C* of data set b
+ * (b = 0 full, b = 1 + i leaves out block i).  OR_ERR_ARG when [lo, hi] does
+ * not bracket the maximum for some data set. */
+int or_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_rows, int32_t row_len,
+                 const double *lnW, int e_min, int nE, double beta, double lo, double hi,
+                 int n_iter, int n_jack, int n_threads, double *out);
+
 #ifdef __cplusplus
 }
 #endif

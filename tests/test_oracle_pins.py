@@ -13,6 +13,7 @@ import pytest
 
 import exact
 import oracle
+from paper_1502_07214_gb300 import workloads as wl
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 P_MIN = 1e-4  # fixed in advance for every chi-square test below
@@ -336,3 +337,77 @@ def test_fp64_oracle_against_binary128_at_large_volume():
     err = np.abs(a - q) / scale
     assert err.max() < 1e-10
     assert np.median(err) < 1e-14
+
+
+# ---------------------------------------------------------------- Delta*_L
+def _two_state_rows(V, n_rows, per_row1, per_row0):
+    """Rows (sweeps) of the two T = 0 ground states: per_row1 samples of the
+    all-(+-1) state (E_J = -3V, E_Delta = V) and per_row0 of the all-0 state."""
+    ed = np.array([[V] * per_row1 + [0] * per_row0] * n_rows, dtype=np.int32)
+    ej = np.array([[-3 * V] * per_row1 + [0] * per_row0] * n_rows, dtype=np.int32)
+    return ej, ed
+
+
+def test_peak_two_ground_states_closed_form():
+    """Sec. III's Delta*_L on the two-state series: C = 3 beta V^2 q (1 - q) with
+    q the reweighted weight of the all-(+-1) state, largest at q = 1/2, i.e. at
+    Delta* = 3 + (ln(n1/n0) - lnW(V) + lnW(0)) / (beta V) - 3 = 3 + ln(n1/n0)/(beta V)
+    (lnW(V) = -3 beta V), with C* = 3 beta V^2 / 4.  Every jackknife subset holds
+    the same proportions, so all subsets agree and the jackknife spread is 0."""
+    V, T = 64, 0.25
+    beta = 1 / T
+    lnW = np.zeros(V + 1)
+    lnW[V] = -beta * 3 * V
+    ej, ed = _two_state_rows(V, n_rows=40, per_row1=3, per_row0=5)
+    out = oracle.find_peak(ej, ed, lnW, 0, beta, 2.9, 3.1, n_iter=60, n_jack=8)
+    want = 3 + np.log(3 / 5) / (beta * V)
+    np.testing.assert_allclose(out[:, 0], want, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(out[:, 1], 3 * beta * V * V / 4, rtol=1e-12)
+
+
+def test_peak_subsets_are_the_series_without_their_block():
+    """Subset i of the jackknife is the full-series search on the series with
+    rows [i n / w, (i + 1) n / w) removed: built here by slicing, the two agree
+    exactly."""
+    ej, ed, m, lnW, dt = wl.synthetic_series(L=6, T=1.4182, n_walkers=16, n_samples=60, seed=21)
+    beta = 1 / 1.4182
+    grid = np.linspace(dt - 0.3, dt + 0.3, 121)
+    c = oracle.reweight(ej, ed, m, lnW, 0, beta, 6 ** 3, grid)[:, 2]
+    k = int(np.argmax(c))
+    lo, hi = grid[max(k - 3, 0)], grid[min(k + 3, len(grid) - 1)]
+    w = 5
+    out = oracle.find_peak(ej, ed, lnW, 0, beta, lo, hi, n_iter=50, n_jack=w)
+    n = ed.shape[0]
+    for i in range(w):
+        keep = np.r_[0:i * n // w, (i + 1) * n // w:n]
+        sub = oracle.find_peak(ej[keep], ed[keep], lnW, 0, beta, lo, hi, n_iter=50)
+        assert np.array_equal(out[1 + i], sub[0])
+
+
+def test_peak_is_the_maximum_of_the_reweighted_c():
+    """Delta* from the bisection on dC/dDelta against a dense scan of C(Delta)
+    by the reweighting (Eq. 3, 6): the scan's largest value lies within one
+    grid step of Delta*, and no scanned C exceeds C*."""
+    ej, ed, m, lnW, dt = wl.synthetic_series(L=8, T=1.4182, n_walkers=32, n_samples=200, seed=5)
+    beta, V = 1 / 1.4182, 8 ** 3
+    coarse = np.linspace(dt - 0.3, dt + 0.3, 61)
+    c = oracle.reweight(ej, ed, m, lnW, 0, beta, V, coarse)[:, 2]
+    k = int(np.argmax(c))
+    lo, hi = coarse[k - 2], coarse[k + 2]
+    out = oracle.find_peak(ej, ed, lnW, 0, beta, lo, hi, n_iter=60)
+    ds, cs = out[0]
+    fine = np.linspace(lo, hi, 801)
+    cf = oracle.reweight(ej, ed, m, lnW, 0, beta, V, fine)[:, 2]
+    assert abs(fine[int(np.argmax(cf))] - ds) <= (fine[1] - fine[0])
+    assert cf.max() <= cs * (1 + 1e-12)
+    assert abs(oracle.reweight(ej, ed, m, lnW, 0, beta, V, [ds])[0, 2] - cs) <= 1e-12 * abs(cs)
+
+
+def test_peak_rejects_an_interval_without_the_maximum():
+    V, T = 64, 0.25
+    beta = 1 / T
+    lnW = np.zeros(V + 1)
+    lnW[V] = -beta * 3 * V
+    ej, ed = _two_state_rows(V, n_rows=10, per_row1=3, per_row0=5)
+    with pytest.raises(oracle.OracleError):
+        oracle.find_peak(ej, ed, lnW, 0, beta, 3.05, 3.2)
