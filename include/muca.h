@@ -190,6 +190,32 @@ int muca_reweight_noalloc(const int32_t *e_j, const int32_t *e_d, const int32_t 
                           const double *delta_grid, int32_t n_grid, int32_t precision,
                           double *out, void *stream);
 
+/* Pseudo-transition point (Sec. III): Delta*_L, the crystal field where C of
+ * Eq. 6 is largest, and C*_L = C(Delta*_L), with jackknife errors.  Delta*_L
+ * is the zero crossing of dC/dDelta = beta^2 <(E_J - <E_J>)(E_Delta - <E_Delta>)^2>,
+ * found by n_iter bisection steps in [delta_lo, delta_hi] with time-series
+ * reweighting (Eq. 3): each step keeps the half whose ends still bracket it
+ * (mid = lo + (hi - lo) / 2; dC/dDelta(mid) > 0 moves lo, else hi), and the
+ * result is the last interval's midpoint.  This is done for the full series
+ * and for n_jack subsets (0, or 2 .. 1024) that each leave out one block of
+ * rows [i n_rows / n_jack, (i + 1) n_rows / n_jack).
+ *   e_j, e_d      device int32, sample (r, c) at [r * row_stride + c]; a row
+ *                 is one sweep of all walkers (as muca_reweight)
+ *   lnW, e_min, n_e, beta   as muca_reweight
+ *   n_iter        bisection steps (0 .. 200; 60 reach FP64 resolution)
+ *   out           host FP64 [4 + 2 n_jack]: Delta*_L, its jackknife error,
+ *                 C*_L, its jackknife error (errors 0 when n_jack = 0), then
+ *                 (Delta*, C*) of each subset; the error of x is
+ *                 sqrt((w - 1) / w sum_i (x_i - mean x_i)^2), w = n_jack
+ * MUCA_ERR_INVALID_ARG when [delta_lo, delta_hi] does not bracket the maximum
+ * for the full series or a subset (dC/dDelta must be > 0 at delta_lo and < 0
+ * at delta_hi); MUCA_ERR_WINDOW for a sample outside the window.  Allocates
+ * its scratch with cudaMallocAsync on the stream; synchronises the stream. */
+int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_rows, int32_t row_len,
+                   int64_t row_stride, const double *lnW, int32_t e_min, int32_t n_e,
+                   double beta, double delta_lo, double delta_hi, int32_t n_iter, int32_t n_jack,
+                   double *out, void *stream);
+
 /* ------------------------------------------------------------ time series */
 
 /* Reserve room for n_samples recorded sweeps per walker (device memory,

@@ -1,0 +1,361 @@
+// peak.cu -- the pseudo-transition point Delta*_L of Sec. III: the crystal
+// field where C(Delta) of Eq. 6 is largest, found as the zero crossing of
+// dC/dDelta by bisection with time-series reweighting (Eq. 3), for the full
+// series and for w jackknife subsets that each leave out one block of
+// consecutive measurements; C*_L = C(Delta*_L).
+//
+// Differentiating a reweighted mean, d<O>/dDelta = -beta (<O E_Delta> - <O><E_Delta>);
+// applied to Eq. 6,
+//   dC/dDelta = beta^2 <(E_J - <E_J>)(E_Delta - <E_Delta>)^2>.
+// A sample enters C and dC/dDelta only through its E_Delta bin and its E_J,
+// and (E_Delta - <E_Delta>) is constant within a bin, so both need per bin
+// only the number of samples n and their mean E_J:
+//   C = -beta / Z sum_E w(E) n(E) (mj(E) - <E_J>)(E - <E_Delta>),
+//   dC/dDelta / beta^2 = 1 / Z sum_E w(E) n(E) (mj(E) - <E_J>)(E - <E_Delta>)^2,
+// with w(E) = exp(-beta Delta E - lnW(E)) taken relative to its largest value.
+//
+// GPU layout: one pass over the series forms exact integer sums (count, sum
+// E_J) per bin and per jackknife block; each data set's sums are all blocks'
+// sums minus the left-out block's (integers, exact); one thread block per data
+// set then runs the whole bisection, each step three FP64 passes over the
+// bins (largest weight, weighted means, centred moments).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/muca.h"
+#include "muca_internal.h"
+
+namespace {
+
+// Integer sums per jackknife block: cnt[b][E], sej[b][E].  bnd[i] is the first
+// row of block i (bnd[n_blocks] = n_rows).
+__global__ void jk_bin_kernel(const int32_t *__restrict__ ej, const int32_t *__restrict__ ed,
+                              int64_t n_rows, int row_len, int64_t row_stride, int e_min, int nE,
+                              const int64_t *__restrict__ bnd, int n_blocks,
+                              unsigned long long *cnt, unsigned long long *sej, int *err)
+{
+    for (int64_t r = blockIdx.y; r < n_rows; r += gridDim.y) {
+        int b = 0;
+        while (b + 1 < n_blocks && bnd[b + 1] <= r) ++b;
+        unsigned long long *cb = cnt + (size_t)b * nE, *sb = sej + (size_t)b * nE;
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < row_len;
+             c += gridDim.x * blockDim.x) {
+            const int64_t o = r * row_stride + c;
+            const int e = __ldg(ed + o) - e_min;
+            if (e < 0 || e >= nE) {
+                atomicOr(err, 1);
+                continue;
+            }
+            atomicAdd(cb + e, 1ull);
+            atomicAdd(sb + e, (unsigned long long)(long long)__ldg(ej + o));
+        }
+    }
+}
+
+// Per data set d (0: every block; 1 + i: every block but i) and bin: the
+// sample count and the mean E_J.
+__global__ void jk_stats_kernel(const unsigned long long *__restrict__ cnt,
+                                const unsigned long long *__restrict__ sej, int n_blocks, int nE,
+                                double *n_out, double *mj_out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.y;
+    if (e >= nE) return;
+    unsigned long long n = 0, s = 0;
+    for (int b = 0; b < n_blocks; ++b) {
+        n += cnt[(size_t)b * nE + e];
+        s += sej[(size_t)b * nE + e];
+    }
+    if (d > 0) {
+        n -= cnt[(size_t)(d - 1) * nE + e];
+        s -= sej[(size_t)(d - 1) * nE + e];
+    }
+    n_out[(size_t)d * nE + e] = (double)n;
+    mj_out[(size_t)d * nE + e] = n ? (double)(long long)s / (double)n : 0.0;
+}
+
+struct KS {  // Kahan-compensated FP64 sum
+    double s = 0.0, c = 0.0;
+    __device__ void add(double x)
+    {
+        const double y = x - c;
+        const double t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+constexpr int kPkThreads = 256;
+
+// Sum over the block of K compensated sums (every thread gets the results).
+template <int K>
+__device__ void pk_block_sum(KS (&a)[K], double (&out)[K], double *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = a[k].s, c = -a[k].c;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double s2 = __shfl_xor_sync(0xFFFFFFFFu, s, o);
+            const double c2 = __shfl_xor_sync(0xFFFFFFFFu, c, o);
+            const double t = s + s2;
+            const double bp = t - s;
+            const double err = (s - (t - bp)) + (s2 - bp);
+            s = t;
+            c = c + c2 + err;
+        }
+        __syncthreads();
+        if (lane == 0) {
+            sh[2 * wid] = s;
+            sh[2 * wid + 1] = c;
+        }
+        __syncthreads();
+        double tot = 0.0, cc = 0.0;
+        for (int i = 0; i < nw; ++i) {
+            const double y = sh[2 * i] - cc;
+            const double t = tot + y;
+            cc = (t - tot) - y;
+            tot = t;
+            cc -= sh[2 * i + 1];
+        }
+        out[k] = tot - cc;
+    }
+}
+
+// The bin E* of the largest weight exp(-c E - lnW(E)) among occupied bins
+// (ties to the smaller bin).
+__device__ int pk_argmax(const double *n, const double *lnW, int nE, int e_min, double c, double *sh,
+                         int *shi)
+{
+    double v = -INFINITY;
+    int arg = 0x7FFFFFFF;
+    for (int e = threadIdx.x; e < nE; e += blockDim.x)
+        if (n[e] > 0.0) {
+            const double a = __dsub_rn(-__dmul_rn(c, (double)(e_min + e)), lnW[e]);
+            if (a > v) {
+                v = a;
+                arg = e;
+            }
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        const int a2 = __shfl_xor_sync(0xFFFFFFFFu, arg, o);
+        if (v2 > v || (v2 == v && a2 < arg)) {
+            v = v2;
+            arg = a2;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh[wid] = v;
+        shi[wid] = arg;
+    }
+    __syncthreads();
+    v = sh[0];
+    arg = shi[0];
+    for (int i = 1; i < nw; ++i)
+        if (sh[i] > v || (sh[i] == v && shi[i] < arg)) {
+            v = sh[i];
+            arg = shi[i];
+        }
+    return arg;
+}
+
+// Covariance <(E_J - <E_J>)(E_Delta - <E_Delta>)> and third moment
+// <(E_J - <E_J>)(E_Delta - <E_Delta>)^2> of the data set at field Delta.
+__device__ void pk_moments(const double *n, const double *mj, const double *lnW, int nE, int e_min,
+                           double beta, double delta, double *sh, int *shi, double &cov,
+                           double &third)
+{
+    const double c = beta * delta;
+    int es = pk_argmax(n, lnW, nE, e_min, c, sh, shi);
+    if (es >= nE) es = 0;  // no occupied bin: nothing to weigh
+    const double lstar = lnW[es];
+    KS a[3];
+    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+        const double ne = n[e];
+        if (ne <= 0.0) continue;
+        const double w =
+            exp(__dsub_rn(-__dmul_rn(c, (double)(e - es)), __dsub_rn(lnW[e], lstar))) * ne;
+        a[0].add(w);
+        a[1].add(w * mj[e]);
+        a[2].add(w * (double)(e_min + e));
+    }
+    double S[3];
+    pk_block_sum<3>(a, S, sh);
+    const double jbar = S[1] / S[0], dbar = S[2] / S[0];
+    KS b[2];
+    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+        const double ne = n[e];
+        if (ne <= 0.0) continue;
+        const double w =
+            exp(__dsub_rn(-__dmul_rn(c, (double)(e - es)), __dsub_rn(lnW[e], lstar))) * ne;
+        const double dj = mj[e] - jbar, dd = (double)(e_min + e) - dbar;
+        b[0].add(w * (dj * dd));
+        b[1].add(w * (dj * dd * dd));
+    }
+    double T[2];
+    pk_block_sum<2>(b, T, sh);
+    cov = T[0] / S[0];
+    third = T[1] / S[0];
+}
+
+// One block per data set: bisection on the sign of dC/dDelta in [lo, hi].
+__global__ void __launch_bounds__(kPkThreads)
+peak_kernel(const double *__restrict__ n_all, const double *__restrict__ mj_all,
+            const double *__restrict__ lnW, int nE, int e_min, double beta, double lo, double hi,
+            int n_iter, double *res, int *bad)
+{
+    __shared__ double sh[64];
+    __shared__ int shi[32];
+    const int d = blockIdx.x;
+    const double *n = n_all + (size_t)d * nE, *mj = mj_all + (size_t)d * nE;
+    double cov, t_lo, t_hi;
+    pk_moments(n, mj, lnW, nE, e_min, beta, lo, sh, shi, cov, t_lo);
+    pk_moments(n, mj, lnW, nE, e_min, beta, hi, sh, shi, cov, t_hi);
+    if (!(t_lo > 0.0 && t_hi < 0.0)) {
+        if (threadIdx.x == 0) bad[d] = 1;
+        return;
+    }
+    for (int i = 0; i < n_iter; ++i) {
+        const double mid = lo + 0.5 * (hi - lo);
+        double t;
+        pk_moments(n, mj, lnW, nE, e_min, beta, mid, sh, shi, cov, t);
+        if (t > 0.0) lo = mid;
+        else hi = mid;
+    }
+    const double ds = lo + 0.5 * (hi - lo);
+    double t;
+    pk_moments(n, mj, lnW, nE, e_min, beta, ds, sh, shi, cov, t);
+    if (threadIdx.x == 0) {
+        res[2 * d] = ds;
+        res[2 * d + 1] = -beta * cov;
+    }
+}
+
+int pk_fail(int code, const std::string &msg)
+{
+    muca::set_last_error(msg.c_str());
+    return code;
+}
+
+}  // namespace
+
+extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_rows,
+                              int32_t row_len, int64_t row_stride, const double *lnW,
+                              int32_t e_min, int32_t n_e, double beta, double delta_lo,
+                              double delta_hi, int32_t n_iter, int32_t n_jack, double *out,
+                              void *stream)
+{
+    if (!e_j || !e_d || !lnW || !out)
+        return pk_fail(MUCA_ERR_INVALID_ARG, "muca_find_peak: null pointer");
+    if (n_rows < 1 || row_len < 1 || (n_rows > 1 && row_stride < row_len) || n_e < 1 ||
+        n_iter < 0 || n_iter > 200 || n_jack < 0 || n_jack == 1 || n_jack > n_rows ||
+        n_jack > 1024)
+        return pk_fail(MUCA_ERR_INVALID_ARG, "muca_find_peak: bad sizes");
+    if (!(beta > 0.0) || !std::isfinite(beta) || !std::isfinite(delta_lo) ||
+        !std::isfinite(delta_hi) || !(delta_lo < delta_hi))
+        return pk_fail(MUCA_ERR_INVALID_ARG, "muca_find_peak: need beta > 0 and delta_lo < delta_hi");
+    for (int e = 0; e < n_e; ++e)
+        if (!std::isfinite(lnW[e])) return pk_fail(MUCA_ERR_INVALID_ARG, "muca_find_peak: lnW not finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_blocks = n_jack > 0 ? n_jack : 1, n_sets = 1 + n_jack;
+    std::vector<int64_t> bnd(n_blocks + 1);
+    for (int i = 0; i <= n_blocks; ++i) bnd[i] = (int64_t)i * n_rows / n_blocks;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b_sums = al((size_t)2 * n_blocks * n_e * sizeof(unsigned long long));
+    const size_t b_sets = al((size_t)2 * n_sets * n_e * sizeof(double));
+    const size_t b_lnw = al((size_t)n_e * sizeof(double));
+    const size_t b_bnd = al(bnd.size() * sizeof(int64_t));
+    const size_t b_res = al((size_t)2 * n_sets * sizeof(double));
+    const size_t b_bad = al((size_t)(n_sets + 1) * sizeof(int));
+    char *p = nullptr;
+    cudaError_t ce = cudaMallocAsync((void **)&p, b_sums + b_sets + b_lnw + b_bnd + b_res + b_bad, st);
+    if (ce != cudaSuccess)
+        return pk_fail(ce == cudaErrorMemoryAllocation ? MUCA_ERR_OOM : MUCA_ERR_CUDA,
+                       std::string("cudaMallocAsync: ") + cudaGetErrorString(ce));
+    unsigned long long *cnt = (unsigned long long *)p, *sej = cnt + (size_t)n_blocks * n_e;
+    double *n_all = (double *)(p + b_sums), *mj_all = n_all + (size_t)n_sets * n_e;
+    double *d_lnW = (double *)(p + b_sums + b_sets);
+    int64_t *d_bnd = (int64_t *)(p + b_sums + b_sets + b_lnw);
+    double *d_res = (double *)(p + b_sums + b_sets + b_lnw + b_bnd);
+    int *d_bad = (int *)(p + b_sums + b_sets + b_lnw + b_bnd + b_res);  // [0]: window, [1 + d]
+    std::vector<double> res(2 * (size_t)n_sets, 0.0);
+    std::vector<int> bad(n_sets + 1, 0);
+    int rc = MUCA_OK;
+#define PCK(call)                                                                         \
+    do {                                                                                  \
+        ce = (call);                                                                      \
+        if (ce != cudaSuccess) {                                                          \
+            rc = pk_fail(MUCA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(ce)); \
+            goto done;                                                                    \
+        }                                                                                 \
+    } while (0)
+    PCK(cudaMemsetAsync(p, 0, b_sums, st));
+    PCK(cudaMemsetAsync(d_bad, 0, b_bad, st));
+    PCK(cudaMemcpyAsync(d_lnW, lnW, (size_t)n_e * sizeof(double), cudaMemcpyHostToDevice, st));
+    PCK(cudaMemcpyAsync(d_bnd, bnd.data(), bnd.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    {
+        dim3 g((unsigned)std::min<int64_t>((row_len + 255) / 256, 1024),
+               (unsigned)std::min<int64_t>(n_rows, 4096));
+        jk_bin_kernel<<<g, 256, 0, st>>>(e_j, e_d, n_rows, row_len, row_stride, e_min, n_e, d_bnd,
+                                         n_blocks, cnt, sej, d_bad);
+        PCK(cudaGetLastError());
+        dim3 g2((unsigned)((n_e + 255) / 256), (unsigned)n_sets);
+        jk_stats_kernel<<<g2, 256, 0, st>>>(cnt, sej, n_blocks, n_e, n_all, mj_all);
+        PCK(cudaGetLastError());
+        peak_kernel<<<n_sets, kPkThreads, 0, st>>>(n_all, mj_all, d_lnW, n_e, e_min, beta,
+                                                   delta_lo, delta_hi, n_iter, d_res, d_bad + 1);
+        PCK(cudaGetLastError());
+    }
+    PCK(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PCK(cudaMemcpyAsync(bad.data(), d_bad, bad.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+#undef PCK
+    if (bad[0]) {
+        rc = pk_fail(MUCA_ERR_WINDOW, "a sample's E_Delta lies outside [e_min, e_min + n_e)");
+        goto done;
+    }
+    for (int d = 0; d < n_sets; ++d)
+        if (bad[1 + d]) {
+            rc = pk_fail(MUCA_ERR_INVALID_ARG,
+                         "muca_find_peak: [delta_lo, delta_hi] does not bracket the maximum of C "
+                         "for data set " + std::to_string(d) +
+                         " (dC/dDelta must be > 0 at delta_lo and < 0 at delta_hi)");
+            goto done;
+        }
+    {
+        // jackknife errors: var = (w - 1) / w sum_i (x_i - mean_i x_i)^2
+        double err[2] = {0.0, 0.0};
+        if (n_jack > 0) {
+            for (int q = 0; q < 2; ++q) {
+                double mean = 0.0;
+                for (int i = 0; i < n_jack; ++i) mean += res[2 * (1 + i) + q];
+                mean /= n_jack;
+                double ss = 0.0;
+                for (int i = 0; i < n_jack; ++i) {
+                    const double dv = res[2 * (1 + i) + q] - mean;
+                    ss += dv * dv;
+                }
+                err[q] = std::sqrt((double)(n_jack - 1) / n_jack * ss);
+            }
+        }
+        out[0] = res[0];
+        out[1] = err[0];
+        out[2] = res[1];
+        out[3] = err[1];
+        for (int i = 0; i < n_jack; ++i) {
+            out[4 + 2 * i] = res[2 * (1 + i)];
+            out[5 + 2 * i] = res[2 * (1 + i) + 1];
+        }
+    }
+done:
+    cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}

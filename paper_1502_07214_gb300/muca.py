@@ -63,6 +63,7 @@ SIGNATURES = {
                       _P, _P],
     "muca_reweight_noalloc": [_P, _P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _P, _I32,
                               _I32, _P, _P],
+    "muca_find_peak": [_P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _D, _D, _I32, _I32, _P, _P],
     "muca_reserve_timeseries": [_P, _I64],
     "muca_timeseries_device": [_P, ctypes.c_int, _P, _P],
     "muca_get_timeseries": [_P, ctypes.c_int, _P],
@@ -298,6 +299,35 @@ def reweight(e_j, e_d, m, lnW, e_min, beta, V, delta_grid, precision=64, n_rows=
             _stream_ptr(stream))
     _ck(rc)
     return out
+
+
+def find_peak(e_j, e_d, lnW, e_min, beta, delta_lo, delta_hi, n_iter=60, n_jack=0, n_rows=None,
+              row_len=None, row_stride=None, stream=None):
+    """``muca_find_peak``: Delta*_L and C*_L (Sec. III) with jackknife errors.
+    e_j, e_d are int32 CUDA tensors shaped [n_rows][row_len] (one row per
+    sweep), or raw device addresses with n_rows/row_len/row_stride given.
+    Returns (delta_star, delta_err, c_star, c_err, subsets [n_jack][2])."""
+    ptrs = []
+    for t in (e_j, e_d):
+        if isinstance(t, int):
+            ptrs.append(ctypes.c_void_p(t))
+        else:
+            import torch
+            assert t.is_cuda and t.dtype == torch.int32, "samples must be int32 CUDA tensors"
+            assert t.is_contiguous()
+            ptrs.append(ctypes.c_void_p(t.data_ptr()))
+    if n_rows is None:
+        if e_d.dim() == 2:
+            n_rows, row_len = int(e_d.shape[0]), int(e_d.shape[1])
+        else:
+            n_rows, row_len = 1, int(e_d.numel())
+        row_stride = row_len
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    out = np.zeros(4 + 2 * n_jack)
+    _ck(lib().muca_find_peak(ptrs[0], ptrs[1], n_rows, row_len, row_stride, _np_ptr(lnW), e_min,
+                             len(lnW), beta, delta_lo, delta_hi, n_iter, n_jack, _np_ptr(out),
+                             _stream_ptr(stream)))
+    return out[0], out[1], out[2], out[3], out[4:].reshape(n_jack, 2)
 
 
 def reweight_context(ctx, g, delta_grid, precision=64, stream=None):
