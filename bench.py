@@ -438,6 +438,21 @@ def reweight_bench(torch, muca):
     out["samples"] = int(ed.size)
     out["grid_points"] = int(len(grid))
     out["pairs_per_s_fp32"] = out["fp32_pts_per_s"] * ed.size
+    # Delta*_L and C*_L with 20 jackknife blocks (Sec. III), bracket from the
+    # FP64 scan above
+    c = res[64][:, 2]
+    k = int(np.argmax(c))
+    lo, hi = grid[max(k - 8, 0)], grid[min(k + 8, len(grid) - 1)]
+    pk = muca.find_peak(dj.view(ed.shape), dd.view(ed.shape), lnW, 0, beta, lo, hi, n_jack=20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        pk = muca.find_peak(dj.view(ed.shape), dd.view(ed.shape), lnW, 0, beta, lo, hi,
+                            n_jack=20)
+    out["peak"] = {"delta_star": pk[0], "delta_star_err": pk[1], "c_star": pk[2],
+                   "c_star_err": pk[3], "jackknife_blocks": 20, "bisection_steps": 60,
+                   "ms": (time.perf_counter() - t0) / reps * 1e3}
     return out
 
 
