@@ -37,9 +37,11 @@ def lib():
         L.or_reweight.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
         L.or_reweight_q.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
         L.or_find_peak.argtypes = [P, P, i64, i32, P, i32, i32, dbl, dbl, dbl, i32, i32, i32, P]
+        L.or_equal_height.argtypes = [P, i64, i32, P, i32, i32, dbl, i32, dbl, dbl, i32, i32,
+                                      i32, P]
         for f in ("or_init_spins", "or_energies", "or_build_table", "or_sweeps",
                   "or_update_lnW", "or_muca_run", "or_reweight", "or_reweight_q",
-                  "or_find_peak"):
+                  "or_find_peak", "or_equal_height"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -165,4 +167,20 @@ def find_peak(e_j, e_d, lnW, e_min, beta, lo, hi, n_iter=60, n_jack=0, n_threads
     nt = n_threads or min(os.cpu_count() or 1, 1 + n_jack)
     _ck(lib().or_find_peak(_p(ej), _p(ed), ed.shape[0], ed.shape[1], _p(lw), e_min, len(lw),
                            beta, lo, hi, n_iter, n_jack, nt, _p(out)), "or_find_peak")
+    return out
+
+
+def equal_height(e_d, lnW, e_min, beta, split, lo, hi, n_iter=60, n_jack=0, n_threads=None):
+    """Delta_eqh and the barrier B (equal-height reweighted E_Delta distribution)
+    for the full series and the n_jack leave-one-block-out subsets.  e_d is
+    [n_rows][row_len].  Returns [1 + n_jack][5]: Delta_eqh, B, E of the left
+    peak, E of the right peak, E of the minimum between them."""
+    ed = np.ascontiguousarray(e_d, dtype=np.int32)
+    if ed.ndim == 1:
+        ed = ed[None, :]
+    lw = np.ascontiguousarray(lnW, dtype=np.float64)
+    out = np.zeros((1 + n_jack, 5))
+    nt = n_threads or min(os.cpu_count() or 1, 1 + n_jack)
+    _ck(lib().or_equal_height(_p(ed), ed.shape[0], ed.shape[1], _p(lw), e_min, len(lw), beta,
+                              split, lo, hi, n_iter, n_jack, nt, _p(out)), "or_equal_height")
     return out

@@ -782,3 +782,146 @@ int or_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_rows, int32_t
     free(tid);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Equal-height field and barrier (Sec. II and the barrier of Sec. IV): the    */
+/* reweighted E_Delta distribution of the series at field Delta is            */
+/*   P(E) ~ n(E) exp(-beta Delta E) / W(E),  n(E) the samples in bin E.        */
+/* Delta_eqh is where its two peaks have equal height, and                     */
+/*   B = ln(P_max / P_min)_eqh / (2 beta Delta_eqh)                            */
+/* with P_max the (common) peak height and P_min the lowest value between the */
+/* peaks.  Readings: the peaks are the highest occupied bins below and at or   */
+/* above a split E_split; raising Delta tilts ln P towards small E, so         */
+/* g = ln P_left,max - ln P_right,max grows with Delta and the caller's         */
+/* [lo, hi] must have g(lo) < 0 < g(hi); each of n_iter steps halves it (g(mid) */
+/* < 0 moves lo, else hi) and Delta_eqh is the last midpoint; ties between     */
+/* bins go to the smaller E; P_min is the smallest ln P over occupied bins     */
+/* between the two peak bins; jackknife subsets as in or_find_peak.            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const int32_t *e_d;
+    int64_t n_rows;
+    int32_t row_len;
+    int64_t skip0, skip1;
+    const double *lnW;
+    int e_min, nE, split;
+    double beta, lo, hi;
+    int n_iter;
+    double *out; /* Delta_eqh, B, E of the left peak, E of the right peak, E of the minimum */
+    int rc;
+} eqh_job;
+
+/* the two peak bins (relative to e_min) of ln P at Delta; returns g */
+static double eqh_peaks(const eqh_job *j, const double *ln_n, double delta, int *pl, int *pr)
+{
+    double vl = -INFINITY, vr = -INFINITY;
+    int al = -1, ar = -1;
+    for (int e = 0; e < j->nE; ++e) {
+        if (ln_n[e] == -INFINITY) continue;
+        const double v = ln_n[e] - j->beta * delta * (double)(j->e_min + e) - j->lnW[e];
+        if (j->e_min + e < j->split) {
+            if (v > vl) { vl = v; al = e; }
+        } else {
+            if (v > vr) { vr = v; ar = e; }
+        }
+    }
+    *pl = al;
+    *pr = ar;
+    return vl - vr;
+}
+
+static void *eqh_job_run(void *arg)
+{
+    eqh_job *j = (eqh_job *)arg;
+    double *ln_n = (double *)malloc((size_t)j->nE * sizeof(double));
+    int64_t *cnt = (int64_t *)calloc((size_t)j->nE, sizeof(int64_t));
+    if (!ln_n || !cnt) {
+        free(ln_n);
+        free(cnt);
+        j->rc = OR_ERR_NOMEM;
+        return NULL;
+    }
+    for (int64_t r = 0; r < j->n_rows; ++r) {
+        if (r >= j->skip0 && r < j->skip1) continue;
+        for (int32_t k = 0; k < j->row_len; ++k) ++cnt[j->e_d[r * j->row_len + k] - j->e_min];
+    }
+    for (int e = 0; e < j->nE; ++e) ln_n[e] = cnt[e] > 0 ? log((double)cnt[e]) : -INFINITY;
+    int pl, pr;
+    const double g_lo = eqh_peaks(j, ln_n, j->lo, &pl, &pr);
+    const int ok_lo = pl >= 0 && pr >= 0;
+    const double g_hi = eqh_peaks(j, ln_n, j->hi, &pl, &pr);
+    if (!ok_lo || pl < 0 || pr < 0 || !(g_lo < 0.0 && g_hi > 0.0)) {
+        free(ln_n);
+        free(cnt);
+        j->rc = OR_ERR_ARG;
+        return NULL;
+    }
+    double lo = j->lo, hi = j->hi;
+    for (int i = 0; i < j->n_iter; ++i) {
+        const double mid = lo + 0.5 * (hi - lo);
+        if (eqh_peaks(j, ln_n, mid, &pl, &pr) < 0.0) lo = mid;
+        else hi = mid;
+    }
+    const double d = lo + 0.5 * (hi - lo);
+    eqh_peaks(j, ln_n, d, &pl, &pr);
+    const double vl = ln_n[pl] - j->beta * d * (double)(j->e_min + pl) - j->lnW[pl];
+    const double vr = ln_n[pr] - j->beta * d * (double)(j->e_min + pr) - j->lnW[pr];
+    const double vmax = vl > vr ? vl : vr;
+    double vmin = INFINITY;
+    int pm = pl;
+    for (int e = pl; e <= pr; ++e) {
+        if (ln_n[e] == -INFINITY) continue;
+        const double v = ln_n[e] - j->beta * d * (double)(j->e_min + e) - j->lnW[e];
+        if (v < vmin) { vmin = v; pm = e; }
+    }
+    j->out[0] = d;
+    j->out[1] = (vmax - vmin) / (2.0 * j->beta * d);
+    j->out[2] = (double)(j->e_min + pl);
+    j->out[3] = (double)(j->e_min + pr);
+    j->out[4] = (double)(j->e_min + pm);
+    free(ln_n);
+    free(cnt);
+    j->rc = OR_OK;
+    return NULL;
+}
+
+int or_equal_height(const int32_t *e_d, int64_t n_rows, int32_t row_len, const double *lnW,
+                    int e_min, int nE, double beta, int split, double lo, double hi, int n_iter,
+                    int n_jack, int n_threads, double *out)
+{
+    if (!e_d || !lnW || !out || n_rows < 1 || row_len < 1 || nE < 1 || !(beta > 0.0) ||
+        !(lo < hi) || n_iter < 0 || n_jack < 0 || n_jack == 1 || n_jack > n_rows)
+        return OR_ERR_ARG;
+    for (int64_t s = 0; s < n_rows * (int64_t)row_len; ++s)
+        if (e_d[s] < e_min || e_d[s] >= e_min + nE) return OR_ERR_WINDOW;
+    const int n_sets = 1 + n_jack;
+    eqh_job *jobs = (eqh_job *)calloc((size_t)n_sets, sizeof(eqh_job));
+    pthread_t *tid = (pthread_t *)calloc((size_t)n_sets, sizeof(pthread_t));
+    if (!jobs || !tid) {
+        free(jobs);
+        free(tid);
+        return OR_ERR_NOMEM;
+    }
+    for (int b = 0; b < n_sets; ++b) {
+        eqh_job j = {e_d, n_rows, row_len, 0, 0, lnW, e_min, nE, split, beta, lo, hi, n_iter,
+                     out + 5 * b, OR_OK};
+        if (b > 0) {
+            j.skip0 = (int64_t)(b - 1) * n_rows / n_jack;
+            j.skip1 = (int64_t)b * n_rows / n_jack;
+        }
+        jobs[b] = j;
+    }
+    if (n_threads < 1) n_threads = 1;
+    for (int b0 = 0; b0 < n_sets; b0 += n_threads) {
+        const int b1 = b0 + n_threads < n_sets ? b0 + n_threads : n_sets;
+        for (int b = b0 + 1; b < b1; ++b) pthread_create(&tid[b], NULL, eqh_job_run, &jobs[b]);
+        eqh_job_run(&jobs[b0]);
+        for (int b = b0 + 1; b < b1; ++b) pthread_join(tid[b], NULL);
+    }
+    int rc = OR_OK;
+    for (int b = 0; b < n_sets; ++b)
+        if (jobs[b].rc != OR_OK) rc = jobs[b].rc;
+    free(jobs);
+    free(tid);
+    return rc;
+}

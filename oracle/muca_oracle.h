@@ -101,6 +101,15 @@ int or_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_rows, int32_t
                  const double *lnW, int e_min, int nE, double beta, double lo, double hi,
                  int n_iter, int n_jack, int n_threads, double *out);
 
+/* Equal-height field Delta_eqh and barrier B = ln(P_max/P_min)/(2 beta Delta)
+ * of the reweighted E_Delta distribution (peaks: the highest occupied bins
+ * below and at or above split), by n_iter bisection steps in [lo, hi], for
+ * the full series and the n_jack leave-one-block-out subsets.  out[5 b ..]:
+ * Delta_eqh, B, E of the left peak, E of the right peak, E of the minimum. */
+int or_equal_height(const int32_t *e_d, int64_t n_rows, int32_t row_len, const double *lnW,
+                    int e_min, int nE, double beta, int split, double lo, double hi, int n_iter,
+                    int n_jack, int n_threads, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -411,3 +411,47 @@ def test_peak_rejects_an_interval_without_the_maximum():
     ej, ed = _two_state_rows(V, n_rows=10, per_row1=3, per_row0=5)
     with pytest.raises(oracle.OracleError):
         oracle.find_peak(ej, ed, lnW, 0, beta, 3.05, 3.2)
+
+
+# ---------------------------------------------------- equal height, barrier
+def _double_well(L, T, delta_t):
+    """lnW and the series of the synthetic recipe with every E_Delta in [0, V]
+    occupied exactly once per row: the reweighted distribution at delta_t is
+    exp(0.6 L^2 (well(e) - max well)), peaks at e = 0.25 and 0.8, minimum at
+    e = 0.525 (V = L^3 divisible by 40 puts all three on bins)."""
+    V = L ** 3
+    beta = 1.0 / T
+    E = np.arange(V + 1, dtype=np.float64)
+    e = E / V
+    well = -((e - 0.25) * (e - 0.8)) ** 2 / 0.01
+    lnW = -(beta * delta_t * E + (0.6 * L * L) * (well - well.max()))
+    rows = np.array([np.roll(np.arange(V + 1), 37 * r) for r in range(8)], dtype=np.int32)
+    barrier = 0.6 * L * L * (well.max() - well[int(0.525 * V)])
+    return V, beta, lnW, rows, barrier
+
+
+def test_equal_height_closed_form():
+    L, T, dt = 10, 1.0, 2.6
+    V, beta, lnW, rows, barrier = _double_well(L, T, dt)
+    out = oracle.equal_height(rows, lnW, 0, beta, int(0.525 * V), dt - 0.05, dt + 0.05,
+                              n_iter=60, n_jack=4)
+    np.testing.assert_allclose(out[:, 0], dt, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(out[:, 1], barrier / (2 * beta * dt), rtol=1e-9)
+    assert np.all(out[:, 2] == 0.25 * V) and np.all(out[:, 3] == 0.8 * V)
+    assert np.all(out[:, 4] == 0.525 * V)
+    assert np.all(out[1:] == out[1])  # identical subsets, identical results
+
+
+def test_equal_height_noisy_series_near_the_construction():
+    """The sampled synthetic series (Poisson noise in every bin) puts Delta_eqh
+    near the constructed transition field."""
+    ej, ed, m, lnW, dt = wl.synthetic_series(L=10, T=1.4182, n_walkers=64, n_samples=2000, seed=7)
+    out = oracle.equal_height(ed, lnW, 0, 1 / 1.4182, 525, dt - 0.05, dt + 0.05)
+    assert abs(out[0, 0] - dt) < 2e-3
+
+
+def test_equal_height_rejects_an_interval_without_it():
+    L, T, dt = 10, 1.0, 2.6
+    V, beta, lnW, rows, barrier = _double_well(L, T, dt)
+    with pytest.raises(oracle.OracleError):
+        oracle.equal_height(rows, lnW, 0, beta, int(0.525 * V), dt + 0.01, dt + 0.05)
