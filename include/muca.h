@@ -216,6 +216,30 @@ int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_rows, int32
                    double beta, double delta_lo, double delta_hi, int32_t n_iter, int32_t n_jack,
                    double *out, void *stream);
 
+/* Equal-height field and barrier (Sec. II, Eq. of B in Sec. IV): the series'
+ * reweighted E_Delta distribution at field Delta is
+ * P(E) ~ n(E) exp(-beta Delta E) / W(E), n(E) its samples in bin E.  Its peaks
+ * are the highest occupied bins below and at or above split; Delta_eqh is
+ * where they are equally high, found by n_iter bisection steps in
+ * [delta_lo, delta_hi] (the lower-E peak must be lower at delta_lo and higher
+ * at delta_hi; mid = lo + (hi - lo) / 2, lower at mid moves lo, else hi; the
+ * result is the last midpoint; ties between bins go to the smaller E), and
+ * B = ln(P_max / P_min) / (2 beta Delta_eqh) with P_min the lowest occupied
+ * bin between the peaks.  Full series and n_jack leave-one-block-out subsets
+ * as muca_find_peak.
+ *   e_d, n_rows, row_len, row_stride, lnW, e_min, n_e, beta   as muca_find_peak
+ *   out   host FP64 [7 + 2 n_jack]: Delta_eqh, its jackknife error, B, its
+ *         jackknife error, E of the lower peak, E of the upper peak, E of the
+ *         minimum (full series), then (Delta_eqh, B) of each subset
+ * MUCA_ERR_INVALID_ARG when the interval does not bracket Delta_eqh for the
+ * full series or a subset; MUCA_ERR_WINDOW for a sample outside the window.
+ * Allocates its scratch with cudaMallocAsync on the stream; synchronises the
+ * stream. */
+int muca_equal_height(const int32_t *e_d, int64_t n_rows, int32_t row_len, int64_t row_stride,
+                      const double *lnW, int32_t e_min, int32_t n_e, double beta, int32_t split,
+                      double delta_lo, double delta_hi, int32_t n_iter, int32_t n_jack,
+                      double *out, void *stream);
+
 /* ------------------------------------------------------------ time series */
 
 /* Reserve room for n_samples recorded sweeps per walker (device memory,

@@ -33,6 +33,7 @@ namespace {
 
 // Integer sums per jackknife block: cnt[b][E], sej[b][E].  bnd[i] is the first
 // row of block i (bnd[n_blocks] = n_rows).
+template <bool SEJ>
 __global__ void jk_bin_kernel(const int32_t *__restrict__ ej, const int32_t *__restrict__ ed,
                               int64_t n_rows, int row_len, int64_t row_stride, int e_min, int nE,
                               const int64_t *__restrict__ bnd, int n_blocks,
@@ -51,7 +52,7 @@ __global__ void jk_bin_kernel(const int32_t *__restrict__ ej, const int32_t *__r
                 continue;
             }
             atomicAdd(cb + e, 1ull);
-            atomicAdd(sb + e, (unsigned long long)(long long)__ldg(ej + o));
+            if (SEJ) atomicAdd(sb + e, (unsigned long long)(long long)__ldg(ej + o));
         }
     }
 }
@@ -238,6 +239,140 @@ peak_kernel(const double *__restrict__ n_all, const double *__restrict__ mj_all,
     }
 }
 
+// ---------------------------------------------------- equal height, barrier
+// The reweighted E_Delta distribution at field Delta, from the series' count
+// n(E) per bin: ln P(E) = ln n(E) - beta Delta E - lnW(E) (+ const).  Delta_eqh
+// is where its highest bins below and at or above split are equally high;
+// B = ln(P_max / P_min) / (2 beta Delta_eqh), P_min the lowest occupied bin
+// between the two peaks.
+
+// Per data set d and bin: ln of the sample count (-inf when empty).
+__global__ void jk_lncount_kernel(const unsigned long long *__restrict__ cnt, int n_blocks, int nE,
+                                  double *lnn)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.y;
+    if (e >= nE) return;
+    unsigned long long n = 0;
+    for (int b = 0; b < n_blocks; ++b) n += cnt[(size_t)b * nE + e];
+    if (d > 0) n -= cnt[(size_t)(d - 1) * nE + e];
+    lnn[(size_t)d * nE + e] = n ? log((double)n) : -INFINITY;
+}
+
+// ln P(E) at Delta, evaluated in the order (ln n - (beta Delta) E) - lnW.
+__device__ __forceinline__ double eqh_lnp(double lnn, double bd, int E, double lnw)
+{
+    return __dsub_rn(__dsub_rn(lnn, __dmul_rn(bd, (double)E)), lnw);
+}
+
+// Block-wide best (value, bin): larger value wins when want_max, smaller when
+// not; ties go to the smaller bin.  Every thread gets the result.
+__device__ void eqh_best(double &v, int &a, bool want_max, double *sh, int *shi)
+{
+    auto better = [&](double v2, int a2) {
+        if (a2 < 0) return false;
+        if (a < 0) return true;
+        if (want_max ? v2 > v : v2 < v) return true;
+        return v2 == v && a2 < a;
+    };
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        const int a2 = __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        if (better(v2, a2)) {
+            v = v2;
+            a = a2;
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh[wid] = v;
+        shi[wid] = a;
+    }
+    __syncthreads();
+    v = sh[0];
+    a = shi[0];
+    for (int i = 1; i < nw; ++i)
+        if (better(sh[i], shi[i])) {
+            v = sh[i];
+            a = shi[i];
+        }
+}
+
+// The two peak bins at Delta (relative to e_min, -1 when a side is empty); returns g.
+__device__ double eqh_peaks(const double *lnn, const double *lnW, int nE, int e_min, int split,
+                            double bd, int &pl, int &pr, double &vl, double &vr, double *sh,
+                            int *shi)
+{
+    vl = -INFINITY;
+    vr = -INFINITY;
+    pl = -1;
+    pr = -1;
+    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+        if (lnn[e] == -INFINITY) continue;
+        const double v = eqh_lnp(lnn[e], bd, e_min + e, lnW[e]);
+        if (e_min + e < split) {
+            if (pl < 0 || v > vl) {
+                vl = v;
+                pl = e;
+            }
+        } else if (pr < 0 || v > vr) {
+            vr = v;
+            pr = e;
+        }
+    }
+    eqh_best(vl, pl, true, sh, shi);
+    eqh_best(vr, pr, true, sh, shi);
+    return vl - vr;
+}
+
+__global__ void __launch_bounds__(kPkThreads)
+eqh_kernel(const double *__restrict__ lnn_all, const double *__restrict__ lnW, int nE, int e_min,
+           int split, double beta, double lo, double hi, int n_iter, double *res, int *bad)
+{
+    __shared__ double sh[32];
+    __shared__ int shi[32];
+    const int d = blockIdx.x;
+    const double *lnn = lnn_all + (size_t)d * nE;
+    int pl, pr;
+    double vl, vr;
+    const double g_lo = eqh_peaks(lnn, lnW, nE, e_min, split, beta * lo, pl, pr, vl, vr, sh, shi);
+    const bool ok_lo = pl >= 0 && pr >= 0;
+    const double g_hi = eqh_peaks(lnn, lnW, nE, e_min, split, beta * hi, pl, pr, vl, vr, sh, shi);
+    if (!ok_lo || pl < 0 || pr < 0 || !(g_lo < 0.0 && g_hi > 0.0)) {
+        if (threadIdx.x == 0) bad[d] = 1;
+        return;
+    }
+    for (int i = 0; i < n_iter; ++i) {
+        const double mid = lo + 0.5 * (hi - lo);
+        if (eqh_peaks(lnn, lnW, nE, e_min, split, beta * mid, pl, pr, vl, vr, sh, shi) < 0.0) lo = mid;
+        else hi = mid;
+    }
+    const double dq = lo + 0.5 * (hi - lo);
+    const double bd = beta * dq;
+    eqh_peaks(lnn, lnW, nE, e_min, split, bd, pl, pr, vl, vr, sh, shi);
+    const double vmax = vl > vr ? vl : vr;
+    double vmin = INFINITY;
+    int pm = -1;
+    for (int e = pl + (int)threadIdx.x; e <= pr; e += blockDim.x) {
+        if (lnn[e] == -INFINITY) continue;
+        const double v = eqh_lnp(lnn[e], bd, e_min + e, lnW[e]);
+        if (pm < 0 || v < vmin) {
+            vmin = v;
+            pm = e;
+        }
+    }
+    eqh_best(vmin, pm, false, sh, shi);
+    if (threadIdx.x == 0) {
+        double *o = res + 5 * (size_t)d;
+        o[0] = dq;
+        o[1] = (vmax - vmin) / (2.0 * beta * dq);
+        o[2] = (double)(e_min + pl);
+        o[3] = (double)(e_min + pr);
+        o[4] = (double)(e_min + pm);
+    }
+}
+
 int pk_fail(int code, const std::string &msg)
 {
     muca::set_last_error(msg.c_str());
@@ -303,8 +438,8 @@ extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_
     {
         dim3 g((unsigned)std::min<int64_t>((row_len + 255) / 256, 1024),
                (unsigned)std::min<int64_t>(n_rows, 4096));
-        jk_bin_kernel<<<g, 256, 0, st>>>(e_j, e_d, n_rows, row_len, row_stride, e_min, n_e, d_bnd,
-                                         n_blocks, cnt, sej, d_bad);
+        jk_bin_kernel<true><<<g, 256, 0, st>>>(e_j, e_d, n_rows, row_len, row_stride, e_min, n_e,
+                                               d_bnd, n_blocks, cnt, sej, d_bad);
         PCK(cudaGetLastError());
         dim3 g2((unsigned)((n_e + 255) / 256), (unsigned)n_sets);
         jk_stats_kernel<<<g2, 256, 0, st>>>(cnt, sej, n_blocks, n_e, n_all, mj_all);
@@ -352,6 +487,123 @@ extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_
         for (int i = 0; i < n_jack; ++i) {
             out[4 + 2 * i] = res[2 * (1 + i)];
             out[5 + 2 * i] = res[2 * (1 + i) + 1];
+        }
+    }
+done:
+    cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
+    return rc;
+}
+
+extern "C" int muca_equal_height(const int32_t *e_d, int64_t n_rows, int32_t row_len,
+                                 int64_t row_stride, const double *lnW, int32_t e_min,
+                                 int32_t n_e, double beta, int32_t split, double delta_lo,
+                                 double delta_hi, int32_t n_iter, int32_t n_jack, double *out,
+                                 void *stream)
+{
+    if (!e_d || !lnW || !out) return pk_fail(MUCA_ERR_INVALID_ARG, "muca_equal_height: null pointer");
+    if (n_rows < 1 || row_len < 1 || (n_rows > 1 && row_stride < row_len) || n_e < 1 ||
+        n_iter < 0 || n_iter > 200 || n_jack < 0 || n_jack == 1 || n_jack > n_rows ||
+        n_jack > 1024)
+        return pk_fail(MUCA_ERR_INVALID_ARG, "muca_equal_height: bad sizes");
+    if (!(beta > 0.0) || !std::isfinite(beta) || !std::isfinite(delta_lo) ||
+        !std::isfinite(delta_hi) || !(delta_lo < delta_hi))
+        return pk_fail(MUCA_ERR_INVALID_ARG,
+                       "muca_equal_height: need beta > 0 and delta_lo < delta_hi");
+    for (int e = 0; e < n_e; ++e)
+        if (!std::isfinite(lnW[e]))
+            return pk_fail(MUCA_ERR_INVALID_ARG, "muca_equal_height: lnW not finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n_blocks = n_jack > 0 ? n_jack : 1, n_sets = 1 + n_jack;
+    std::vector<int64_t> bnd(n_blocks + 1);
+    for (int i = 0; i <= n_blocks; ++i) bnd[i] = (int64_t)i * n_rows / n_blocks;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b_cnt = al((size_t)n_blocks * n_e * sizeof(unsigned long long));
+    const size_t b_lnn = al((size_t)n_sets * n_e * sizeof(double));
+    const size_t b_lnw = al((size_t)n_e * sizeof(double));
+    const size_t b_bnd = al(bnd.size() * sizeof(int64_t));
+    const size_t b_res = al((size_t)5 * n_sets * sizeof(double));
+    const size_t b_bad = al((size_t)(n_sets + 1) * sizeof(int));
+    char *p = nullptr;
+    cudaError_t ce = cudaMallocAsync((void **)&p, b_cnt + b_lnn + b_lnw + b_bnd + b_res + b_bad, st);
+    if (ce != cudaSuccess)
+        return pk_fail(ce == cudaErrorMemoryAllocation ? MUCA_ERR_OOM : MUCA_ERR_CUDA,
+                       std::string("cudaMallocAsync: ") + cudaGetErrorString(ce));
+    unsigned long long *cnt = (unsigned long long *)p;
+    double *lnn = (double *)(p + b_cnt);
+    double *d_lnW = (double *)(p + b_cnt + b_lnn);
+    int64_t *d_bnd = (int64_t *)(p + b_cnt + b_lnn + b_lnw);
+    double *d_res = (double *)(p + b_cnt + b_lnn + b_lnw + b_bnd);
+    int *d_bad = (int *)(p + b_cnt + b_lnn + b_lnw + b_bnd + b_res);
+    std::vector<double> res(5 * (size_t)n_sets, 0.0);
+    std::vector<int> bad(n_sets + 1, 0);
+    int rc = MUCA_OK;
+#define PCK(call)                                                                         \
+    do {                                                                                  \
+        ce = (call);                                                                      \
+        if (ce != cudaSuccess) {                                                          \
+            rc = pk_fail(MUCA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(ce)); \
+            goto done;                                                                    \
+        }                                                                                 \
+    } while (0)
+    PCK(cudaMemsetAsync(p, 0, b_cnt, st));
+    PCK(cudaMemsetAsync(d_bad, 0, b_bad, st));
+    PCK(cudaMemcpyAsync(d_lnW, lnW, (size_t)n_e * sizeof(double), cudaMemcpyHostToDevice, st));
+    PCK(cudaMemcpyAsync(d_bnd, bnd.data(), bnd.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    {
+        dim3 g((unsigned)std::min<int64_t>((row_len + 255) / 256, 1024),
+               (unsigned)std::min<int64_t>(n_rows, 4096));
+        jk_bin_kernel<false><<<g, 256, 0, st>>>(e_d, e_d, n_rows, row_len, row_stride, e_min, n_e,
+                                                d_bnd, n_blocks, cnt, nullptr, d_bad);
+        PCK(cudaGetLastError());
+        dim3 g2((unsigned)((n_e + 255) / 256), (unsigned)n_sets);
+        jk_lncount_kernel<<<g2, 256, 0, st>>>(cnt, n_blocks, n_e, lnn);
+        PCK(cudaGetLastError());
+        eqh_kernel<<<n_sets, kPkThreads, 0, st>>>(lnn, d_lnW, n_e, e_min, split, beta, delta_lo,
+                                                  delta_hi, n_iter, d_res, d_bad + 1);
+        PCK(cudaGetLastError());
+    }
+    PCK(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PCK(cudaMemcpyAsync(bad.data(), d_bad, bad.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PCK(cudaStreamSynchronize(st));
+#undef PCK
+    if (bad[0]) {
+        rc = pk_fail(MUCA_ERR_WINDOW, "a sample's E_Delta lies outside [e_min, e_min + n_e)");
+        goto done;
+    }
+    for (int d = 0; d < n_sets; ++d)
+        if (bad[1 + d]) {
+            rc = pk_fail(MUCA_ERR_INVALID_ARG,
+                         "muca_equal_height: [delta_lo, delta_hi] does not bracket the equal-height "
+                         "field for data set " + std::to_string(d) +
+                         " (the peak below split must be lower at delta_lo and higher at delta_hi)");
+            goto done;
+        }
+    {
+        double err[2] = {0.0, 0.0};
+        if (n_jack > 0) {
+            for (int q = 0; q < 2; ++q) {
+                double mean = 0.0;
+                for (int i = 0; i < n_jack; ++i) mean += res[5 * (1 + i) + q];
+                mean /= n_jack;
+                double ss = 0.0;
+                for (int i = 0; i < n_jack; ++i) {
+                    const double dv = res[5 * (1 + i) + q] - mean;
+                    ss += dv * dv;
+                }
+                err[q] = std::sqrt((double)(n_jack - 1) / n_jack * ss);
+            }
+        }
+        out[0] = res[0];
+        out[1] = err[0];
+        out[2] = res[1];
+        out[3] = err[1];
+        out[4] = res[2];
+        out[5] = res[3];
+        out[6] = res[4];
+        for (int i = 0; i < n_jack; ++i) {
+            out[7 + 2 * i] = res[5 * (1 + i)];
+            out[8 + 2 * i] = res[5 * (1 + i) + 1];
         }
     }
 done:

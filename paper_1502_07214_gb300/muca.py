@@ -64,6 +64,8 @@ SIGNATURES = {
     "muca_reweight_noalloc": [_P, _P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _P, _I32,
                               _I32, _P, _P],
     "muca_find_peak": [_P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _D, _D, _I32, _I32, _P, _P],
+    "muca_equal_height": [_P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _D, _D, _I32, _I32, _P,
+                          _P],
     "muca_reserve_timeseries": [_P, _I64],
     "muca_timeseries_device": [_P, ctypes.c_int, _P, _P],
     "muca_get_timeseries": [_P, ctypes.c_int, _P],
@@ -328,6 +330,33 @@ def find_peak(e_j, e_d, lnW, e_min, beta, delta_lo, delta_hi, n_iter=60, n_jack=
                              len(lnW), beta, delta_lo, delta_hi, n_iter, n_jack, _np_ptr(out),
                              _stream_ptr(stream)))
     return out[0], out[1], out[2], out[3], out[4:].reshape(n_jack, 2)
+
+
+def equal_height(e_d, lnW, e_min, beta, split, delta_lo, delta_hi, n_iter=60, n_jack=0,
+                 n_rows=None, row_len=None, row_stride=None, stream=None):
+    """``muca_equal_height``: Delta_eqh and the barrier B with jackknife errors.
+    e_d is an int32 CUDA tensor [n_rows][row_len] (or a raw device address with
+    n_rows/row_len/row_stride given).  Returns (delta_eqh, delta_err, B, B_err,
+    (E_lower_peak, E_upper_peak, E_min), subsets [n_jack][2])."""
+    if isinstance(e_d, int):
+        ptr = ctypes.c_void_p(e_d)
+    else:
+        import torch
+        assert e_d.is_cuda and e_d.dtype == torch.int32, "samples must be int32 CUDA tensors"
+        assert e_d.is_contiguous()
+        ptr = ctypes.c_void_p(e_d.data_ptr())
+    if n_rows is None:
+        if e_d.dim() == 2:
+            n_rows, row_len = int(e_d.shape[0]), int(e_d.shape[1])
+        else:
+            n_rows, row_len = 1, int(e_d.numel())
+        row_stride = row_len
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    out = np.zeros(7 + 2 * n_jack)
+    _ck(lib().muca_equal_height(ptr, n_rows, row_len, row_stride, _np_ptr(lnW), e_min, len(lnW),
+                                beta, split, delta_lo, delta_hi, n_iter, n_jack, _np_ptr(out),
+                                _stream_ptr(stream)))
+    return out[0], out[1], out[2], out[3], tuple(int(v) for v in out[4:7]), out[7:].reshape(n_jack, 2)
 
 
 def reweight_context(ctx, g, delta_grid, precision=64, stream=None):

@@ -130,3 +130,71 @@ def test_full_size_peak_is_the_maximum_of_c():
     assert cf.max() <= cs * (1 + 1e-12)
     assert abs(fine[int(np.argmax(cf))] - ds) <= fine[1] - fine[0]
     assert de > 0 and np.all(np.abs(sub[:, 0] - ds) <= 10 * de)
+
+
+# ---------------------------------------------------- equal height, barrier
+def double_well(L, T, delta_t):
+    """Every E_Delta in [0, V] once per row under the synthetic recipe's lnW:
+    equal peaks at e = 0.25 and 0.8 exactly at delta_t, minimum at e = 0.525."""
+    V = L ** 3
+    beta = 1.0 / T
+    E = np.arange(V + 1, dtype=np.float64)
+    e = E / V
+    well = -((e - 0.25) * (e - 0.8)) ** 2 / 0.01
+    lnW = -(beta * delta_t * E + (0.6 * L * L) * (well - well.max()))
+    rows = np.array([np.roll(np.arange(V + 1), 37 * r) for r in range(8)], dtype=np.int32)
+    return V, beta, lnW, rows, 0.6 * L * L * (well.max() - well[int(0.525 * V)])
+
+
+def test_equal_height_closed_form_and_oracle():
+    L, T, dt = 10, 1.0, 2.6
+    V, beta, lnW, rows, barrier = double_well(L, T, dt)
+    got = muca().equal_height(dev(rows), lnW, 0, beta, int(0.525 * V), dt - 0.05, dt + 0.05,
+                              n_jack=4)
+    assert abs(got[0] - dt) <= 1e-12
+    assert abs(got[2] - barrier / (2 * beta * dt)) <= 1e-9 * got[2]
+    assert got[4] == (250, 800, 525)
+    assert got[1] <= 1e-12 and got[3] <= 1e-9 * got[2]
+
+
+@pytest.mark.parametrize("L,nw,ns,w", [(10, 64, 2000, 5), (16, 256, 400, 8)])
+def test_equal_height_matches_oracle(L, nw, ns, w):
+    T = 1.4182
+    beta, V = 1 / T, L ** 3
+    ej, ed, m, lnW, dt = wl.synthetic_series(L=L, T=T, n_walkers=nw, n_samples=ns, seed=3 * L)
+    split = int(0.525 * V)
+    ref = oracle.equal_height(ed, lnW, 0, beta, split, dt - 0.05, dt + 0.05, n_jack=w)
+    got = muca().equal_height(dev(ed), lnW, 0, beta, split, dt - 0.05, dt + 0.05, n_jack=w)
+    assert abs(got[0] - ref[0, 0]) <= 1e-9
+    assert abs(got[2] - ref[0, 1]) <= 1e-12 * abs(ref[0, 1])
+    assert got[4] == tuple(int(v) for v in ref[0, 2:5])
+    np.testing.assert_allclose(got[5][:, 0], ref[1:, 0], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(got[5][:, 1], ref[1:, 1], rtol=1e-12)
+    np.testing.assert_allclose(got[1], jack_err(ref[1:, 0]), rtol=1e-5)
+    np.testing.assert_allclose(got[3], jack_err(ref[1:, 1]), rtol=1e-5)
+
+
+def test_equal_height_full_size_matches_oracle():
+    """The reweight workload (4096 walkers x 10^4 samples of L = 32), 10 jackknife blocks."""
+    s = wl.REWEIGHT
+    ej, ed, m, lnW, dt = wl.synthetic_series()
+    beta, V = 1 / s["T"], s["L"] ** 3
+    split = int(0.525 * V)
+    ref = oracle.equal_height(ed, lnW, 0, beta, split, dt - 0.01, dt + 0.01, n_jack=10)
+    got = muca().equal_height(dev(ed), lnW, 0, beta, split, dt - 0.01, dt + 0.01, n_jack=10)
+    assert abs(got[0] - ref[0, 0]) <= 1e-9 and abs(got[0] - dt) < 1e-3
+    assert abs(got[2] - ref[0, 1]) <= 1e-12 * abs(ref[0, 1])
+    np.testing.assert_allclose(got[5][:, 0], ref[1:, 0], rtol=0, atol=1e-9)
+
+
+def test_equal_height_errors():
+    L, T, dt = 10, 1.0, 2.6
+    V, beta, lnW, rows, barrier = double_well(L, T, dt)
+    with pytest.raises(muca().MucaError) as e:
+        muca().equal_height(dev(rows), lnW, 0, beta, int(0.525 * V), dt + 0.01, dt + 0.05)
+    assert e.value.code == muca().ERR_INVALID_ARG
+    bad = rows.copy()
+    bad[2, 5] = V + 3
+    with pytest.raises(muca().MucaError) as e:
+        muca().equal_height(dev(bad), lnW, 0, beta, int(0.525 * V), dt - 0.05, dt + 0.05)
+    assert e.value.code == muca().ERR_WINDOW
