@@ -453,6 +453,19 @@ def reweight_bench(torch, muca):
     out["peak"] = {"delta_star": pk[0], "delta_star_err": pk[1], "c_star": pk[2],
                    "c_star_err": pk[3], "jackknife_blocks": 20, "bisection_steps": 60,
                    "ms": (time.perf_counter() - t0) / reps * 1e3}
+    # equal-height field and barrier, split between the phases at e = 0.525
+    split = int(0.525 * V)
+    eq = muca.equal_height(dd.view(ed.shape), lnW, 0, beta, split, lo - 0.01, hi + 0.01,
+                           n_jack=20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        eq = muca.equal_height(dd.view(ed.shape), lnW, 0, beta, split, lo - 0.01, hi + 0.01,
+                               n_jack=20)
+    out["equal_height"] = {"delta_eqh": eq[0], "delta_eqh_err": eq[1], "barrier": eq[2],
+                           "barrier_err": eq[3], "barrier_over_L2": eq[2] / s["L"] ** 2,
+                           "jackknife_blocks": 20,
+                           "ms": (time.perf_counter() - t0) / reps * 1e3}
     return out
 
 
