@@ -725,9 +725,12 @@ __device__ __forceinline__ void ws_stage(const WsSmem &sm, const uint32_t *lat, 
     const int r_self = z1 * L + y1;
     const int lg = __ffs(sm.G >> 2) - 1;  // chunks of 4 walkers per word: G / 4 (a power of 2)
     const int nch = sm.G >> 2;
-    for (int c = ht; c < 5 * Lw * nch; c += kWsHelp) {
+    // the y-1 row is read only by rows with y = 0 (the others take the old
+    // spins of the row before, already in shared memory)
+    const int f0 = (y1 == 0) ? 0 : 1;
+    for (int c = ht; c < (5 - f0) * Lw * nch; c += kWsHelp) {
         const int fj = c >> lg, k = c & (nch - 1);
-        const int f = fj / Lw, j = fj - f * Lw;
+        const int f = f0 + fj / Lw, j = fj - (fj / Lw) * Lw;
         const int row = f == 0 ? r_ym : f == 1 ? r_yp : f == 2 ? r_zm : f == 3 ? r_zp : r_self;
         cp_async16(sm.pf(f, j) + 4 * k, lat + ((ptrdiff_t)row * Lw + j) * st + 4 * k);
     }
