@@ -63,6 +63,24 @@ def traffic_per_launch(res, sweeps):
     return None if b is None else b * sweeps
 
 
+def replica_seed(seed, rank):
+    """With N GPUs every rank runs an independent replica of the workload: the
+    same sizes, its own Philox seed."""
+    return seed + 7919 * rank
+
+
+def job_rate(ms_local, units_per_rank, world, dist=None, device="cpu"):
+    """Whole-job rate over N ranks: every rank's units over the slowest rank's
+    time (the maximum of the ranks' timed regions).  Returns (rate, max_ms)."""
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return units_per_rank * world / (ms / 1e3), ms
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -219,7 +237,7 @@ def run_ours(args, rank, world, local_rank):
     grid = wl.delta_grid(2.964)  # the first-order transition field at T=0.9 (Sec. III)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ctx = muca.Context([{"L": L, "T": T, "n_walkers": W}], seed=s["seed"] + 7919 * rank)
+    ctx = muca.Context([{"L": L, "T": T, "n_walkers": W}], seed=replica_seed(s["seed"], rank))
     ctx.reserve_timeseries(meas)
     res, wpb, lanes = ctx.get_config(0)
     launches_per_sweep_call = 1
@@ -246,11 +264,7 @@ def run_ours(args, rank, world, local_rank):
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    elapsed = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(elapsed, op=dist.ReduceOp.MAX)
-    ms = float(elapsed.item())
-    value = attempts_step * args.steps * world / (ms / 1e3)
+    value, ms = job_rate(ms, attempts_step * args.steps, world, dist, device="cuda")
 
     # plain form: the same step with one launch per call and host-driven merges;
     # CUDA events on the launching stream around every sweep launch give the
