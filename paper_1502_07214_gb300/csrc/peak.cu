@@ -169,9 +169,11 @@ __device__ int pk_argmax(const double *n, const double *lnW, int nE, int e_min, 
 
 // Covariance <(E_J - <E_J>)(E_Delta - <E_Delta>)> and third moment
 // <(E_J - <E_J>)(E_Delta - <E_Delta>)^2> of the data set at field Delta.
+// wb: this data set's scratch of nE weights; each thread reads back only the
+// weights it wrote, so the second pass needs no synchronisation for them.
 __device__ void pk_moments(const double *n, const double *mj, const double *lnW, int nE, int e_min,
-                           double beta, double delta, double *sh, int *shi, double &cov,
-                           double &third)
+                           double beta, double delta, double *sh, int *shi, double *wb,
+                           double &cov, double &third)
 {
     const double c = beta * delta;
     int es = pk_argmax(n, lnW, nE, e_min, c, sh, shi);
@@ -183,6 +185,7 @@ __device__ void pk_moments(const double *n, const double *mj, const double *lnW,
         if (ne <= 0.0) continue;
         const double w =
             exp(__dsub_rn(-__dmul_rn(c, (double)(e - es)), __dsub_rn(lnW[e], lstar))) * ne;
+        wb[e] = w;
         a[0].add(w);
         a[1].add(w * mj[e]);
         a[2].add(w * (double)(e_min + e));
@@ -194,8 +197,7 @@ __device__ void pk_moments(const double *n, const double *mj, const double *lnW,
     for (int e = threadIdx.x; e < nE; e += blockDim.x) {
         const double ne = n[e];
         if (ne <= 0.0) continue;
-        const double w =
-            exp(__dsub_rn(-__dmul_rn(c, (double)(e - es)), __dsub_rn(lnW[e], lstar))) * ne;
+        const double w = wb[e];
         const double dj = mj[e] - jbar, dd = (double)(e_min + e) - dbar;
         b[0].add(w * (dj * dd));
         b[1].add(w * (dj * dd * dd));
@@ -210,15 +212,16 @@ __device__ void pk_moments(const double *n, const double *mj, const double *lnW,
 __global__ void __launch_bounds__(kPkThreads)
 peak_kernel(const double *__restrict__ n_all, const double *__restrict__ mj_all,
             const double *__restrict__ lnW, int nE, int e_min, double beta, double lo, double hi,
-            int n_iter, double *res, int *bad)
+            int n_iter, double *res, int *bad, double *wscr)
 {
     __shared__ double sh[64];
     __shared__ int shi[32];
     const int d = blockIdx.x;
     const double *n = n_all + (size_t)d * nE, *mj = mj_all + (size_t)d * nE;
+    double *wb = wscr + (size_t)d * nE;
     double cov, t_lo, t_hi;
-    pk_moments(n, mj, lnW, nE, e_min, beta, lo, sh, shi, cov, t_lo);
-    pk_moments(n, mj, lnW, nE, e_min, beta, hi, sh, shi, cov, t_hi);
+    pk_moments(n, mj, lnW, nE, e_min, beta, lo, sh, shi, wb, cov, t_lo);
+    pk_moments(n, mj, lnW, nE, e_min, beta, hi, sh, shi, wb, cov, t_hi);
     if (!(t_lo > 0.0 && t_hi < 0.0)) {
         if (threadIdx.x == 0) bad[d] = 1;
         return;
@@ -226,13 +229,13 @@ peak_kernel(const double *__restrict__ n_all, const double *__restrict__ mj_all,
     for (int i = 0; i < n_iter; ++i) {
         const double mid = lo + 0.5 * (hi - lo);
         double t;
-        pk_moments(n, mj, lnW, nE, e_min, beta, mid, sh, shi, cov, t);
+        pk_moments(n, mj, lnW, nE, e_min, beta, mid, sh, shi, wb, cov, t);
         if (t > 0.0) lo = mid;
         else hi = mid;
     }
     const double ds = lo + 0.5 * (hi - lo);
     double t;
-    pk_moments(n, mj, lnW, nE, e_min, beta, ds, sh, shi, cov, t);
+    pk_moments(n, mj, lnW, nE, e_min, beta, ds, sh, shi, wb, cov, t);
     if (threadIdx.x == 0) {
         res[2 * d] = ds;
         res[2 * d + 1] = -beta * cov;
@@ -409,8 +412,10 @@ extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_
     const size_t b_bnd = al(bnd.size() * sizeof(int64_t));
     const size_t b_res = al((size_t)2 * n_sets * sizeof(double));
     const size_t b_bad = al((size_t)(n_sets + 1) * sizeof(int));
+    const size_t b_w = al((size_t)n_sets * n_e * sizeof(double));
     char *p = nullptr;
-    cudaError_t ce = cudaMallocAsync((void **)&p, b_sums + b_sets + b_lnw + b_bnd + b_res + b_bad, st);
+    cudaError_t ce =
+        cudaMallocAsync((void **)&p, b_sums + b_sets + b_lnw + b_bnd + b_res + b_bad + b_w, st);
     if (ce != cudaSuccess)
         return pk_fail(ce == cudaErrorMemoryAllocation ? MUCA_ERR_OOM : MUCA_ERR_CUDA,
                        std::string("cudaMallocAsync: ") + cudaGetErrorString(ce));
@@ -420,6 +425,7 @@ extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_
     int64_t *d_bnd = (int64_t *)(p + b_sums + b_sets + b_lnw);
     double *d_res = (double *)(p + b_sums + b_sets + b_lnw + b_bnd);
     int *d_bad = (int *)(p + b_sums + b_sets + b_lnw + b_bnd + b_res);  // [0]: window, [1 + d]
+    double *d_w = (double *)(p + b_sums + b_sets + b_lnw + b_bnd + b_res + b_bad);
     std::vector<double> res(2 * (size_t)n_sets, 0.0);
     std::vector<int> bad(n_sets + 1, 0);
     int rc = MUCA_OK;
@@ -445,7 +451,8 @@ extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_
         jk_stats_kernel<<<g2, 256, 0, st>>>(cnt, sej, n_blocks, n_e, n_all, mj_all);
         PCK(cudaGetLastError());
         peak_kernel<<<n_sets, kPkThreads, 0, st>>>(n_all, mj_all, d_lnW, n_e, e_min, beta,
-                                                   delta_lo, delta_hi, n_iter, d_res, d_bad + 1);
+                                                   delta_lo, delta_hi, n_iter, d_res, d_bad + 1,
+                                                   d_w);
         PCK(cudaGetLastError());
     }
     PCK(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
