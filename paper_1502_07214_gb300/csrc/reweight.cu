@@ -519,7 +519,7 @@ __device__ __forceinline__ F2 expo32(float chi, float clo, int E, float lwh, flo
 constexpr int kGridD = 4;
 
 template <int D>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)  // four blocks per SM: more warps hide the latencies
 grid_kernel_f32(BinStats<float> s, int nE, int e_min, float beta, int V,
                 const float *__restrict__ c_hi, const float *__restrict__ c_lo, int n_grid,
                 double *__restrict__ out)
