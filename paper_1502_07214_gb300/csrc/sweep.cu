@@ -14,13 +14,17 @@
 // sits on the chain; from L2 that load costs hundreds of cycles, from shared
 // memory a few tens.  Each walker therefore keeps a window of kRing table
 // rows around its E_Delta in shared memory (a ring indexed by row mod kRing),
-// re-centred between rows with cp.async; a group of four sites whose rows
-// might leave the window reads the global table instead (decided by a warp
-// vote, so the warp never diverges on it).
+// re-centred between rows with cp.async.  A row's chain reads only the window,
+// without asking whether a row is there, and records the lowest and highest
+// row it read; a walker whose row read outside the rows valid during it runs
+// the row again from the global table.
 //
-// P lanes of a warp serve one walker (walker slot t / P, lane h = t % P).
-// A row (fixed y, z) of L sites goes through these phases, staged in shared
-// memory:
+// Two kernel designs share these pieces.  In the lane kernels (below), P lanes
+// of a warp serve one walker (walker slot t / P, lane h = t % P) and do every
+// phase of a row themselves; the warp-specialised kernel (further below) gives
+// the chain a warp of its own and the other phases to helper warps.  In the
+// lane kernels a row (fixed y, z) of L sites goes through these phases, staged
+// in shared memory:
 //   1. cp.async (L2 -> shared) of the NEXT row's old spins and of its four y/z
 //      neighbour rows, and of the table rows that re-centre the window;
 //   2. the Philox blocks of the row, split over the P lanes;
@@ -29,8 +33,8 @@
 //      site x-1's move, and site x's own move;
 //   4. the chain, unrolled over the row: compare u with the threshold in
 //      flight, select the next site's address, issue its load, record the
-//      acceptance bit - nothing else depends on the previous step;
-//   5. the new spins of the row from the acceptance bits, and the energy
+//      new spin - nothing else depends on the previous step;
+//   5. the new spins of the row stored, and the energy
 //      tallies from byte dot products of old and new spins:
 //        dM = sum (N - O), dE_Delta = sum (N^2 - O^2),
 //        dE_J = -sum (N - O) H - sum_cyclic (N_x N_{x+1} - O_x O_{x+1}),
