@@ -344,7 +344,7 @@ def run_ours(args, rank, world, local_rank):
                          "unit": "Tops/s", "frac": achieved_ops / int_peak,
                          "traffic": traffic_per_launch(res, sweeps),
                          "kernel": {1: "sweep_global_kernel<false>", 2: "sweep_smem_kernel<false>",
-                                    3: "sweep_ws_kernel<false>"}.get(res, str(res)),
+                                    3: "sweep_ws_kernel<false, true>"}.get(res, str(res)),
                          "ops_per_attempt": ops_per_attempt,
                          "peak_source": f"152 SMs x 128 INT32 lanes x median SM clock "
                                         f"{sm_clock:.0f} MHz",

@@ -68,12 +68,15 @@ cudaError_t launch_sweeps(const GroupDev *groups_dev, const BlockDesc *blocks_de
                           cudaStream_t st);
 cudaError_t prepare_smem_kernel(size_t smem_bytes);
 cudaError_t prepare_global_kernel(size_t smem_bytes);
-// Warp-specialised launch (blocks of one chain warp and three helper warps;
-// BlockDesc.S walker slots, a power of 2 in [4, 32]).
+// Warp-specialised launch (blocks of one chain warp and helper warps;
+// BlockDesc.S walker slots, a power of 2 in [4, 32]).  Two instantiations:
+// rows of up to kWsNarrowMaxL sites (wide = false) and longer rows.
+constexpr int kWsNarrowMaxL = 32;
+constexpr int kKinds = 4;  // kernel kinds: lanes, shared tile, split narrow, split wide
 cudaError_t launch_sweeps_ws(const GroupDev *groups_dev, const BlockDesc *blocks_dev, int n_blocks,
                              size_t smem_bytes, uint32_t seed, uint64_t sweep0, int n_sweeps,
-                             int64_t ts_pos, bool record, cudaStream_t st);
-cudaError_t prepare_ws_kernel(size_t smem_bytes);
+                             int64_t ts_pos, bool record, bool wide, cudaStream_t st);
+cudaError_t prepare_ws_kernel(size_t smem_bytes, bool wide);
 size_t ws_bytes_for(int slots);
 // Bytes of one walker's lattice (padded rows), of a shared-memory tile, and of
 // the per-row staging area and table windows of `slots` walkers.

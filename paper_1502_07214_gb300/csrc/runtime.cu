@@ -60,9 +60,9 @@ struct muca_ctx {
     uint32_t seed = 0;
     int debug = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // one stream per kernel kind
+    cudaStream_t side[kKinds] = {};  // one stream per kernel kind
     cudaStream_t cap = nullptr;   // stream the iteration graph is captured on
-    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[kKinds] = {};
     uint64_t sweep = 0;
     int64_t ts_cap = 0, ts_len = 0;
     std::string err = "no error";
@@ -70,9 +70,9 @@ struct muca_ctx {
     GroupDev *d_groups = nullptr;
     // one launch per kernel kind in use: 0 lanes-per-walker (global lattice),
     // 1 shared-memory lattice, 2 split warps (global lattice)
-    BlockDesc *d_blocks[3] = {nullptr, nullptr, nullptr};
-    int n_blocks[3] = {0, 0, 0};
-    size_t smem[3] = {0, 0, 0};
+    BlockDesc *d_blocks[kKinds] = {};
+    int n_blocks[kKinds] = {};
+    size_t smem[kKinds] = {};
 };
 
 namespace {
@@ -225,17 +225,19 @@ int upload_groups(muca_ctx *ctx)
 // Kernel kind of a group's configuration.
 int kind_of(const Group &g)
 {
-    return g.residency == MUCA_RES_SMEM ? 1 : g.residency == MUCA_RES_SPLIT ? 2 : 0;
+    if (g.residency == MUCA_RES_SPLIT) return g.L > kWsNarrowMaxL ? 3 : 2;
+    return g.residency == MUCA_RES_SMEM ? 1 : 0;
 }
 
 // Block lists of the launches.  A block of group g serves wpb_g walkers:
 //   kind 0: one warp, P_g lanes per walker, staging area and table windows;
 //   kind 1: one warp, the walkers' lattices as a [L*L][Lw][wpb_g] tile too;
-//   kind 2: four warps (chain + helpers), wpb_g a power of 2 in [4, 32].
+//   kinds 2, 3: split kernel (chain warp + helpers), wpb_g a power of 2 in
+//   [4, 32]; kind 2 for rows of up to kWsNarrowMaxL sites, kind 3 above.
 int build_blocks(muca_ctx *ctx)
 {
-    std::vector<BlockDesc> b[3];
-    size_t sm[3] = {0, 0, 0};
+    std::vector<BlockDesc> b[kKinds];
+    size_t sm[kKinds] = {};
     for (size_t gi = 0; gi < ctx->g.size(); ++gi) {
         const Group &g = ctx->g[gi];
         const int k = kind_of(g);
@@ -249,18 +251,18 @@ int build_blocks(muca_ctx *ctx)
     // Longest blocks first: when a launch needs more than one wave of blocks,
     // the blocks of the largest lattices (work per sweep: walkers x sites)
     // start first instead of forming the tail.
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < kKinds; ++k)
         std::stable_sort(b[k].begin(), b[k].end(), [&](const BlockDesc &x, const BlockDesc &y) {
             return (int64_t)x.nw * ctx->g[x.group].V > (int64_t)y.nw * ctx->g[y.group].V;
         });
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kKinds; ++k) {
         if (sm[k] > 0 && (int64_t)sm[k] + 1024 > (int64_t)max_smem_per_block())
             return fail(ctx, MUCA_ERR_INVALID_ARG, "%zu bytes of shared memory per block do not fit",
                         sm[k]);
         if (!b[k].empty()) {
             if (k == 0) CK(prepare_global_kernel(sm[k]));
             if (k == 1) CK(prepare_smem_kernel(sm[k]));
-            if (k == 2) CK(prepare_ws_kernel(sm[k]));
+            if (k >= 2) CK(prepare_ws_kernel(sm[k], k == 3));
         }
         if (ctx->d_blocks[k]) cudaFree(ctx->d_blocks[k]);
         ctx->d_blocks[k] = nullptr;
@@ -280,16 +282,16 @@ int build_blocks(muca_ctx *ctx)
 int launch_all(muca_ctx *ctx, int n_sweeps, bool record, cudaStream_t st)
 {
     int used = 0;
-    for (int k = 0; k < 3; ++k) used += ctx->n_blocks[k] > 0;
+    for (int k = 0; k < kKinds; ++k) used += ctx->n_blocks[k] > 0;
     const bool fork = used > 1;
     if (fork) CK(cudaEventRecord(ctx->ev_fork, st));
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kKinds; ++k) {
         if (ctx->n_blocks[k] == 0) continue;
         cudaStream_t s = fork ? ctx->side[k] : st;
         if (fork) CK(cudaStreamWaitEvent(s, ctx->ev_fork, 0));
-        if (k == 2)
+        if (k >= 2)
             CK(launch_sweeps_ws(ctx->d_groups, ctx->d_blocks[k], ctx->n_blocks[k], ctx->smem[k],
-                                ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record, s));
+                                ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record, k == 3, s));
         else
             CK(launch_sweeps(ctx->d_groups, ctx->d_blocks[k], ctx->n_blocks[k], 32, ctx->smem[k],
                              k == 1, ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record, s));
@@ -623,7 +625,7 @@ void muca_destroy(muca_ctx *ctx)
     for (auto &g : ctx->g) free_group(g);
     cudaFree(ctx->d_err);
     cudaFree(ctx->d_groups);
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kKinds; ++k) {
         if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
         if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
         cudaFree(ctx->d_blocks[k]);
@@ -684,7 +686,7 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
         }                                                                                  \
     } while (0)
     {
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < kKinds; ++k) {
             CKI(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
             CKI(cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming));
         }

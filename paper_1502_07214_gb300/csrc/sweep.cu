@@ -679,6 +679,9 @@ constexpr int kWsThreads = 32 * kWsWarps;
 constexpr int kWsIdle = 4;
 constexpr int kWsHelp = kWsThreads - 64;  // helper threads
 constexpr int kWsSync = 32 + kWsHelp;     // threads of the ready / free barriers
+// words of a row per helper thread: Lw <= kMaxLw words over at least
+// kWsHelp / 32 helpers per walker slot
+constexpr int kWsItems = (kMaxLw + kWsHelp / 32 - 1) / (kWsHelp / 32);
 constexpr int kBarReady = 1, kBarFree = 3, kBarHelp = 5;
 // shared words per walker slot: window, descriptors and random words x2, the
 // packed-word buffers (O, H, N x3, staged rows x5, proposals x2), acceptance
@@ -955,6 +958,18 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
         const bool hact = hs < nw;
         const uint32_t key0 = g.walker0 + (uint32_t)(bd.w0 + hs);
         uint32_t *const hwin = sm.win(hs);
+        // CARRY (rows of up to 32 sites): the thread's words j = hj0 + t hstep
+        // (t < kWsItems) keep their old spins, proposals and neighbour sums in
+        // registers for the two rows in flight (c*: the row prepared last, p*:
+        // the row before) and pN the new spins of the row finished last; only
+        // neighbouring words are read from shared memory.  Without CARRY every
+        // word goes through shared memory (measured faster for L = 48, slower
+        // for L <= 32).
+        constexpr bool CARRY = L <= 32;
+        uint32_t cO[kWsItems], cS[kWsItems], cH[kWsItems];
+        uint32_t pO[kWsItems], pS[kWsItems], pH[kWsItems], pN[kWsItems];
+#pragma unroll
+        for (int t = 0; t < kWsItems; ++t) cO[t] = cS[t] = cH[t] = pO[t] = pS[t] = pH[t] = pN[t] = 0u;
         for (int k = 0; k < n_sweeps; ++k) {
             const uint64_t sw = sweep0 + (uint64_t)k;
             const uint32_t slo = (uint32_t)sw, shi = (uint32_t)(sw >> 32);
@@ -970,23 +985,48 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                     const int bj = jr % 3, bp = (jr + 2) % 3, ba = jr & 1;
                     if (hact) {
                         // new spins of word jj of row jr from its acceptance bits
-                        auto nword = [&](int jj) {
+                        auto nword = [&](int jj, uint32_t o, uint32_t sp) {
                             const uint32_t bits4 =
                                 (sm.ACC(ba, (4 * jj) >> 5, hs)[0] >> ((4 * jj) & 31)) & 15u;
-                            return new_word(sm.O(bj, jj)[hs], sm.SP(ba, jj)[hs], bits4);
+                            return new_word(o, sp, bits4);
                         };
-                        for (int j = hj0; j < Lw; j += hstep) {
-                            const uint32_t N0 = nword(j), O0 = sm.O(bj, j)[hs];
-                            sm.N(bj, j)[hs] = N0;
-                            const int j1 = (j + 1 == Lw) ? 0 : j + 1;
-                            const uint32_t n1 = __funnelshift_r(N0, nword(j1), 8);
-                            const uint32_t o1 = __funnelshift_r(O0, sm.O(bj, j1)[hs], 8);
-                            uint32_t Hw = sm.H(bj, j)[hs];
-                            if (nonwrap) Hw = __vadd4(Hw, sm.N(bp, j)[hs]);
-                            dJ -= __dp4a((int)__vsub4(N0, O0), (int)Hw, 0);
-                            dJ -= __dp4a((int)N0, (int)n1, 0) - __dp4a((int)O0, (int)o1, 0);
-                            dM += __dp4a((int)N0, 0x01010101, 0) - __dp4a((int)O0, 0x01010101, 0);
-                            lat[((ptrdiff_t)jr * Lw + j) * st + hs] = N0;
+                        if constexpr (CARRY) {
+#pragma unroll
+                            for (int t = 0; t < kWsItems; ++t) {
+                                const int j = hj0 + t * hstep;
+                                if (j >= Lw) break;
+                                const int j1 = (j + 1 == Lw) ? 0 : j + 1;
+                                const uint32_t O0 = pO[t], O1 = sm.O(bj, j1)[hs];
+                                const uint32_t N0 = nword(j, O0, pS[t]);
+                                const uint32_t n1 =
+                                    __funnelshift_r(N0, nword(j1, O1, sm.SP(ba, j1)[hs]), 8);
+                                const uint32_t o1 = __funnelshift_r(O0, O1, 8);
+                                const uint32_t Hw = nonwrap ? __vadd4(pH[t], pN[t]) : pH[t];
+                                dJ -= __dp4a((int)__vsub4(N0, O0), (int)Hw, 0);
+                                dJ -= __dp4a((int)N0, (int)n1, 0) - __dp4a((int)O0, (int)o1, 0);
+                                dM += __dp4a((int)N0, 0x01010101, 0) -
+                                      __dp4a((int)O0, 0x01010101, 0);
+                                lat[((ptrdiff_t)jr * Lw + j) * st + hs] = N0;
+                                pN[t] = N0;
+                            }
+                        } else {
+                            for (int j = hj0; j < Lw; j += hstep) {
+                                const uint32_t O0 = sm.O(bj, j)[hs];
+                                const uint32_t N0 = nword(j, O0, sm.SP(ba, j)[hs]);
+                                sm.N(bj, j)[hs] = N0;
+                                const int j1 = (j + 1 == Lw) ? 0 : j + 1;
+                                const uint32_t O1 = sm.O(bj, j1)[hs];
+                                const uint32_t n1 =
+                                    __funnelshift_r(N0, nword(j1, O1, sm.SP(ba, j1)[hs]), 8);
+                                const uint32_t o1 = __funnelshift_r(O0, O1, 8);
+                                uint32_t Hw = sm.H(bj, j)[hs];
+                                if (nonwrap) Hw = __vadd4(Hw, sm.N(bp, j)[hs]);
+                                dJ -= __dp4a((int)__vsub4(N0, O0), (int)Hw, 0);
+                                dJ -= __dp4a((int)N0, (int)n1, 0) - __dp4a((int)O0, (int)o1, 0);
+                                dM += __dp4a((int)N0, 0x01010101, 0) -
+                                      __dp4a((int)O0, 0x01010101, 0);
+                                lat[((ptrdiff_t)jr * Lw + j) * st + hs] = N0;
+                            }
                         }
                         // the table rows the chain asked for at the end of row jr
                         const int ra = sm.req(jr & 1, hs)[0], rb = sm.req(jr & 1, hs)[1];
@@ -999,6 +1039,15 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                     }
                     cp_async_commit();
                 }
+                if constexpr (CARRY) {
+                    // the row prepared last becomes the row before
+#pragma unroll
+                    for (int t = 0; t < kWsItems; ++t) {
+                        pO[t] = cO[t];
+                        pS[t] = cS[t];
+                        pH[t] = cH[t];
+                    }
+                }
                 if (i < R) {
                     // prepare row i
                     const bool wrap = (i % L == 0);
@@ -1006,14 +1055,24 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                     cp_async_wait_all();
                     bar_sync(kBarHelp, kWsHelp);
                     if (hact) {
-                        // old spins, neighbour sums, Philox words, proposals
-                        for (int j = hj0; j < Lw; j += hstep) {
+                        // old spins, neighbour sums, Philox words, proposals (the
+                        // words unrolled only with CARRY: for 48-site rows the
+                        // unrolled helpers slowed the chain down)
+#pragma unroll(CARRY ? kWsItems : 1)
+                        for (int t = 0; t < kWsItems; ++t) {
+                            const int j = hj0 + t * hstep;
+                            if (j >= Lw) break;
                             const uint32_t o = sm.pf(4, j)[hs];
                             uint32_t Hw =
                                 __vadd4(sm.pf(1, j)[hs], __vadd4(sm.pf(2, j)[hs], sm.pf(3, j)[hs]));
                             if (wrap) Hw = __vadd4(Hw, sm.pf(0, j)[hs]);
                             sm.O(bo, j)[hs] = o;
-                            sm.H(bo, j)[hs] = Hw;
+                            if constexpr (CARRY) {
+                                cO[t] = o;
+                                cH[t] = Hw;
+                            } else {
+                                sm.H(bo, j)[hs] = Hw;
+                            }
                             const uint4 v = philox4x32_10(
                                 make_uint4((uint32_t)(i * Lw + j), slo, shi, 0u), key0, seed);
                             sm.rnd(b, 4 * j)[hs] = v.x & 0x7FFFFFFFu;
@@ -1025,6 +1084,7 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                                 (((uint32_t)proposal(sbyte(o, 1), v.y) & 0xFFu) << 8) |
                                 (((uint32_t)proposal(sbyte(o, 2), v.z) & 0xFFu) << 16) |
                                 (((uint32_t)proposal(sbyte(o, 3), v.w) & 0xFFu) << 24);
+                            if constexpr (CARRY) cS[t] = spw;
                             sm.SP(b, j)[hs] = spw;
                         }
                     }
@@ -1033,16 +1093,32 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                         // descriptors of the four sites of each word
                         const int bq = (i + 2) % 3;  // row i-1: its old spins
                         const int s0 = sbyte(sm.O(bo, 0)[hs], 0), sp0 = sbyte(sm.SP(b, 0)[hs], 0);
-                        for (int j = hj0; j < Lw; j += hstep) {
+#pragma unroll(CARRY ? kWsItems : 1)
+                        for (int t = 0; t < kWsItems; ++t) {
+                            const int j = hj0 + t * hstep;
+                            if (j >= Lw) break;
                             const int jl = (j == 0) ? Lw - 1 : j - 1, jn = (j + 1 == Lw) ? 0 : j + 1;
-                            const uint32_t o = sm.O(bo, j)[hs], spw = sm.SP(b, j)[hs];
+                            uint32_t o, spw, Hw, yo = 0u, yp = 0u;
+                            if constexpr (CARRY) {
+                                o = cO[t];
+                                spw = cS[t];
+                                Hw = cH[t];
+                            } else {
+                                o = sm.O(bo, j)[hs];
+                                spw = sm.SP(b, j)[hs];
+                                Hw = sm.H(bo, j)[hs];
+                            }
                             const uint32_t ol = sm.O(bo, jl)[hs], spl = sm.SP(b, jl)[hs];
                             const uint32_t on = sm.O(bo, jn)[hs];
                             // neighbour sums with the old y-1 row; its changes: yo -> yp
-                            uint32_t Hw = sm.H(bo, j)[hs], yo = 0u, yp = 0u;
                             if (!wrap) {
-                                yo = sm.O(bq, j)[hs];
-                                yp = sm.SP(b ^ 1, j)[hs];
+                                if constexpr (CARRY) {
+                                    yo = pO[t];
+                                    yp = pS[t];
+                                } else {
+                                    yo = sm.O(bq, j)[hs];
+                                    yp = sm.SP(b ^ 1, j)[hs];
+                                }
                                 Hw = __vadd4(Hw, yo);
                             }
 #pragma unroll
@@ -1091,7 +1167,10 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
     }
 }
 
-template <bool RECORD>
+// WIDE: rows longer than kWsNarrowMaxL sites.  The two classes are separate
+// kernels: compiled together, the register-carrying helpers of the narrow
+// rows made the 48-site rows measurably slower.
+template <bool RECORD, bool WIDE>
 __global__ void __launch_bounds__(kWsThreads, 1)
 sweep_ws_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restrict__ blocks,
                 uint32_t seed, uint64_t sweep0, int n_sweeps, int64_t ts_pos)
@@ -1105,21 +1184,27 @@ sweep_ws_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restrict
         sm.tal(threadIdx.x)[1] = 0;
     }
     __syncthreads();
-    switch (g.L) {
 #define MUCA_WS(LL)                                                           \
     case LL: ws_sweeps<LL, RECORD>(g, bd, sm, seed, sweep0, n_sweeps, ts_pos); \
         break;
-        MUCA_WS(8)
-        MUCA_WS(12)
-        MUCA_WS(16)
-        MUCA_WS(20)
-        MUCA_WS(24)
-        MUCA_WS(28)
-        MUCA_WS(32)
-        MUCA_WS(48)
-#undef MUCA_WS
-        default: break;
+    if constexpr (WIDE) {
+        switch (g.L) {
+            MUCA_WS(48)
+            default: break;
+        }
+    } else {
+        switch (g.L) {
+            MUCA_WS(8)
+            MUCA_WS(12)
+            MUCA_WS(16)
+            MUCA_WS(20)
+            MUCA_WS(24)
+            MUCA_WS(28)
+            MUCA_WS(32)
+            default: break;
+        }
     }
+#undef MUCA_WS
 }
 
 // Initial spins i.i.d. uniform on {-1, 0, +1} from Philox stream 1; thread
@@ -1243,27 +1328,25 @@ cudaError_t prepare_global_kernel(size_t smem_bytes)
 
 size_t ws_bytes_for(int slots) { return (size_t)slots * kWsWords * sizeof(uint32_t); }
 
-cudaError_t prepare_ws_kernel(size_t smem_bytes)
+cudaError_t prepare_ws_kernel(size_t smem_bytes, bool wide)
 {
-    cudaError_t e = cudaFuncSetAttribute(sweep_ws_kernel<true>,
+    cudaError_t e = cudaFuncSetAttribute(wide ? sweep_ws_kernel<true, true> : sweep_ws_kernel<true, false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sweep_ws_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes);
+    return cudaFuncSetAttribute(wide ? sweep_ws_kernel<false, true> : sweep_ws_kernel<false, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 cudaError_t launch_sweeps_ws(const GroupDev *groups_dev, const BlockDesc *blocks_dev, int n_blocks,
                              size_t smem_bytes, uint32_t seed, uint64_t sweep0, int n_sweeps,
-                             int64_t ts_pos, bool record, cudaStream_t st)
+                             int64_t ts_pos, bool record, bool wide, cudaStream_t st)
 {
     if (n_blocks <= 0 || n_sweeps <= 0) return cudaSuccess;
-    if (record)
-        sweep_ws_kernel<true><<<n_blocks, kWsThreads, smem_bytes, st>>>(groups_dev, blocks_dev, seed,
-                                                                        sweep0, n_sweeps, ts_pos);
-    else
-        sweep_ws_kernel<false><<<n_blocks, kWsThreads, smem_bytes, st>>>(
-            groups_dev, blocks_dev, seed, sweep0, n_sweeps, ts_pos);
+    auto k = record ? (wide ? sweep_ws_kernel<true, true> : sweep_ws_kernel<true, false>)
+                    : (wide ? sweep_ws_kernel<false, true> : sweep_ws_kernel<false, false>);
+    k<<<n_blocks, kWsThreads, smem_bytes, st>>>(groups_dev, blocks_dev, seed, sweep0, n_sweeps,
+                                                ts_pos);
     return cudaGetLastError();
 }
 
