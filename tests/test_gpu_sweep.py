@@ -173,6 +173,30 @@ def test_generic_and_unrolled_sizes_in_one_launch(P):
         assert np.array_equal(got[g]["ts"], ref["ts"].transpose(1, 2, 0))
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_narrow_and_wide_split_kernels_in_one_context(use_graph):
+    """Split residency over rows of 8..32 sites (register-carry helpers) and of
+    48 sites (rolled helpers), plus a size the split kernel does not cover
+    (L = 5, lanes-per-walker kernel): three launches of one iteration, ragged
+    walker counts, plain and graph form."""
+    groups = [{"L": L, "T": T, "n_walkers": nw}
+              for L, T, nw in [(48, 0.9, 19), (8, 2.0, 40), (5, 1.0, 7), (32, 1.4182, 9),
+                               (12, 1.0, 33)]]
+    seed, n_iter, sweeps = 29, 2, 2
+    got = gpu_run(groups, seed, n_iter, sweeps, n_meas=2, use_graph=use_graph, residency=3)
+    for g, (spec, w0) in enumerate(zip(groups, walker_offsets(groups))):
+        assert got[g]["config"][0] == (3 if spec["L"] % 4 == 0 else 1), spec
+        ref = oracle.muca_run(spec["L"], spec["T"], spec["n_walkers"], seed, n_iter, sweeps,
+                              n_meas=2, walker_id0=w0)
+        if use_graph:
+            assert np.array_equal(got[g]["lnW"], ref["lnW"])
+            assert np.array_equal(got[g]["spins"], ref["spins"])
+            assert np.array_equal(got[g]["tallies"], ref["tallies"])
+        else:
+            compare_group(got[g], ref, n_iter)
+        assert np.array_equal(got[g]["ts"], ref["ts"].transpose(1, 2, 0))
+
+
 def test_medium_workload_reduced_bit_exact():
     """L=16, T=1.0, 1024 walkers, seed 1: 2 iterations x 8 sweeps + 4 measured."""
     s = wl.MEDIUM
