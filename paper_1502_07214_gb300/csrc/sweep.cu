@@ -665,7 +665,11 @@ sweep_smem_kernel(const GroupDev *__restrict__ groups, const BlockDesc *__restri
 // may trust only rows that are in both the previous and the new window.
 // Buffers: descriptors, random words, proposals, acceptance bits and window
 // requests double-buffered by row parity; old spins, neighbour sums and new
-// spins triple-buffered by row mod 3.  Named barriers: ready[b] (helpers arrive, chain waits), free[b]
+// spins triple-buffered by row mod 3.  Descriptors and random words keep the
+// four sites of a packed word together (16 bytes per walker slot), so a
+// helper writes a word's four with one store and the chain reads a row's
+// 2 L inputs with L / 2 loads: fewer shared-memory instructions beside the
+// chain's dependent loads made the 48-site sweep 6 % faster.  Named barriers: ready[b] (helpers arrive, chain waits), free[b]
 // (chain arrives, helpers wait), and one among the helpers.  Helper thread ht
 // serves walker slot ht mod G and the words j = ht / G, ht / G + kWsHelp / G, ...
 // of each row, so that its share of the energy changes belongs to one walker
@@ -703,8 +707,11 @@ struct WsSmem {
     int G;
     __device__ uint32_t *win(int slot) const { return base + (size_t)slot * kRingStride; }
     __device__ uint32_t *rest() const { return base + (size_t)G * kRingStride; }
-    __device__ uint32_t *desc(int b, int x) const { return rest() + ((b * kMaxL) + x) * G; }
-    __device__ uint32_t *rnd(int b, int x) const { return rest() + ((2 + b) * kMaxL + x) * G; }
+    // descriptors and random words of buffer b: site x of slot s at word
+    // (x / 4) 4G + 4 s + x % 4, so that the four sites of a packed word are
+    // one 16-byte unit (one store by a helper, one load by the chain)
+    __device__ uint32_t *descq(int b) const { return rest() + b * kMaxL * G; }
+    __device__ uint32_t *rndq(int b) const { return rest() + (2 + b) * kMaxL * G; }
     __device__ uint32_t *words(int k, int j) const
     {
         return rest() + 4 * kMaxL * G + (k * kMaxLw + j) * G;
@@ -772,9 +779,17 @@ __device__ __forceinline__ int ws_chain_fast(const uint32_t *dsc, const uint32_t
     constexpr int NB = (L + 31) / 32;
     uint32_t A[L], U[L];
 #pragma unroll
-    for (int x = 0; x < L; ++x) {
-        A[x] = dsc[x * stride];
-        U[x] = rn[x * stride];
+    for (int j = 0; j < L / 4; ++j) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(dsc + j * stride);
+        const uint4 u = *reinterpret_cast<const uint4 *>(rn + j * stride);
+        A[4 * j] = a.x;
+        A[4 * j + 1] = a.y;
+        A[4 * j + 2] = a.z;
+        A[4 * j + 3] = a.w;
+        U[4 * j] = u.x;
+        U[4 * j + 1] = u.y;
+        U[4 * j + 2] = u.z;
+        U[4 * j + 3] = u.w;
     }
 #pragma unroll
     for (int q = 0; q < NB; ++q) accb[q] = 0u;
@@ -820,11 +835,11 @@ __device__ __noinline__ int ws_chain_global(const uint32_t *dsc, const uint32_t 
     uint32_t bits = 0u;
 #pragma unroll 1
     for (int x = 0; x < L; ++x) {
-        const uint32_t a = dsc[x * stride];
+        const uint32_t a = dsc[(x >> 2) * stride + (x & 3)];
         int col = prev ? dw_colA(a) : dw_colR(a);
         if (pacc && ((pacc[(x >> 5) * G] >> (x & 31)) & 1u)) col += dw_q(a);
         if (x == L - 1) col += corr;
-        const bool acc = rn[x * stride] < __ldg(thrE + (ptrdiff_t)e * kRow + col);
+        const bool acc = rn[(x >> 2) * stride + (x & 3)] < __ldg(thrE + (ptrdiff_t)e * kRow + col);
         if (acc) {
             e += dw_d(a);
             bits |= 1u << (x & 31);
@@ -833,7 +848,7 @@ __device__ __noinline__ int ws_chain_global(const uint32_t *dsc, const uint32_t 
             accb[(x >> 5) * G] = bits;
             bits = 0u;
         }
-        if (x == 0) corr = acc ? dw_Q(dsc[(L - 1) * stride]) : 0;
+        if (x == 0) corr = acc ? dw_Q(dsc[((L - 1) >> 2) * stride + ((L - 1) & 3)]) : 0;
         prev = acc;
     }
     return e;
@@ -894,14 +909,14 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                     const int vlo = max(lo_a, lo_b), vhi = min(lo_a, lo_b) + kRing;
                     uint32_t accb[NB];
                     int lo, hi;
-                    const int ce = ws_chain_fast<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
+                    const int ce = ws_chain_fast<L>(sm.descq(b) + 4 * slot, sm.rndq(b) + 4 * slot, 4 * G,
                                                     pacc, e, win, accb, lo, hi);
                     if (lo >= vlo && hi < vhi) {
                         e = ce;
 #pragma unroll
                         for (int q = 0; q < NB; ++q) sm.ACC(b, q, slot)[0] = accb[q];
                     } else {
-                        e = ws_chain_global<L>(sm.desc(b, 0) + slot, sm.rnd(b, 0) + slot, G,
+                        e = ws_chain_global<L>(sm.descq(b) + 4 * slot, sm.rndq(b) + 4 * slot, 4 * G,
                                                sm.ACC(b ^ 1, 0, slot), e, thrE, sm.ACC(b, 0, slot),
                                                G);
 #pragma unroll
@@ -1075,10 +1090,9 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                             }
                             const uint4 v = philox4x32_10(
                                 make_uint4((uint32_t)(i * Lw + j), slo, shi, 0u), key0, seed);
-                            sm.rnd(b, 4 * j)[hs] = v.x & 0x7FFFFFFFu;
-                            sm.rnd(b, 4 * j + 1)[hs] = v.y & 0x7FFFFFFFu;
-                            sm.rnd(b, 4 * j + 2)[hs] = v.z & 0x7FFFFFFFu;
-                            sm.rnd(b, 4 * j + 3)[hs] = v.w & 0x7FFFFFFFu;
+                            *reinterpret_cast<uint4 *>(sm.rndq(b) + j * 4 * G + 4 * hs) =
+                                make_uint4(v.x & 0x7FFFFFFFu, v.y & 0x7FFFFFFFu, v.z & 0x7FFFFFFFu,
+                                           v.w & 0x7FFFFFFFu);
                             const uint32_t spw =
                                 ((uint32_t)proposal(sbyte(o, 0), v.x) & 0xFFu) |
                                 (((uint32_t)proposal(sbyte(o, 1), v.y) & 0xFFu) << 8) |
@@ -1121,6 +1135,7 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                                 }
                                 Hw = __vadd4(Hw, yo);
                             }
+                            uint32_t dq[4];
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
                                 const int s = sbyte(o, q), sp = sbyte(spw, q);
@@ -1141,11 +1156,13 @@ __device__ __forceinline__ void ws_sweeps(const GroupDev &g, const BlockDesc &bd
                                 }
                                 const int qy = -kk * (sbyte(yp, q) - sbyte(yo, q));
                                 const int qL = (4 * j + q == L - 1) ? -kk * (sp0 - s0) : 0;
-                                sm.desc(b, 4 * j + q)[hs] =
+                                dq[q] =
                                     (uint32_t)(c0 - kk * psp) | ((uint32_t)(c0 - kk * ps) << 6) |
                                     ((uint32_t)(d + 1) << 12) | ((uint32_t)(qy + 2) << 14) |
                                     ((uint32_t)(qL + 2) << 17);
                             }
+                            *reinterpret_cast<uint4 *>(sm.descq(b) + j * 4 * G + 4 * hs) =
+                                make_uint4(dq[0], dq[1], dq[2], dq[3]);
                         }
                     }
                     bar_arrive(kBarReady + b, kWsSync);
