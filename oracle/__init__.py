@@ -32,15 +32,19 @@ def lib():
         L.or_build_table.argtypes = [i32, dbl, i32, i32, P, P]
         L.or_sweeps.argtypes = [i32, i32, i32, P, u32, u32, u64, i32, P, P, P, P, i32]
         L.or_update_lnW.argtypes = [i32, P, P]
+        L.or_update_lnW_acc.argtypes = [i32, P, P, P]
         L.or_muca_run.argtypes = [i32, dbl, i32, i32, i32, u32, u32, i32, i32, i32,
                                   P, P, P, P, P, i32, i32]
+        L.or_muca_run_rec.argtypes = [i32, dbl, i32, i32, i32, u32, u32, i32, i32, i32,
+                                      P, P, P, P, P, i32, i32, i32, P]
         L.or_reweight.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
         L.or_reweight_q.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
         L.or_find_peak.argtypes = [P, P, i64, i32, P, i32, i32, dbl, dbl, dbl, i32, i32, i32, P]
         L.or_equal_height.argtypes = [P, i64, i32, P, i32, i32, dbl, i32, dbl, dbl, i32, i32,
                                       i32, P]
         for f in ("or_init_spins", "or_energies", "or_build_table", "or_sweeps",
-                  "or_update_lnW", "or_muca_run", "or_reweight", "or_reweight_q",
+                  "or_update_lnW", "or_update_lnW_acc", "or_muca_run", "or_muca_run_rec",
+                  "or_reweight", "or_reweight_q",
                   "or_find_peak", "or_equal_height"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
@@ -110,24 +114,50 @@ def update_lnW(H, lnW):
     _ck(lib().or_update_lnW(len(H), _p(H), _p(lnW)), "update_lnW")
 
 
+def update_lnW_acc(H, lnW, acc):
+    """The accumulated, error-weighted recursion (reading R13 of muca_oracle.c);
+    lnW[nE] and the pair weights acc[nE - 1] are updated in place."""
+    H = np.ascontiguousarray(H, dtype=np.uint64)
+    assert lnW.dtype == np.float64 and lnW.flags.c_contiguous
+    assert acc.dtype == np.float64 and acc.flags.c_contiguous and len(acc) == max(len(H) - 1, 1)
+    _ck(lib().or_update_lnW_acc(len(H), _p(H), _p(lnW), _p(acc)), "update_lnW_acc")
+
+
+def flatness(H):
+    """Flatness of a merged histogram over its window: (min H / mean H,
+    max H / mean H, bins with H > 0); mean = sum / bins; zeros if H is empty."""
+    H = np.asarray(H, dtype=np.uint64)
+    total = int(H.sum())
+    if total == 0:
+        return np.zeros(3)
+    mean = float(total) / len(H)
+    return np.array([float(H.min()) / mean, float(H.max()) / mean, float((H > 0).sum())])
+
+
 def muca_run(L, T, n_walkers, seed, n_iter, sweeps_per_iter, n_meas=0, e_min=0, e_max=None,
-             walker_id0=0, lnW=None, check=False, n_threads=None, want_spins=True):
-    """A whole run of one (L, T) group; returns a dict of numpy arrays."""
+             walker_id0=0, lnW=None, check=False, n_threads=None, want_spins=True, recursion=0,
+             acc=None):
+    """A whole run of one (L, T) group; returns a dict of numpy arrays.
+    recursion 0: lnW -= ln H; 1: the accumulated recursion, whose pair
+    weights start from acc (zeros by default) and are returned as "acc"."""
     V = L ** 3
     if e_max is None:
         e_max = V
     nE = e_max - e_min + 1
     lnW = np.zeros(nE) if lnW is None else np.array(lnW, dtype=np.float64, copy=True)
+    acc = np.zeros(max(nE - 1, 1)) if acc is None else np.array(acc, dtype=np.float64, copy=True)
     hist = np.zeros((max(n_iter, 1), nE), dtype=np.uint64)
     spins = np.zeros((n_walkers, V), dtype=np.int8) if want_spins else None
     tal = np.zeros((n_walkers, 3), dtype=np.int32)
     ts = np.zeros((n_walkers, n_meas, 3), dtype=np.int32) if n_meas > 0 else None
     if n_threads is None:
         n_threads = os.cpu_count() or 1
-    _ck(lib().or_muca_run(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
-                          sweeps_per_iter, n_meas, _p(lnW), _p(hist), _p(spins), _p(tal),
-                          _p(ts), int(check), n_threads), "muca_run")
-    return {"lnW": lnW, "hist": hist[:n_iter], "spins": spins, "tallies": tal, "ts": ts}
+    _ck(lib().or_muca_run_rec(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
+                              sweeps_per_iter, n_meas, _p(lnW), _p(hist), _p(spins), _p(tal),
+                              _p(ts), int(check), n_threads, int(recursion), _p(acc)),
+        "muca_run")
+    return {"lnW": lnW, "hist": hist[:n_iter], "spins": spins, "tallies": tal, "ts": ts,
+            "acc": acc}
 
 
 def _rw(fn, e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads):

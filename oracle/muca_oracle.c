@@ -47,6 +47,8 @@
  *   R8 chi = beta V (<m^2> - <|m|>^2) and U4 = 1 - <m^4>/(3 <m^2>^2), m = M/V
  *      (the paper names chi without defining it and does not use U4).
  *   R9, R10 (rounding of the reweighting) are stated where they are used.
+ *   R13 the accumulated, error-weighted form of the weight recursion and its
+ *       rule for empty bins are stated at or_update_lnW_acc.
  */
 #include "muca_oracle.h"
 
@@ -263,6 +265,49 @@ int or_update_lnW(int nE, const uint64_t *H, double *lnW)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Accumulated, error-weighted weight recursion (reading R13).  Sec. II      */
+/* adapts W iteratively by the recursion of the multicanonical method that   */
+/* it cites (Berg and Neuhaus; Janke); this is that recursion's accumulated  */
+/* form, restated from its published definition.  Iteration n estimates the  */
+/* ratio of neighbouring weights r(E) = lnW(E+1) - lnW(E) from its histogram */
+/* H, and the estimates of all iterations so far are averaged with weights   */
+/* equal to their inverse variances:                                         */
+/*   est(E) = r(E) + ln H(E) - ln H(E+1)      this iteration's estimate       */
+/*   p(E)   = H(E) H(E+1) / (H(E) + H(E+1))   1 / variance of est(E)          */
+/*   acc(E) <- acc(E) + p(E)                  accumulated weight              */
+/*   r(E)   <- r(E) + (p(E) / acc(E)) (ln H(E) - ln H(E+1))                   */
+/* so r stays the p-weighted mean of every estimate so far.  An iteration    */
+/* with H(E) = 0 or H(E+1) = 0 gives no estimate for the pair.  A pair that  */
+/* has never had one (acc(E) = 0) takes the plain recursion's step instead,  */
+/* with an empty bin counted as 1: r(E) += ln max(H(E), 1) - ln max(H(E+1), 1) */
+/* (then the weights still push into unvisited bins as lnW -= ln H does).    */
+/* lnW at the first bin of the window is kept and lnW(E+1) = lnW(E) + r(E).  */
+/* acc has nE - 1 entries (one per neighbouring pair), zero at the start.    */
+/* ------------------------------------------------------------------------ */
+int or_update_lnW_acc(int nE, const uint64_t *H, double *lnW, double *acc)
+{
+    if (nE <= 0 || !H || !lnW || (nE > 1 && !acc)) return OR_ERR_ARG;
+    if (nE == 1) return OR_OK;
+    double *r = (double *)malloc((size_t)(nE - 1) * sizeof(double));
+    if (!r) return OR_ERR_NOMEM;
+    for (int e = 0; e + 1 < nE; ++e) {
+        const double h0 = (double)H[e], h1 = (double)H[e + 1];
+        double re = lnW[e + 1] - lnW[e];
+        if (H[e] > 0 && H[e + 1] > 0) {
+            const double p = h0 * h1 / (h0 + h1);
+            acc[e] = acc[e] + p;
+            re = re + (p / acc[e]) * (log(h0) - log(h1));
+        } else if (acc[e] == 0.0) {
+            re = re + (log(h0 > 1.0 ? h0 : 1.0) - log(h1 > 1.0 ? h1 : 1.0));
+        }
+        r[e] = re;
+    }
+    for (int e = 0; e + 1 < nE; ++e) lnW[e + 1] = lnW[e] + r[e];
+    free(r);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* A whole run of one group: walkers are independent given the table, so the */
 /* walkers of an iteration are split over threads; histograms are summed.    */
 /* ------------------------------------------------------------------------ */
@@ -337,8 +382,19 @@ int or_muca_run(int L, double T, int n_walkers, int e_min, int e_max, uint32_t s
                 double *lnW, uint64_t *hist_iter, int8_t *spins_out,
                 int32_t *tallies_out, int32_t *ts, int check, int n_threads)
 {
+    return or_muca_run_rec(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
+                           sweeps_per_iter, n_meas, lnW, hist_iter, spins_out, tallies_out, ts,
+                           check, n_threads, 0, NULL);
+}
+
+int or_muca_run_rec(int L, double T, int n_walkers, int e_min, int e_max, uint32_t seed,
+                    uint32_t walker_id0, int n_iter, int sweeps_per_iter, int n_meas,
+                    double *lnW, uint64_t *hist_iter, int8_t *spins_out,
+                    int32_t *tallies_out, int32_t *ts, int check, int n_threads,
+                    int recursion, double *acc)
+{
     if (L < 2 || !(T > 0.0) || n_walkers < 1 || n_iter < 0 || sweeps_per_iter < 0 ||
-        n_meas < 0 || !lnW)
+        n_meas < 0 || !lnW || recursion < 0 || recursion > 1 || (recursion == 1 && !acc))
         return OR_ERR_ARG;
     int64_t V = (int64_t)L * L * L;
     if (e_min < 0 || e_max > V || e_min > e_max) return OR_ERR_ARG;
@@ -387,7 +443,12 @@ int or_muca_run(int L, double T, int n_walkers, int e_min, int e_max, uint32_t s
         if (rc != OR_OK) goto done;
         sweep += (uint64_t)sweeps_per_iter;
         if (hist_iter) memcpy(hist_iter + (size_t)it * nE, hist, (size_t)nE * sizeof(uint64_t));
-        or_update_lnW(nE, hist, lnW);
+        if (recursion == 1) {
+            rc = or_update_lnW_acc(nE, hist, lnW, acc);
+            if (rc != OR_OK) goto done;
+        } else {
+            or_update_lnW(nE, hist, lnW);
+        }
         or_build_table(L, T, e_min, e_max, lnW, thr);
     }
     if (n_meas > 0) {

@@ -62,6 +62,11 @@ int or_sweeps(int L, int e_min, int e_max, const uint32_t *thr, uint32_t seed,
 /* Weight recursion: lnW[E] -= ln H[E] wherever H[E] > 0. */
 int or_update_lnW(int nE, const uint64_t *H, double *lnW);
 
+/* Accumulated, error-weighted weight recursion (reading R13 in the .c file):
+ * acc[nE - 1] holds the accumulated pair weights (zero before the first
+ * iteration) and is updated with lnW. */
+int or_update_lnW_acc(int nE, const uint64_t *H, double *lnW, double *acc);
+
 /* A whole parallel MUCA run of one (L, T) group (init, n_iter weight
  * iterations of sweeps_per_iter sweeps with merge + update + table rebuild,
  * then n_meas measurement sweeps under the final weights).
@@ -76,6 +81,15 @@ int or_muca_run(int L, double T, int n_walkers, int e_min, int e_max, uint32_t s
                 uint32_t walker_id0, int n_iter, int sweeps_per_iter, int n_meas,
                 double *lnW, uint64_t *hist_iter, int8_t *spins_out,
                 int32_t *tallies_out, int32_t *ts, int check, int n_threads);
+
+/* The same run with a choice of weight recursion: 0 the plain one
+ * (or_update_lnW), 1 the accumulated one (or_update_lnW_acc, with its pair
+ * weights in acc[nE - 1], in/out). */
+int or_muca_run_rec(int L, double T, int n_walkers, int e_min, int e_max, uint32_t seed,
+                    uint32_t walker_id0, int n_iter, int sweeps_per_iter, int n_meas,
+                    double *lnW, uint64_t *hist_iter, int8_t *spins_out,
+                    int32_t *tallies_out, int32_t *ts, int check, int n_threads,
+                    int recursion, double *acc);
 
 /* Time-series reweighting (Eq. 3) to each Delta_k of grid[n_grid], FP64 with
  * compensated sums.  Samples: e_j[n], e_d[n], m[n].  lnW[nE] indexed by
