@@ -276,11 +276,14 @@ int or_update_lnW(int nE, const uint64_t *H, double *lnW)
 /*   p(E)   = H(E) H(E+1) / (H(E) + H(E+1))   1 / variance of est(E)          */
 /*   acc(E) <- acc(E) + p(E)                  accumulated weight              */
 /*   r(E)   <- r(E) + (p(E) / acc(E)) (ln H(E) - ln H(E+1))                   */
-/* so r stays the p-weighted mean of every estimate so far.  An iteration    */
-/* with H(E) = 0 or H(E+1) = 0 gives no estimate for the pair.  A pair that  */
-/* has never had one (acc(E) = 0) takes the plain recursion's step instead,  */
-/* with an empty bin counted as 1: r(E) += ln max(H(E), 1) - ln max(H(E+1), 1) */
-/* (then the weights still push into unvisited bins as lnW -= ln H does).    */
+/* so r stays the p-weighted mean of every estimate so far, taken over the  */
+/* iterations that hit both bins of the pair.  A pair with an empty bin      */
+/* takes the plain recursion's step instead, with the empty bin counted as 1 */
+/* (r(E) += ln max(H(E), 1) - ln max(H(E+1), 1), what lnW -= ln H for H > 0  */
+/* does to the ratio), and adds nothing to acc: the weights keep pushing     */
+/* into unvisited bins as fast as the plain recursion, no pseudo-count       */
+/* dilutes the first real estimates there, and the first iteration           */
+/* (acc = 0) is exactly the plain step.                                       */
 /* lnW at the first bin of the window is kept and lnW(E+1) = lnW(E) + r(E).  */
 /* acc has nE - 1 entries (one per neighbouring pair), zero at the start.    */
 /* ------------------------------------------------------------------------ */
@@ -297,7 +300,7 @@ int or_update_lnW_acc(int nE, const uint64_t *H, double *lnW, double *acc)
             const double p = h0 * h1 / (h0 + h1);
             acc[e] = acc[e] + p;
             re = re + (p / acc[e]) * (log(h0) - log(h1));
-        } else if (acc[e] == 0.0) {
+        } else {
             re = re + (log(h0 > 1.0 ? h0 : 1.0) - log(h1 > 1.0 ? h1 : 1.0));
         }
         r[e] = re;

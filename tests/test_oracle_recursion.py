@@ -73,9 +73,8 @@ def test_ratios_are_the_weighted_mean_of_the_estimates():
 
 
 def test_empty_bins():
-    """A pair without any estimate so far takes the plain step with empty bins
-    counted as 1; a pair with earlier estimates keeps its ratio when this
-    iteration leaves one of its bins empty."""
+    """A pair with an empty bin takes the plain step (the empty bin counted as
+    1) and adds nothing to its accumulated weight, whatever that weight is."""
     lnW = np.array([0.0, 0.3, -0.2, 0.5, 1.0, 0.7])
     acc = np.array([0.0, 0.0, 0.0, 4.0, 4.0])
     H = np.array([8, 0, 0, 5, 0, 3], dtype=np.uint64)
@@ -87,9 +86,24 @@ def test_empty_bins():
     assert abs(r[0] - (r0[0] + np.log(8.0))) < 1e-14      # frontier: plain step
     assert abs(r[1] - r0[1]) < 1e-14                      # both empty: unchanged
     assert abs(r[2] - (r0[2] - np.log(5.0))) < 1e-14      # frontier: plain step
-    assert abs(r[3] - r0[3]) < 1e-14 and abs(r[4] - r0[4]) < 1e-14  # earlier estimates kept
+    assert abs(r[3] - (r0[3] + np.log(5.0))) < 1e-14      # with earlier estimates too
+    assert abs(r[4] - (r0[4] - np.log(3.0))) < 1e-14
     np.testing.assert_array_equal(a, acc)
     assert got[0] == lnW[0]
+
+
+def test_accumulated_recursion_reaches_a_steadier_flat_histogram_l4():
+    """L = 4: both recursions reach min H / mean H >= 0.5 within 40
+    iterations from lnW = 0; over the last five iterations the accumulated one,
+    which averages the estimates instead of following the last histogram, keeps
+    the histogram flatter and steadier."""
+    tail = {}
+    for rec in (0, 1):
+        out = oracle.muca_run(4, 1.4182, 64, 21, 40, 100, recursion=rec, want_spins=False)
+        f = np.array([oracle.flatness(h)[0] for h in out["hist"]])
+        assert (f >= 0.5).any()
+        tail[rec] = f[-5:]
+    assert tail[1].min() > tail[0].min() and tail[1].std() < tail[0].std(), tail
 
 
 def exact_target(L, T):
