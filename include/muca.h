@@ -130,9 +130,11 @@ int muca_sync(muca_ctx *ctx);
 int muca_sweep_iter(muca_ctx *ctx, int n_sweeps, int record);
 
 /* The merge and weight update of one MUCA iteration for every group (Sec. II):
- * the merged histogram H is read back, lnW[E] -= ln H[E] wherever H[E] > 0 (in
- * FP64 on the host), the threshold table is rebuilt in FP64 and uploaded, and
- * H is cleared.  Synchronises the stream. */
+ * the merged histogram H is read back, lnW is updated in FP64 on the host by
+ * the context's weight recursion (muca_set_recursion; by default
+ * lnW[E] -= ln H[E] wherever H[E] > 0), the flatness of H is recorded
+ * (muca_get_flatness), the threshold table is rebuilt in FP64 and uploaded,
+ * and H is cleared.  Synchronises the stream. */
 int muca_merge_update(muca_ctx *ctx);
 
 /* The batched form: n_iters x (sweeps_per_iter sweeps of all groups in one
@@ -141,6 +143,56 @@ int muca_merge_update(muca_ctx *ctx);
  * to calling muca_sweep_iter + muca_merge_update n_iters times.
  * Synchronises the stream. */
 int muca_run_graph(muca_ctx *ctx, int n_iters, int sweeps_per_iter);
+
+/* ------------------------------------------------ weight-iteration variants */
+
+/* Weight recursions.  Sec. II adapts W iteratively by the recursion of the
+ * multicanonical method it cites (Berg and Neuhaus; Janke) without printing
+ * it.  With r(E) = lnW[E+1] - lnW[E] the ratio of neighbouring weights:
+ *   MUCA_REC_PLAIN        lnW[E] -= ln H[E] wherever H[E] > 0 (the default).
+ *   MUCA_REC_ACCUMULATED  the accumulated, error-weighted form: every
+ *       iteration estimates r(E) as r(E) + ln H[E] - ln H[E+1] with inverse
+ *       variance p(E) = H[E] H[E+1] / (H[E] + H[E+1]); then acc(E) += p(E) and
+ *       r(E) += (p(E) / acc(E)) (ln H[E] - ln H[E+1]), which keeps r(E) the
+ *       p-weighted mean of the estimates of every iteration that hit both
+ *       bins.  In an iteration with H[E] = 0 or H[E+1] = 0 the pair takes the
+ *       plain step instead (the empty bin counted as 1, which is what the
+ *       plain recursion does to the ratio) and acc(E) is unchanged.  lnW[0]
+ *       is kept and lnW[E+1] = lnW[E] + r(E). */
+#define MUCA_REC_PLAIN 0
+#define MUCA_REC_ACCUMULATED 1
+
+/* One weight update on the host; no device work, no context (the merge of
+ * muca_merge_update and muca_run_graph runs this same function).
+ *   kind   MUCA_REC_PLAIN or MUCA_REC_ACCUMULATED
+ *   hist   host uint64 [n_e]: the merged histogram of the iteration
+ *   lnW    host FP64 [n_e], updated in place
+ *   acc    host FP64 [n_e - 1]: the accumulated pair weights, updated in place
+ *          (zeros before the first iteration); unused, and may be NULL, for
+ *          MUCA_REC_PLAIN or n_e == 1
+ * MUCA_ERR_INVALID_ARG for an unknown kind, n_e < 1 or a missing array. */
+int muca_weight_update(int32_t kind, int32_t n_e, const uint64_t *hist, double *lnW,
+                       double *acc);
+
+/* Select the weight recursion of every group of ctx (MUCA_REC_*) and clear
+ * the accumulated pair weights (muca_set_lnW clears a group's as well). */
+int muca_set_recursion(muca_ctx *ctx, int32_t kind);
+
+/* Flatness of the histogram H merged by the last weight update of group g
+ * (muca_merge_update, muca_run_graph or muca_iterate) over its n_e bins:
+ * out host FP64 [3] = (min H / mean H, max H / mean H, number of bins with
+ * H > 0), mean H = (sum H) / n_e; zeros before the first update or when H
+ * was empty. */
+int muca_get_flatness(muca_ctx *ctx, int group, double *out);
+
+/* Weight iteration until the histograms are flat: up to max_iters iterations
+ * of sweeps_per_iter sweeps followed by muca_merge_update; stops after the
+ * first iteration at which min H / mean H >= flat_min for every group.
+ * *n_done receives the number of iterations run (host int32; max_iters if the
+ * histograms never became flat, which is not an error).  Synchronises the
+ * stream. */
+int muca_iterate(muca_ctx *ctx, int32_t max_iters, int32_t sweeps_per_iter, double flat_min,
+                 int32_t *n_done);
 
 /* Time-series reweighting (Eq. 3) of n = n_rows x row_len samples to every
  * Delta_k of delta_grid, with C from Eq. 6.
@@ -260,7 +312,8 @@ int muca_get_timeseries(muca_ctx *ctx, int group, int32_t *out);
 /* Number of sweeps done so far by group g (the next sweep's Philox index). */
 int muca_get_sweep_count(muca_ctx *ctx, int group, uint64_t *out);
 
-/* lnW of group g, host FP64 [n_e]. set replaces it and rebuilds the table. */
+/* lnW of group g, host FP64 [n_e]. set replaces it, clears the accumulated
+ * pair weights of the weight recursion and rebuilds the table. */
 int muca_get_lnW(muca_ctx *ctx, int group, double *out);
 int muca_set_lnW(muca_ctx *ctx, int group, const double *in);
 
@@ -292,9 +345,12 @@ int muca_check_tallies(muca_ctx *ctx);
 int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walkers_per_block,
                     int32_t *lanes_per_walker);
 
-/* Checkpoint / restore: spins, tallies, lnW, histograms, sweep counters and
- * the seed, to / from a file.  Philox is counter-based, so a restored run
- * continues bit-identically.  restore requires a context with the same groups. */
+/* Checkpoint / restore: spins, tallies, lnW, histograms, the weight
+ * recursion with its accumulated pair weights, sweep counters and the seed,
+ * to / from a file.  Philox is counter-based, so a restored run continues
+ * bit-identically.  restore requires a context with the same groups; it also
+ * reads files of the earlier format without the recursion (plain recursion,
+ * no accumulated weights). */
 int muca_checkpoint(muca_ctx *ctx, const char *path);
 int muca_restore(muca_ctx *ctx, const char *path);
 

@@ -37,6 +37,9 @@ struct Group {
     int32_t *ts = nullptr;
     // host
     std::vector<double> lnW;
+    int recursion = MUCA_REC_PLAIN;  // weight recursion (muca_set_recursion)
+    std::vector<double> acc;         // its accumulated pair weights, max(nE - 1, 1)
+    double flat[3] = {0.0, 0.0, 0.0};  // flatness of the histogram of the last update
     std::vector<uint32_t> injected;  // logical table given by muca_set_table (empty if none)
     uint32_t *h_thr = nullptr;       // pinned copy of the table allocation
     unsigned long long *h_hist = nullptr;  // pinned [nE]
@@ -188,11 +191,60 @@ int upload_table(muca_ctx *ctx, Group &g)
     return MUCA_OK;
 }
 
-// The weight recursion of one iteration: lnW[E] -= ln H[E] where H[E] > 0.
+// One weight update (muca_weight_update).  Plain: lnW[E] -= ln H[E] where
+// H[E] > 0.  Accumulated: the ratio r(E) = lnW[E+1] - lnW[E] of every pair
+// with both bins hit moves by (p / acc) (ln H[E] - ln H[E+1]), p = H[E] H[E+1]
+// / (H[E] + H[E+1]) added to acc first, which keeps r the inverse-variance
+// mean of the estimates of every iteration that hit both bins; a pair with an
+// empty bin takes the plain step (the empty bin counted as 1) and adds
+// nothing to acc; lnW[0] stays and the weights are summed up from the new
+// ratios.
+void weight_update(int kind, int nE, const unsigned long long *H, double *lnW, double *acc)
+{
+    if (kind == MUCA_REC_PLAIN) {
+        for (int e = 0; e < nE; ++e)
+            if (H[e] > 0) lnW[e] -= std::log((double)H[e]);
+        return;
+    }
+    if (nE < 2) return;
+    std::vector<double> r((size_t)nE - 1);
+    for (int e = 0; e + 1 < nE; ++e) {
+        const double h0 = (double)H[e], h1 = (double)H[e + 1];
+        double re = lnW[e + 1] - lnW[e];
+        if (H[e] > 0 && H[e + 1] > 0) {
+            const double p = h0 * h1 / (h0 + h1);
+            acc[e] = acc[e] + p;
+            re = re + (p / acc[e]) * (std::log(h0) - std::log(h1));
+        } else {
+            re = re + (std::log(h0 > 1.0 ? h0 : 1.0) - std::log(h1 > 1.0 ? h1 : 1.0));
+        }
+        r[e] = re;
+    }
+    for (int e = 0; e + 1 < nE; ++e) lnW[e + 1] = lnW[e] + r[e];
+}
+
+// The weight update of one iteration of group g on its merged histogram,
+// after recording the histogram's flatness.
 void update_lnW(Group &g)
 {
-    for (int e = 0; e < g.nE; ++e)
-        if (g.h_hist[e] > 0) g.lnW[e] -= std::log((double)g.h_hist[e]);
+    unsigned long long lo = ~0ull, hi = 0, sum = 0;
+    int64_t hit = 0;
+    for (int e = 0; e < g.nE; ++e) {
+        const unsigned long long h = g.h_hist[e];
+        lo = std::min(lo, h);
+        hi = std::max(hi, h);
+        sum += h;
+        hit += h > 0;
+    }
+    if (sum == 0) {
+        g.flat[0] = g.flat[1] = g.flat[2] = 0.0;
+    } else {
+        const double mean = (double)sum / g.nE;
+        g.flat[0] = (double)lo / mean;
+        g.flat[1] = (double)hi / mean;
+        g.flat[2] = (double)hit;
+    }
+    weight_update(g.recursion, g.nE, g.h_hist, g.lnW.data(), g.acc.data());
 }
 
 GroupDev dev_of(const Group &g)
@@ -713,6 +765,7 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
             g.walker0 = w0;
             w0 += (uint32_t)g.W;
             g.lnW.assign(g.nE, 0.0);
+            g.acc.assign((size_t)std::max(g.nE - 1, 1), 0.0);
             const size_t sbytes = (size_t)g.L * g.L * g.Lw * g.Wpad * sizeof(uint32_t);
             CKI(cudaMalloc(&g.spins, sbytes));
             CKI(cudaMemsetAsync(g.spins, 0, sbytes, ctx->stream));
@@ -807,6 +860,64 @@ int muca_merge_update(muca_ctx *ctx)
         CK(cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long), ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_weight_update(int32_t kind, int32_t n_e, const uint64_t *hist, double *lnW, double *acc)
+{
+    if (kind != MUCA_REC_PLAIN && kind != MUCA_REC_ACCUMULATED)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "unknown weight recursion %d", kind);
+    if (n_e < 1 || !hist || !lnW || (kind == MUCA_REC_ACCUMULATED && n_e > 1 && !acc))
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "weight update: n_e < 1 or a NULL array");
+    static_assert(sizeof(uint64_t) == sizeof(unsigned long long), "64-bit histogram counts");
+    weight_update(kind, n_e, reinterpret_cast<const unsigned long long *>(hist), lnW, acc);
+    return MUCA_OK;
+}
+
+int muca_set_recursion(muca_ctx *ctx, int32_t kind)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    if (kind != MUCA_REC_PLAIN && kind != MUCA_REC_ACCUMULATED)
+        return fail(ctx, MUCA_ERR_INVALID_ARG, "unknown weight recursion %d", kind);
+    CK(cudaStreamSynchronize(ctx->stream));  // a graph's host node may still update
+    for (auto &g : ctx->g) {
+        g.recursion = kind;
+        std::fill(g.acc.begin(), g.acc.end(), 0.0);
+    }
+    return MUCA_OK;
+}
+
+int muca_get_flatness(muca_ctx *ctx, int group, double *out)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!out) return fail(ctx, MUCA_ERR_INVALID_ARG, "out is NULL");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const Group &g = ctx->g[group];
+    for (int k = 0; k < 3; ++k) out[k] = g.flat[k];
+    return MUCA_OK;
+}
+
+int muca_iterate(muca_ctx *ctx, int32_t max_iters, int32_t sweeps_per_iter, double flat_min,
+                 int32_t *n_done)
+{
+    if (!ctx) return fail(nullptr, MUCA_ERR_INVALID_ARG, "null context");
+    if (!n_done) return fail(ctx, MUCA_ERR_INVALID_ARG, "n_done is NULL");
+    *n_done = 0;
+    if (max_iters < 0 || sweeps_per_iter < 1 || !std::isfinite(flat_min))
+        return fail(ctx, MUCA_ERR_INVALID_ARG,
+                    "iterate: max_iters %d, sweeps_per_iter %d, flat_min %g", max_iters,
+                    sweeps_per_iter, flat_min);
+    for (int it = 0; it < max_iters; ++it) {
+        int rc = muca_sweep_iter(ctx, sweeps_per_iter, 0);
+        if (rc != MUCA_OK) return rc;
+        rc = muca_merge_update(ctx);
+        if (rc != MUCA_OK) return rc;
+        *n_done = it + 1;
+        bool flat = true;
+        for (const auto &g : ctx->g) flat = flat && g.flat[0] >= flat_min;
+        if (flat) break;
+    }
     return MUCA_OK;
 }
 
@@ -955,6 +1066,7 @@ int muca_set_lnW(muca_ctx *ctx, int group, const double *in)
         if (!std::isfinite(in[e])) return fail(ctx, MUCA_ERR_INVALID_ARG, "lnW[%d] not finite", e);
     CK(cudaStreamSynchronize(ctx->stream));  // the pinned table may still be in flight
     std::memcpy(g.lnW.data(), in, g.nE * sizeof(double));
+    std::fill(g.acc.begin(), g.acc.end(), 0.0);
     g.injected.clear();
     build_packed(g);
     rc = upload_table(ctx, g);
@@ -1115,9 +1227,12 @@ int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walke
     return MUCA_OK;
 }
 
-// Checkpoint file: magic, version, seed, sweep, n_groups, per group the spec,
-// then per group lnW[nE], hist[nE], tallies[3][Wpad], spins[V][Wpad].
-static const char kMagic[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '1'};
+// Checkpoint file: magic with the format version, seed, sweep, n_groups, per
+// group the spec, per group the weight recursion (int32), then per group
+// lnW[nE], acc[max(nE - 1, 1)], hist[nE], tallies[3][Wpad], spins[V][Wpad].
+// Format 01 (still read) has neither the recursion nor acc.
+static const char kMagic[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '2'};
+static const char kMagic01[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '1'};
 
 int muca_checkpoint(muca_ctx *ctx, const char *path)
 {
@@ -1133,6 +1248,10 @@ int muca_checkpoint(muca_ctx *ctx, const char *path)
     ok = ok && std::fwrite(&ng, sizeof ng, 1, f) == 1;
     for (auto &g : ctx->g) ok = ok && std::fwrite(&g.spec, sizeof g.spec, 1, f) == 1;
     for (auto &g : ctx->g) {
+        const int32_t rec = g.recursion;
+        ok = ok && std::fwrite(&rec, sizeof rec, 1, f) == 1;
+    }
+    for (auto &g : ctx->g) {
         if (!ok) break;
         std::vector<unsigned long long> h(g.nE);
         std::vector<int32_t> t((size_t)3 * g.Wpad);
@@ -1144,6 +1263,7 @@ int muca_checkpoint(muca_ctx *ctx, const char *path)
             return fail(ctx, MUCA_ERR_CUDA, "checkpoint: device read failed");
         }
         ok = ok && std::fwrite(g.lnW.data(), 8, g.nE, f) == (size_t)g.nE;
+        ok = ok && std::fwrite(g.acc.data(), 8, g.acc.size(), f) == g.acc.size();
         ok = ok && std::fwrite(h.data(), 8, h.size(), f) == h.size();
         ok = ok && std::fwrite(t.data(), 4, t.size(), f) == t.size();
         ok = ok && std::fwrite(s.data(), 4, s.size(), f) == s.size();
@@ -1164,7 +1284,9 @@ int muca_restore(muca_ctx *ctx, const char *path)
     uint32_t seed = 0;
     uint64_t sweep = 0;
     int32_t ng = 0;
-    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0;
+    bool ok = std::fread(magic, 1, 8, f) == 8;
+    const bool v2 = ok && std::memcmp(magic, kMagic, 8) == 0;
+    ok = ok && (v2 || std::memcmp(magic, kMagic01, 8) == 0);
     ok = ok && std::fread(&seed, sizeof seed, 1, f) == 1;
     ok = ok && std::fread(&sweep, sizeof sweep, 1, f) == 1;
     ok = ok && std::fread(&ng, sizeof ng, 1, f) == 1 && ng == (int32_t)ctx->g.size();
@@ -1174,16 +1296,23 @@ int muca_restore(muca_ctx *ctx, const char *path)
              s.n_walkers == g.spec.n_walkers && s.e_min == g.spec.e_min &&
              s.e_max == g.spec.e_max;
     }
+    std::vector<int32_t> recs(ctx->g.size(), MUCA_REC_PLAIN);
+    if (v2)
+        for (auto &r : recs)
+            ok = ok && std::fread(&r, sizeof r, 1, f) == 1 &&
+                 (r == MUCA_REC_PLAIN || r == MUCA_REC_ACCUMULATED);
     if (!ok) {
         std::fclose(f);
         return fail(ctx, MUCA_ERR_INVALID_ARG, "restore: %s does not match this context", path);
     }
-    for (auto &g : ctx->g) {
-        std::vector<double> lnW(g.nE);
+    for (size_t gi = 0; gi < ctx->g.size(); ++gi) {
+        Group &g = ctx->g[gi];
+        std::vector<double> lnW(g.nE), acc(g.acc.size(), 0.0);
         std::vector<unsigned long long> h(g.nE);
         std::vector<int32_t> t((size_t)3 * g.Wpad);
         std::vector<uint32_t> s((size_t)g.L * g.L * g.Lw * g.Wpad);
         ok = std::fread(lnW.data(), 8, g.nE, f) == (size_t)g.nE &&
+             (!v2 || std::fread(acc.data(), 8, acc.size(), f) == acc.size()) &&
              std::fread(h.data(), 8, h.size(), f) == h.size() &&
              std::fread(t.data(), 4, t.size(), f) == t.size() &&
              std::fread(s.data(), 4, s.size(), f) == s.size();
@@ -1192,6 +1321,9 @@ int muca_restore(muca_ctx *ctx, const char *path)
             return fail(ctx, MUCA_ERR_IO, "restore: %s is truncated", path);
         }
         g.lnW = lnW;
+        g.acc = acc;
+        g.recursion = recs[gi];
+        g.flat[0] = g.flat[1] = g.flat[2] = 0.0;
         g.injected.clear();
         g.in_window = true;
         if (cudaMemcpy(g.hist, h.data(), h.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||

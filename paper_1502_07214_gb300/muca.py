@@ -25,6 +25,7 @@ ERR_WINDOW = -7
 ERR_IO = -8
 
 RES_AUTO, RES_GLOBAL, RES_SMEM, RES_SPLIT = 0, 1, 2, 3
+REC_PLAIN, REC_ACCUMULATED = 0, 1
 DEBUG_TALLY_CHECK = 1
 NK = 25
 
@@ -59,6 +60,10 @@ SIGNATURES = {
     "muca_sweep_iter": [_P, ctypes.c_int, ctypes.c_int],
     "muca_merge_update": [_P],
     "muca_run_graph": [_P, ctypes.c_int, ctypes.c_int],
+    "muca_weight_update": [_I32, _I32, _P, _P, _P],
+    "muca_set_recursion": [_P, _I32],
+    "muca_get_flatness": [_P, ctypes.c_int, _P],
+    "muca_iterate": [_P, _I32, _I32, _D, _P],
     "muca_reweight": [_P, _P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _P, _I32, _I32,
                       _P, _P],
     "muca_reweight_noalloc": [_P, _P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _P, _I32,
@@ -125,6 +130,19 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
 
 
+def weight_update(kind, hist, lnW, acc=None):
+    """One host-side weight update (muca_weight_update): lnW (float64) and,
+    for REC_ACCUMULATED, the pair weights acc (float64, len(hist) - 1) are
+    updated in place."""
+    hist = np.ascontiguousarray(hist, dtype=np.uint64)
+    assert lnW.dtype == np.float64 and lnW.flags.c_contiguous and len(lnW) == len(hist)
+    if acc is not None:
+        assert acc.dtype == np.float64 and acc.flags.c_contiguous
+        assert len(acc) >= len(hist) - 1
+    _ck(lib().muca_weight_update(int(kind), len(hist), _np_ptr(hist), _np_ptr(lnW),
+                                 None if acc is None else _np_ptr(acc)))
+
+
 class Context:
     """A set of (L, T) walker groups on one GPU (``muca_init`` .. ``muca_destroy``)."""
 
@@ -184,6 +202,25 @@ class Context:
 
     def run_graph(self, n_iters, sweeps_per_iter):
         self._c(lib().muca_run_graph(self._ctx, n_iters, sweeps_per_iter))
+
+    def set_recursion(self, kind):
+        """Weight recursion of every group: REC_PLAIN or REC_ACCUMULATED."""
+        self._c(lib().muca_set_recursion(self._ctx, int(kind)))
+
+    def get_flatness(self, g):
+        """(min H / mean H, max H / mean H, bins hit) of the histogram merged
+        by the last weight update of group g."""
+        out = np.zeros(3)
+        self._c(lib().muca_get_flatness(self._ctx, g, _np_ptr(out)))
+        return out
+
+    def iterate(self, max_iters, sweeps_per_iter, flat_min):
+        """Weight iterations until every group's min H / mean H >= flat_min
+        (at most max_iters); returns the number of iterations run."""
+        n = ctypes.c_int32(0)
+        self._c(lib().muca_iterate(self._ctx, int(max_iters), int(sweeps_per_iter),
+                                   float(flat_min), ctypes.byref(n)))
+        return n.value
 
     def sync(self):
         self._c(lib().muca_sync(self._ctx))
