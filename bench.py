@@ -314,10 +314,11 @@ def run_ours(args, rank, world, local_rank):
     d2h = nE * 8 + meas * 3 * W * 4 + nE * 8 + grid.size * 5 * 8  # hist, series, lnW, results
 
     # reweighting sub-benchmark (FP32 vs FP64), rank 0 only
-    rw = mixed = None
+    rw = mixed = wu = None
     if rank == 0:
         rw = reweight_bench(torch, muca)
         mixed = mixed_bench(torch, muca, stream)
+        wu = weight_update_bench(muca)
 
     if rank == 0:
         pk, pk_kind = peaks()
@@ -359,6 +360,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk,
             "reweight": rw,
             "batched_mixed": mixed,
+            "weight_update": wu,
         }
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline_sample()
@@ -422,6 +424,27 @@ def mixed_bench(torch, muca, stream, n_it=2):
             "batched_configs": [{"residency": {1: "global", 2: "smem", 3: "split"}.get(c[0], str(c[0])),
                                  "walkers_per_block": c[1], "lanes_per_walker": c[2]}
                                 for c in cfgs]}
+
+
+def weight_update_bench(muca, reps=20):
+    """The host FP64 weight update of the graph step on the benchmark window
+    (V + 1 = 110593 bins), both recursions, on a seeded merged histogram of
+    4096 walkers x 1000 sweeps spread evenly over the bins (a flat-histogram
+    iteration); median of `reps` calls of muca_weight_update."""
+    V = wl.LARGE["L"] ** 3
+    rng = np.random.default_rng(7)
+    n = wl.LARGE["n_walkers"] * wl.LARGE["sweeps"]
+    H = rng.multinomial(n, np.full(V + 1, 1.0 / (V + 1))).astype(np.uint64)
+    out = {"n_e": V + 1, "entries": n}
+    for name, kind in (("plain", muca.REC_PLAIN), ("accumulated", muca.REC_ACCUMULATED)):
+        lnW, acc = np.zeros(V + 1), np.zeros(V)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            muca.weight_update(kind, H, lnW, acc)
+            ts.append(time.perf_counter() - t0)
+        out[name + "_ms"] = 1e3 * sorted(ts)[len(ts) // 2]
+    return out
 
 
 def reweight_bench(torch, muca):
