@@ -268,6 +268,33 @@ def test_reweight_two_ground_states_switch():
     np.testing.assert_allclose(out[:, 2], -beta * (-3) * V * V * q * (1 - q), rtol=1e-9)
 
 
+def test_exact_l2_switch_at_low_temperature():
+    """Sec. I: as T -> 0 the ordered (all +1 or all -1) and the empty (all 0)
+    ground states exchange at Delta_0 = zJ/2 = 3.  Exact enumeration of L = 2
+    (3^8 states) at T = 0.05: <E_Delta>/V crosses 1/2 at 3 + T ln 2 / V, the
+    two ordered states against the one empty state; every excited state is
+    suppressed by at least exp(-3/T).  Pins the model reading (Eq. 1, R1) that
+    the sampler pins rest on."""
+    L, T = 2, 0.05
+    V, beta = L ** 3, 1.0 / T
+    E = np.arange(V + 1)
+
+    def e_delta(delta):
+        P = exact.joint_distribution(L, beta, -beta * delta * E)
+        return sum(p * ed for (_, ed), p in P.items()) / V
+
+    lo, hi = 2.9, 3.1
+    assert e_delta(lo) > 0.5 > e_delta(hi)
+    for _ in range(60):
+        mid = lo + (hi - lo) / 2
+        if e_delta(mid) > 0.5:
+            lo = mid
+        else:
+            hi = mid
+    assert abs(lo - (3 + T * np.log(2) / V)) < 1e-9
+    assert abs(lo - 3) < T
+
+
 def test_reweight_sampler_against_exact_l2():
     """Sampler + reweighting together against exact canonical averages at L = 2
     over a Delta range (Eq. 2, Eq. 3, Eq. 6)."""
