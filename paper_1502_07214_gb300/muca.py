@@ -28,6 +28,7 @@ RES_AUTO, RES_GLOBAL, RES_SMEM, RES_SPLIT = 0, 1, 2, 3
 REC_PLAIN, REC_ACCUMULATED = 0, 1
 DEBUG_TALLY_CHECK = 1
 NK = 25
+MAX_L = 64  # largest linear size (MUCA_MAX_L)
 
 
 class MucaError(RuntimeError):

@@ -58,3 +58,15 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
     with pytest.raises(muca.MucaError) as e:
         muca.Context([{"L": 4, "T": 1.0, "n_walkers": 4, "e_min": 10, "e_max": 5}], stream=0)
     assert e.value.code == muca.ERR_INVALID_ARG
+
+
+def test_binding_constants_match_the_header():
+    """Every value the header defines (status codes, residencies, recursions,
+    limits) has the same value in the binding."""
+    from paper_1502_07214_gb300 import muca
+
+    text = open(os.path.join(ROOT, "include", "muca.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define MUCA_([A-Z_0-9]+)\s+\(?(-?\d+)\)?", text)}
+    assert {"OK", "ERR_INVALID_ARG", "RES_SPLIT", "REC_ACCUMULATED", "MAX_L", "NK"} <= set(defs)
+    for name, value in defs.items():
+        assert getattr(muca, name) == value, name

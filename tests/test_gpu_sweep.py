@@ -197,6 +197,21 @@ def test_narrow_and_wide_split_kernels_in_one_context(use_graph):
         assert np.array_equal(got[g]["ts"], ref["ts"].transpose(1, 2, 0))
 
 
+def test_largest_sizes_per_site_path():
+    """Row lengths the unrolled paths do not take (44, and 52 up to the
+    maximum L = 64, V = 262144 sites) run on the per-site path with the
+    global table: spins, tallies, weights and series bit-exact."""
+    groups = [{"L": L, "T": T, "n_walkers": nw}
+              for L, T, nw in [(44, 1.0, 3), (52, 0.9, 2), (64, 0.9, 5)]]
+    assert max(g["L"] for g in groups) == muca().MAX_L
+    got = gpu_run(groups, 17, 2, 1, n_meas=1)
+    for g, (spec, w0) in enumerate(zip(groups, walker_offsets(groups))):
+        ref = oracle.muca_run(spec["L"], spec["T"], spec["n_walkers"], 17, 2, 1, n_meas=1,
+                              walker_id0=w0)
+        compare_group(got[g], ref, 2)
+        assert np.array_equal(got[g]["ts"], ref["ts"].transpose(1, 2, 0))
+
+
 def test_medium_workload_reduced_bit_exact():
     """L=16, T=1.0, 1024 walkers, seed 1: 2 iterations x 8 sweeps + 4 measured."""
     s = wl.MEDIUM
