@@ -50,8 +50,8 @@ def env_int(k, d):
 
 
 # DRAM bytes (read + write) per sweep of the benchmark workload, from one ncu
-# capture of the kernel in this configuration (profiles/sweep_ws_L48_4096w.md):
-# 926.8 MB read + 848.5 MB written over a launch of 2 sweeps.  Valid only for
+# capture of the kernel in this configuration: 926.8 MB read + 848.5 MB
+# written over a launch of 2 sweeps.  Valid only for
 # the kernel source the counters were taken on; empty (traffic reported as
 # null) while no capture of the current source exists.
 TRAFFIC_PER_SWEEP = {3: (926.811392e6 + 848.504064e6) / 2}

@@ -222,20 +222,21 @@ int muca_reweight(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int6
 
 /* muca_reweight without any device allocation (the paper has no counterpart:
  * this is a deployment variant of the same computation).  For callers that
- * cannot allocate device memory at the point of the call - work being
- * recorded into someone else's CUDA graph, services that reserve all device
- * memory up front, real-time loops that cannot afford an allocator's
- * synchronisation, bindings without a device allocator.
+ * cannot allocate device memory at the point of the call: services that
+ * reserve all device memory up front, real-time loops that cannot afford an
+ * allocator's synchronisation, bindings without a device allocator.
  * Arguments, layouts, results and errors are those of muca_reweight.  Its
  * working memory is a fixed 4 MiB array in the library's device memory,
  * present on every GPU that loads the library until the process exits; this
  * covers n_e <= 32769 (an L = 32 lattice) with n_grid <= 4096 in either
  * precision, and larger problems fail with MUCA_ERR_INVALID_ARG.  The first
  * call on a device looks the array's address up (cudaGetSymbolAddress with
- * that device current); make that first call before any stream capture.  All
- * calls share the array and it keeps the last call's contents (the parts that
- * must start at zero are cleared by each call); calls whose GPU work overlaps
- * race on it and must be ordered.  Synchronises the stream. */
+ * that device current) and keeps it; make that first call before any stream
+ * capture, and do not call this entry point on a device after
+ * cudaDeviceReset of that device.  All calls share the array and it keeps the
+ * last call's contents (the parts that must start at zero are cleared by each
+ * call); calls whose GPU work overlaps race on it and must be ordered.
+ * Synchronises the stream. */
 int muca_reweight_noalloc(const int32_t *e_j, const int32_t *e_d, const int32_t *m,
                           int64_t n_rows, int32_t row_len, int64_t row_stride, const double *lnW,
                           int32_t e_min, int32_t n_e, double beta, int32_t V,

@@ -90,7 +90,8 @@ void set_last_error(const char *msg);
 
 // Reweighting on caller-provided device scratch (reweight.cu).
 int reweight_check_args(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n_rows,
-                        int32_t row_len, int64_t row_stride, const double *lnW, int32_t n_e,
+                        int32_t row_len, int64_t row_stride, const double *lnW, int32_t e_min,
+                        int32_t n_e,
                         double beta, int32_t V, const double *delta_grid, int32_t n_grid,
                         int32_t precision, double *out);
 size_t reweight_scratch_bytes(int32_t n_e, int32_t n_grid, int32_t precision);

@@ -46,8 +46,8 @@ __global__ void jk_bin_kernel(const int32_t *__restrict__ ej, const int32_t *__r
         for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < row_len;
              c += gridDim.x * blockDim.x) {
             const int64_t o = r * row_stride + c;
-            const int e = __ldg(ed + o) - e_min;
-            if (e < 0 || e >= nE) {
+            const int e = (int)((unsigned)__ldg(ed + o) - (unsigned)e_min);
+            if ((unsigned)e >= (unsigned)nE) {
                 atomicOr(err, 1);
                 continue;
             }
@@ -396,6 +396,8 @@ extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_
         n_iter < 0 || n_iter > 200 || n_jack < 0 || n_jack == 1 || n_jack > n_rows ||
         n_jack > 1024)
         return pk_fail(MUCA_ERR_INVALID_ARG, "muca_find_peak: bad sizes");
+    if ((int64_t)e_min + n_e - 1 > INT32_MAX)
+        return pk_fail(MUCA_ERR_INVALID_ARG, "muca_find_peak: e_min + n_e - 1 exceeds int32");
     if (!(beta > 0.0) || !std::isfinite(beta) || !std::isfinite(delta_lo) ||
         !std::isfinite(delta_hi) || !(delta_lo < delta_hi))
         return pk_fail(MUCA_ERR_INVALID_ARG, "muca_find_peak: need beta > 0 and delta_lo < delta_hi");
@@ -513,6 +515,8 @@ extern "C" int muca_equal_height(const int32_t *e_d, int64_t n_rows, int32_t row
         n_iter < 0 || n_iter > 200 || n_jack < 0 || n_jack == 1 || n_jack > n_rows ||
         n_jack > 1024)
         return pk_fail(MUCA_ERR_INVALID_ARG, "muca_equal_height: bad sizes");
+    if ((int64_t)e_min + n_e - 1 > INT32_MAX)
+        return pk_fail(MUCA_ERR_INVALID_ARG, "muca_equal_height: e_min + n_e - 1 exceeds int32");
     if (!(beta > 0.0) || !std::isfinite(beta) || !std::isfinite(delta_lo) ||
         !std::isfinite(delta_hi) || !(delta_lo < delta_hi))
         return pk_fail(MUCA_ERR_INVALID_ARG,

@@ -55,6 +55,15 @@ struct BinStats {
     F *lwlo; // FP32 only: lnW - hi
 };
 
+// Offset of a sample's E_Delta from the window start, formed in unsigned
+// arithmetic so that it is defined for every int32 value; a sample lies in the
+// window iff (unsigned)offset < nE (the argument check keeps e_min + nE - 1
+// inside int32, so the window does not wrap).
+__device__ __forceinline__ int bin_offset(int v, int e_min)
+{
+    return (int)((unsigned)v - (unsigned)e_min);
+}
+
 // Stage A, one sample at a time: every sum of every sample is a 64-bit
 // atomic add into the global bin sums; M^4 is a 128-bit sum whose low word's
 // returned old value gives the carry into the high word.
@@ -67,8 +76,8 @@ __global__ void bin_kernel(const int32_t *__restrict__ ej, const int32_t *__rest
         for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < row_len;
              c += gridDim.x * blockDim.x) {
             const int64_t o = base + c;
-            const int e = __ldg(ed + o) - e_min;
-            if (e < 0 || e >= nE) {
+            const int e = bin_offset(__ldg(ed + o), e_min);
+            if ((unsigned)e >= (unsigned)nE) {
                 atomicOr(err, 1);
                 continue;
             }
@@ -124,8 +133,8 @@ __global__ void bucket_count_kernel(const int32_t *__restrict__ ed, int64_t n_ro
     for (int64_t r = blockIdx.y; r < n_rows; r += gridDim.y)
         for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < row_len;
              c += gridDim.x * blockDim.x) {
-            const int e = __ldg(ed + r * row_stride + c) - e_min;
-            if (e < 0 || e >= nE) atomicOr(err, 1);
+            const int e = bin_offset(__ldg(ed + r * row_stride + c), e_min);
+            if ((unsigned)e >= (unsigned)nE) atomicOr(err, 1);
             else atomicAdd(&sc[e >> kBktBits], 1u);
         }
     __syncthreads();
@@ -167,8 +176,8 @@ bucket_scatter_kernel(const int32_t *__restrict__ ej, const int32_t *__restrict_
                 bk[q] = 0;
                 rank[q] = 0u;
                 if (c < row_len) {
-                    const int ee = __ldg(ed + r * row_stride + c) - e_min;
-                    if (ee >= 0 && ee < nE) {
+                    const int ee = bin_offset(__ldg(ed + r * row_stride + c), e_min);
+                    if ((unsigned)ee < (unsigned)nE) {
                         e[q] = ee;
                         bk[q] = ee >> kBktBits;
                         rank[q] = atomicAdd(&lc[bk[q]], 1u);
@@ -804,7 +813,8 @@ size_t reweight_scratch_bytes(int32_t n_e, int32_t n_grid, int32_t precision)
 }
 
 int reweight_check_args(const int32_t *e_j, const int32_t *e_d, const int32_t *m, int64_t n_rows,
-                        int32_t row_len, int64_t row_stride, const double *lnW, int32_t n_e,
+                        int32_t row_len, int64_t row_stride, const double *lnW, int32_t e_min,
+                        int32_t n_e,
                         double beta, int32_t V, const double *delta_grid, int32_t n_grid,
                         int32_t precision, double *out)
 {
@@ -815,6 +825,8 @@ int reweight_check_args(const int32_t *e_j, const int32_t *e_d, const int32_t *m
         return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: bad sizes");
     if (n_rows * (int64_t)row_len < 1)
         return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: no samples");
+    if ((int64_t)e_min + n_e - 1 > INT32_MAX)
+        return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: e_min + n_e - 1 exceeds int32");
     if (precision != 32 && precision != 64)
         return rw_fail(MUCA_ERR_INVALID_ARG, "muca_reweight: precision must be 32 or 64");
     if (!(beta > 0.0) || !std::isfinite(beta))
@@ -870,8 +882,8 @@ extern "C" int muca_reweight(const int32_t *e_j, const int32_t *e_d, const int32
                              const double *delta_grid, int32_t n_grid, int32_t precision,
                              double *out, void *stream)
 {
-    int rc = muca::reweight_check_args(e_j, e_d, m, n_rows, row_len, row_stride, lnW, n_e, beta,
-                                       V, delta_grid, n_grid, precision, out);
+    int rc = muca::reweight_check_args(e_j, e_d, m, n_rows, row_len, row_stride, lnW, e_min, n_e,
+                                       beta, V, delta_grid, n_grid, precision, out);
     if (rc != MUCA_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = muca::reweight_scratch_bytes(n_e, n_grid, precision);

@@ -2,21 +2,25 @@
 // muca_reweight with its working memory in a fixed array that the library
 // carries in device memory, for callers that must not allocate.
 //
-// Who needs it: code that runs where device allocation is off limits or
-// unpredictable - inside a region that another framework is recording into a
-// CUDA graph (an allocation there is either illegal or would be baked into the
-// graph), a service that reserves all of its device memory up front and must
-// not grow or fragment the pool afterwards, a real-time loop that cannot take
-// the synchronisation an allocator may impose, or a binding from a language
-// that reaches the library through plain pointers and has no allocator of its
-// own on the device.
+// Who needs it: code that runs where a device allocation is off limits or
+// unpredictable - a service that reserves all of its device memory up front
+// and must not grow or fragment its pool afterwards, a real-time loop that
+// cannot take the synchronisation an allocator may impose, or a binding from
+// a language that reaches the library through plain pointers and has no
+// device allocator of its own.
 //
 // The working memory is kScratchBytes of __device__ storage.  Every GPU that
 // loads the library holds this array until the process exits.  All calls on a
 // device share it and it keeps whatever the last call left in it; the
 // reweighting clears the parts that must start at zero itself.  Two calls
 // whose GPU work overlaps (for instance issued on different streams without
-// ordering) race on the array and give wrong results: order them.
+// ordering) race on the array and give wrong results: order them.  The call
+// waits for its stream before it returns, like muca_reweight.
+//
+// The array's device address is looked up once per device and kept for the
+// life of the process; after cudaDeviceReset the module, and with it the
+// array, is loaded anew, so a process that resets a device must not call this
+// entry point on that device again.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -77,8 +81,8 @@ extern "C" int muca_reweight_noalloc(const int32_t *e_j, const int32_t *e_d, con
                                      int32_t V, const double *delta_grid, int32_t n_grid,
                                      int32_t precision, double *out, void *stream)
 {
-    int rc = muca::reweight_check_args(e_j, e_d, m, n_rows, row_len, row_stride, lnW, n_e, beta,
-                                       V, delta_grid, n_grid, precision, out);
+    int rc = muca::reweight_check_args(e_j, e_d, m, n_rows, row_len, row_stride, lnW, e_min, n_e,
+                                       beta, V, delta_grid, n_grid, precision, out);
     if (rc != MUCA_OK) return rc;
     const size_t need = muca::reweight_scratch_bytes(n_e, n_grid, precision);
     if (need > kScratchBytes) {
