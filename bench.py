@@ -50,11 +50,13 @@ def env_int(k, d):
 
 
 # DRAM bytes (read + write) per sweep of the benchmark workload, from one ncu
-# capture of the kernel in this configuration: 926.8 MB read + 848.5 MB
-# written over a launch of 2 sweeps.  Valid only for
+# capture of each kernel in this configuration (a launch of 2 sweeps after
+# three 1000-sweep weight iterations): split kernel 926.8 MB read + 848.5 MB
+# written, row-scan kernel 1938.7 MB read + 881.6 MB written.  Valid only for
 # the kernel source the counters were taken on; empty (traffic reported as
 # null) while no capture of the current source exists.
-TRAFFIC_PER_SWEEP = {3: (926.811392e6 + 848.504064e6) / 2}
+TRAFFIC_PER_SWEEP = {3: (926.811392e6 + 848.504064e6) / 2,
+                     4: (1938.680e6 + 881.562624e6) / 2}
 
 
 def traffic_per_launch(res, sweeps):
@@ -338,7 +340,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": "L=48 T=0.9 4096 walkers: 1000-sweep MUCA iteration "
                                    "(graph) + 250 recorded sweeps + FP32 reweight to 4096 Delta",
                        "L": L, "T": T, "walkers": W, "sweeps_per_step": sweeps + meas,
-                       "residency": {1: "global", 2: "smem", 3: "split"}.get(res, str(res)),
+                       "residency": {1: "global", 2: "smem", 3: "split", 4: "scan"}.get(res, str(res)),
                        "walkers_per_block": wpb, "lanes_per_walker": lanes, "seed": s["seed"],
                        "l2": "inputs larger than L2 (lattice 453 MB int8)"},
             "plain": {"value": plain_value, "unit": UNIT, "steps": plain_steps},
@@ -346,7 +348,8 @@ def run_ours(args, rank, world, local_rank):
                          "unit": "Tops/s", "frac": achieved_ops / int_peak,
                          "traffic": traffic_per_launch(res, sweeps),
                          "kernel": {1: "sweep_global_kernel<false>", 2: "sweep_smem_kernel<false>",
-                                    3: "sweep_ws_kernel<false, true>"}.get(res, str(res)),
+                                    3: "sweep_ws_kernel<false, true>",
+                                    4: f"sweep_scan_kernel<{L}>"}.get(res, str(res)),
                          "ops_per_attempt": ops_per_attempt,
                          "peak_source": f"152 SMs x 128 INT32 lanes x median SM clock "
                                         f"{sm_clock:.0f} MHz",
@@ -421,7 +424,7 @@ def mixed_bench(torch, muca, stream, n_it=2):
                         f"512 walkers each, {n_it} iterations x {sweeps} sweeps",
             "unit": UNIT, "batched": vb, "plain_per_config": vp, "batched_over_plain": vb / vp,
             "batched_ms": ms_b, "plain_ms": ms_p,
-            "batched_configs": [{"residency": {1: "global", 2: "smem", 3: "split"}.get(c[0], str(c[0])),
+            "batched_configs": [{"residency": {1: "global", 2: "smem", 3: "split", 4: "scan"}.get(c[0], str(c[0])),
                                  "walkers_per_block": c[1], "lanes_per_walker": c[2]}
                                 for c in cfgs]}
 
@@ -510,8 +513,9 @@ def reweight_bench(torch, muca):
 def run_profile_case(what, cfg):
     """Short fixed launches for profiler captures (not timed): the sweep kernel
     of the benchmark workload in a given configuration "residency,walkers per
-    block,lanes per walker" (one launch of 100 sweeps that relaxes the random
-    start, then 2 launches of 2 sweeps; no autotuning trials) or the
+    block,lanes per walker" (three 1000-sweep weight iterations, the regime of
+    the benchmark's steps, then 2 launches of 2 sweeps; no autotuning trials)
+    or the
     reweighting of the reweight workload (FP32 then FP64)."""
     import torch
 
@@ -524,7 +528,9 @@ def run_profile_case(what, cfg):
         ctx = muca.Context([{"L": s["L"], "T": s["T"], "n_walkers": s["n_walkers"]}],
                            seed=s["seed"], residency=res, walkers_per_block=wpb,
                            lanes_per_walker=lanes)
-        ctx.sweep_iter(100)
+        for _ in range(3):
+            ctx.sweep_iter(1000)
+            ctx.merge_update()
         for _ in range(2):
             ctx.sweep_iter(2)
         ctx.sync()

@@ -80,6 +80,13 @@ typedef struct {
                              walkers' Metropolis chains and three warps that prepare
                              and finish the rows around it (L % 4 == 0, 8 <= L <= 48;
                              other sizes fall back to MUCA_RES_GLOBAL) */
+#define MUCA_RES_SCAN 4   /* spins in HBM/L2; one lane per packed word of a row
+                             (a segment of the next power of 2 >= L / 4 lanes per
+                             walker) resolves every row of L sites at once: the
+                             acceptances that depend on the left neighbour by a
+                             prefix scan of bit masks, re-run from each accepted
+                             move that changes E_Delta (L % 4 == 0, 4 <= L <= 64;
+                             other sizes fall back to MUCA_RES_GLOBAL) */
 
 /* debug_flags bits */
 #define MUCA_DEBUG_TALLY_CHECK 1 /* recompute E_J, E_Delta, M after every sweep call */
@@ -90,9 +97,10 @@ typedef struct {
     int32_t residency;         /* MUCA_RES_* */
     int32_t walkers_per_block; /* 0 = automatic; else 1 .. 32; a block is one warp, so
                                   walkers_per_block x lanes_per_walker <= 32 (== 32 for
-                                  global residency) */
+                                  global residency); fixed by L for MUCA_RES_SCAN */
     int32_t lanes_per_walker;  /* 0 = automatic; else 1, 2, 4 or 8 threads serve one
-                                  walker (they share its random numbers) */
+                                  walker (they share its random numbers); fixed by L
+                                  (1 .. 16) for MUCA_RES_SCAN */
 } muca_options;
 
 /* ---------------------------------------------------------------- lifetime */

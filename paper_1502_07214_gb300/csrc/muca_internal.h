@@ -72,12 +72,43 @@ cudaError_t prepare_global_kernel(size_t smem_bytes);
 // BlockDesc.S walker slots, a power of 2 in [4, 32]).  Two instantiations:
 // rows of up to kWsNarrowMaxL sites (wide = false) and longer rows.
 constexpr int kWsNarrowMaxL = 32;
-constexpr int kKinds = 4;  // kernel kinds: lanes, shared tile, split narrow, split wide
+// kernel kinds: lanes, shared tile, split narrow, split wide, row scan
+constexpr int kKinds = 5;
 cudaError_t launch_sweeps_ws(const GroupDev *groups_dev, const BlockDesc *blocks_dev, int n_blocks,
                              size_t smem_bytes, uint32_t seed, uint64_t sweep0, int n_sweeps,
                              int64_t ts_pos, bool record, bool wide, cudaStream_t st);
 cudaError_t prepare_ws_kernel(size_t smem_bytes, bool wide);
 size_t ws_bytes_for(int slots);
+// Row-scan launch (scan.cu): a walker's packed words of a row are split
+// into runs of scan_words(L) consecutive words, one run per lane of a segment
+// of scan_seg(L) lanes (a power of 2; L / (4 scan_words(L)) of its lanes are
+// used), so a warp serves 32 / scan_seg(L) walkers; blocks are one warp
+// (BlockDesc.S = walkers per warp, BlockDesc.P = segment lanes), one kernel
+// per row length; each walker
+// keeps a ring of scan_ring(L) table rows in shared memory.  Windows shorter
+// than a ring use other kernel kinds.
+__host__ __device__ constexpr int scan_seg(int L)
+{
+    return (L < 4 || L > 64 || L % 4) ? 0
+         : L == 4 ? 1 : L == 8 ? 2 : (L == 20 || L == 28 || L == 40 || L == 56 || L == 60) ? 8
+         : (L == 44 || L == 52) ? 16 : 4;
+}
+__host__ __device__ constexpr int scan_words(int L)
+{
+    return scan_seg(L) == 0 ? 0
+         : (L == 24 || L == 32 || L == 40 || L == 56) ? 2 : (L == 36 || L == 48 || L == 60) ? 3
+         : L == 64 ? 4 : 1;
+}
+__host__ __device__ constexpr int scan_ring(int L) { return L <= 16 ? 16 : 32; }
+bool scan_supported(int L, int nE);
+int scan_block_walkers(int L);
+size_t scan_bytes_for(int L);
+// One kernel per row length L: prepare it (outside any stream capture) and
+// launch it on blocks that all belong to groups of that L.
+cudaError_t prepare_scan_kernel(int L, size_t smem_bytes);
+cudaError_t launch_sweeps_scan(int L, const GroupDev *groups_dev, const BlockDesc *blocks_dev,
+                               int n_blocks, size_t smem_bytes, uint32_t seed, uint64_t sweep0,
+                               int n_sweeps, int64_t ts_pos, bool record, cudaStream_t st);
 // Bytes of one walker's lattice (padded rows), of a shared-memory tile, and of
 // the per-row staging area and table windows of `slots` walkers.
 size_t lattice_bytes(int L);

@@ -76,6 +76,16 @@ struct muca_ctx {
     BlockDesc *d_blocks[kKinds] = {};
     int n_blocks[kKinds] = {};
     size_t smem[kKinds] = {};
+    // the row-scan kind (4) has one kernel per row length: its blocks are
+    // sorted by L and launched per range, each on a stream of its own when
+    // more than one launch is in use
+    struct ScanRange {
+        int L, first, count;
+        size_t smem;
+    };
+    std::vector<ScanRange> scan_ranges;
+    std::vector<cudaStream_t> scan_streams;
+    std::vector<cudaEvent_t> scan_events;
 };
 
 namespace {
@@ -277,6 +287,7 @@ int upload_groups(muca_ctx *ctx)
 // Kernel kind of a group's configuration.
 int kind_of(const Group &g)
 {
+    if (g.residency == MUCA_RES_SCAN) return 4;
     if (g.residency == MUCA_RES_SPLIT) return g.L > kWsNarrowMaxL ? 3 : 2;
     return g.residency == MUCA_RES_SMEM ? 1 : 0;
 }
@@ -285,7 +296,9 @@ int kind_of(const Group &g)
 //   kind 0: one warp, P_g lanes per walker, staging area and table windows;
 //   kind 1: one warp, the walkers' lattices as a [L*L][Lw][wpb_g] tile too;
 //   kinds 2, 3: split kernel (chain warp + helpers), wpb_g a power of 2 in
-//   [4, 32]; kind 2 for rows of up to kWsNarrowMaxL sites, kind 3 above.
+//   [4, 32]; kind 2 for rows of up to kWsNarrowMaxL sites, kind 3 above;
+//   kind 4: row-scan kernel, one warp of wpb_g = 32 / P_g walkers per block,
+//   P_g = scan_seg(L) lanes per walker.
 int build_blocks(muca_ctx *ctx)
 {
     std::vector<BlockDesc> b[kKinds];
@@ -295,6 +308,7 @@ int build_blocks(muca_ctx *ctx)
         const int k = kind_of(g);
         const size_t need = k == 0   ? stage_bytes_for(g.wpb)
                             : k == 1 ? smem_bytes_for(g.L, g.wpb) + stage_bytes_for(g.wpb)
+                            : k == 4 ? scan_bytes_for(g.L)
                                      : ws_bytes_for(g.wpb);
         sm[k] = std::max(sm[k], need);
         for (int w0 = 0; w0 < g.W; w0 += g.wpb)
@@ -302,11 +316,35 @@ int build_blocks(muca_ctx *ctx)
     }
     // Longest blocks first: when a launch needs more than one wave of blocks,
     // the blocks of the largest lattices (work per sweep: walkers x sites)
-    // start first instead of forming the tail.
+    // start first instead of forming the tail.  Row-scan blocks are grouped
+    // by L first (one kernel per row length).
     for (int k = 0; k < kKinds; ++k)
         std::stable_sort(b[k].begin(), b[k].end(), [&](const BlockDesc &x, const BlockDesc &y) {
+            const int lx = ctx->g[x.group].L, ly = ctx->g[y.group].L;
+            if (k == 4 && lx != ly) return lx > ly;
             return (int64_t)x.nw * ctx->g[x.group].V > (int64_t)y.nw * ctx->g[y.group].V;
         });
+    ctx->scan_ranges.clear();
+    for (int i = 0; i < (int)b[4].size(); ++i) {
+        const int L = ctx->g[b[4][i].group].L;
+        if (ctx->scan_ranges.empty() || ctx->scan_ranges.back().L != L)
+            ctx->scan_ranges.push_back({L, i, 0, scan_bytes_for(L)});
+        ++ctx->scan_ranges.back().count;
+    }
+    for (const auto &rg : ctx->scan_ranges) {
+        if ((int64_t)rg.smem + 1024 > (int64_t)max_smem_per_block())
+            return fail(ctx, MUCA_ERR_INVALID_ARG, "%zu bytes of shared memory per block do not fit",
+                        rg.smem);
+        CK(prepare_scan_kernel(rg.L, rg.smem));
+    }
+    while (ctx->scan_streams.size() < ctx->scan_ranges.size()) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        ctx->scan_streams.push_back(s);
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->scan_events.push_back(e);
+    }
     for (int k = 0; k < kKinds; ++k) {
         if (sm[k] > 0 && (int64_t)sm[k] + 1024 > (int64_t)max_smem_per_block())
             return fail(ctx, MUCA_ERR_INVALID_ARG, "%zu bytes of shared memory per block do not fit",
@@ -314,7 +352,7 @@ int build_blocks(muca_ctx *ctx)
         if (!b[k].empty()) {
             if (k == 0) CK(prepare_global_kernel(sm[k]));
             if (k == 1) CK(prepare_smem_kernel(sm[k]));
-            if (k >= 2) CK(prepare_ws_kernel(sm[k], k == 3));
+            if (k == 2 || k == 3) CK(prepare_ws_kernel(sm[k], k == 3));
         }
         if (ctx->d_blocks[k]) cudaFree(ctx->d_blocks[k]);
         ctx->d_blocks[k] = nullptr;
@@ -329,15 +367,26 @@ int build_blocks(muca_ctx *ctx)
     return MUCA_OK;
 }
 
-// The launches of one sweep call: on the caller's stream when one kernel kind
-// is in use, otherwise forked over the per-kind streams and joined.
+// The launches of one sweep call: on the caller's stream when one launch is
+// in use, otherwise forked over per-launch streams and joined.
 int launch_all(muca_ctx *ctx, int n_sweeps, bool record, cudaStream_t st)
 {
-    int used = 0;
-    for (int k = 0; k < kKinds; ++k) used += ctx->n_blocks[k] > 0;
+    int used = (int)ctx->scan_ranges.size();
+    for (int k = 0; k < 4; ++k) used += ctx->n_blocks[k] > 0;
     const bool fork = used > 1;
     if (fork) CK(cudaEventRecord(ctx->ev_fork, st));
-    for (int k = 0; k < kKinds; ++k) {
+    for (size_t i = 0; i < ctx->scan_ranges.size(); ++i) {
+        const auto &rg = ctx->scan_ranges[i];
+        cudaStream_t s = fork ? ctx->scan_streams[i] : st;
+        if (fork) CK(cudaStreamWaitEvent(s, ctx->ev_fork, 0));
+        CK(launch_sweeps_scan(rg.L, ctx->d_groups, ctx->d_blocks[4] + rg.first, rg.count, rg.smem,
+                              ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record, s));
+        if (fork) {
+            CK(cudaEventRecord(ctx->scan_events[i], s));
+            CK(cudaStreamWaitEvent(st, ctx->scan_events[i], 0));
+        }
+    }
+    for (int k = 0; k < 4; ++k) {
         if (ctx->n_blocks[k] == 0) continue;
         cudaStream_t s = fork ? ctx->side[k] : st;
         if (fork) CK(cudaStreamWaitEvent(s, ctx->ev_fork, 0));
@@ -415,6 +464,14 @@ std::vector<Cand> candidates(const Group &g, int residency, int wpb, int P, int 
                 c.push_back({MUCA_RES_GLOBAL, 32 / p, p});
             }
         }
+    const bool want_r = residency == MUCA_RES_AUTO || residency == MUCA_RES_SCAN;
+    if (want_r && scan_supported(g.L, g.nE)) {
+        const int G = scan_block_walkers(g.L), Ps = scan_seg(g.L);
+        if ((wpb == 0 || wpb == G) && (P == 0 || P == Ps)) c.push_back({MUCA_RES_SCAN, G, Ps});
+    } else if (residency == MUCA_RES_SCAN) {
+        // sizes the row-scan kernel does not cover run on the lanes-per-walker kernel
+        c.push_back({MUCA_RES_GLOBAL, 32, 1});
+    }
     const bool want_w = residency == MUCA_RES_AUTO || residency == MUCA_RES_SPLIT;
     if (want_w && fixed_path(g) && g.L >= 8) {
         for (int G : {32, 16, 8}) {
@@ -497,13 +554,22 @@ static int tune_group(muca_ctx *ctx, size_t gi, int residency, int wpb, int P)
     ctx->d_groups = dg;
     int rc = upload_groups(ctx);
     // Trials start from a relaxed copy: the sweeps right after a random start
-    // move E_Delta much faster than a running simulation does.
-    const int relax_sweeps = std::max(4, std::min(64, (1 << 22) / std::max(1, g.V)));
+    // move E_Delta much faster than a running simulation does, and the
+    // row-scan kernel's cost grows with the moves that change E_Delta, so a
+    // short relaxation would favour the kernels whose cost does not (at
+    // L = 48 it is slower than the split kernel after 37 sweeps and faster
+    // after 150).  The relaxation runs on a row-scan or split candidate when
+    // there is one.
+    const int relax_sweeps = std::max(4, std::min(300, (1 << 25) / std::max(1, g.V)));
     const int trial_sweeps = std::max(2, std::min(8, (1 << 18) / std::max(1, g.V)));
+    Cand relax_c = cands[0];
+    for (const Cand &c : cands)
+        if (c.res == MUCA_RES_SCAN || (c.res == MUCA_RES_SPLIT && relax_c.res != MUCA_RES_SCAN))
+            relax_c = c;
     if (rc == MUCA_OK) {
-        ctx->g[0].residency = cands[0].res;
-        ctx->g[0].wpb = cands[0].wpb;
-        ctx->g[0].P = cands[0].P;
+        ctx->g[0].residency = relax_c.res;
+        ctx->g[0].wpb = relax_c.wpb;
+        ctx->g[0].P = relax_c.P;
         rc = build_blocks(ctx);
     }
     if (rc == MUCA_OK) rc = launch_all(ctx, relax_sweeps, false, ctx->stream);
@@ -682,6 +748,8 @@ void muca_destroy(muca_ctx *ctx)
         if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
         cudaFree(ctx->d_blocks[k]);
     }
+    for (auto s : ctx->scan_streams) cudaStreamDestroy(s);
+    for (auto e : ctx->scan_events) cudaEventDestroy(e);
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     delete ctx;
@@ -695,13 +763,13 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
     *out = nullptr;
     if (!groups || n_groups < 1 || !opt)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: need >= 1 group and options");
-    if (opt->residency < MUCA_RES_AUTO || opt->residency > MUCA_RES_SPLIT)
+    if (opt->residency < MUCA_RES_AUTO || opt->residency > MUCA_RES_SCAN)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad residency %d", opt->residency);
     if (opt->walkers_per_block < 0 || opt->walkers_per_block > 32)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad walkers_per_block %d",
                     opt->walkers_per_block);
     if (opt->lanes_per_walker != 0 && opt->lanes_per_walker != 1 && opt->lanes_per_walker != 2 &&
-        opt->lanes_per_walker != 4 && opt->lanes_per_walker != 8)
+        opt->lanes_per_walker != 4 && opt->lanes_per_walker != 8 && opt->lanes_per_walker != 16)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad lanes_per_walker %d",
                     opt->lanes_per_walker);
     int64_t total_w = 0;

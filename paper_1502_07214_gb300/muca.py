@@ -24,7 +24,7 @@ ERR_NOT_SUPPORTED = -6
 ERR_WINDOW = -7
 ERR_IO = -8
 
-RES_AUTO, RES_GLOBAL, RES_SMEM, RES_SPLIT = 0, 1, 2, 3
+RES_AUTO, RES_GLOBAL, RES_SMEM, RES_SPLIT, RES_SCAN = 0, 1, 2, 3, 4
 REC_PLAIN, REC_ACCUMULATED = 0, 1
 DEBUG_TALLY_CHECK = 1
 NK = 25

@@ -118,7 +118,8 @@ def compare_group(got, ref, n_iter):
 
 @pytest.mark.parametrize("residency,wpb,P", [(1, 32, 1), (1, 16, 2), (1, 8, 4), (1, 4, 8),
                                              (2, 32, 1), (2, 16, 1), (2, 8, 4), (2, 4, 8),
-                                             (3, 32, 0), (3, 16, 0), (3, 8, 0), (0, 0, 0)])
+                                             (3, 32, 0), (3, 16, 0), (3, 8, 0), (4, 16, 2),
+                                             (0, 0, 0)])
 def test_small_workload_full_run_bit_exact(residency, wpb, P):
     """L=8, T=2.0, 64 walkers, 10 iterations x 200 sweeps, seed 0, in full,
     in every kernel configuration (results never depend on it)."""
@@ -226,7 +227,7 @@ def sample_walkers(W):
     return sorted({0, 1, 31, 32, 33, W // 2, W - 33, W - 1} & set(range(W)))
 
 
-@pytest.mark.parametrize("residency,P", [(0, 0), (1, 4), (1, 8), (3, 0)])
+@pytest.mark.parametrize("residency,P", [(0, 0), (1, 4), (1, 8), (3, 0), (4, 0)])
 def test_large_workload_full_size_sampled_walkers(residency, P):
     """L=48, T=0.9, all 4096 walkers in the benchmark's launch configuration,
     under a fixed non-trivial weight: sampled walkers recomputed by the oracle,
@@ -328,7 +329,8 @@ def test_restricted_window_and_set_state():
 
 @pytest.mark.parametrize("e_min,e_max,res,P", [(300, 320, 1, 1), (250, 350, 1, 4),
                                               (420, 512, 1, 8), (250, 350, 3, 0),
-                                              (420, 512, 3, 0)])
+                                              (420, 512, 3, 0), (250, 350, 4, 0),
+                                              (420, 512, 4, 0), (300, 312, 4, 0)])
 def test_restricted_window_unrolled_size(e_min, e_max, res, P):
     """L=8 with a restricted E_Delta window: a window narrower than the kernel's
     table window (plain path) and wider ones that reach the top of the range
@@ -443,3 +445,58 @@ def test_injected_table_is_used():
         oracle.sweeps(L, 0, V, thr, 5, w, 0, 20, sp, t)
         assert np.array_equal(spins[w], sp)
     c.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_row_scan_kernel_every_shape_in_one_context(use_graph):
+    """The row-scan kernel over its range of row lengths (segments of 1, 2, 4,
+    8 and 16 lanes per walker, with idle lanes where L / 4 is not a power of
+    2), ragged walker counts (partial warps and blocks) and several warps per
+    block, plus a size it does not cover (L = 10, falls back to the
+    lanes-per-walker kernel): weights after two iterations, recorded series,
+    plain and graph form, against the oracle."""
+    groups = [{"L": L, "T": T, "n_walkers": nw}
+              for L, T, nw in [(4, 1.0, 35), (8, 2.0, 37), (12, 1.4182, 23), (16, 1.0, 9),
+                               (20, 0.9, 14), (24, 1.0, 21), (28, 2.0, 5), (32, 0.9, 11),
+                               (36, 1.0, 3), (48, 0.9, 9), (64, 0.9, 3), (10, 1.0, 7)]]
+    seed, n_iter, sweeps = 41, 2, 3
+    got = gpu_run(groups, seed, n_iter, sweeps, n_meas=3, use_graph=use_graph, residency=4)
+    for g, (spec, w0) in enumerate(zip(groups, walker_offsets(groups))):
+        want_res = 4 if spec["L"] != 10 else 1
+        assert got[g]["config"][0] == want_res, spec
+        ref = oracle.muca_run(spec["L"], spec["T"], spec["n_walkers"], seed, n_iter, sweeps,
+                              n_meas=3, walker_id0=w0)
+        if use_graph:
+            assert np.array_equal(got[g]["lnW"], ref["lnW"])
+            assert np.array_equal(got[g]["spins"], ref["spins"])
+            assert np.array_equal(got[g]["tallies"], ref["tallies"])
+        else:
+            compare_group(got[g], ref, n_iter)
+        assert np.array_equal(got[g]["ts"], ref["ts"].transpose(1, 2, 0)), spec
+
+
+@pytest.mark.parametrize("L,T,delta", [(8, 0.9, 2.964), (16, 0.9, 2.964), (24, 1.0, 2.944),
+                                       (48, 0.9, 2.964)])
+def test_row_scan_kernel_under_transition_weights(L, T, delta):
+    """Canonical weights at the first-order transition field from a random
+    start: many accepted moves that change E_Delta per row, so rows are
+    resolved in several segments and the table window moves often."""
+    V = L ** 3
+    W = 40
+    lnW = -(1.0 / T) * delta * np.arange(V + 1)
+    c = ctx_of([{"L": L, "T": T, "n_walkers": W}], seed=L, residency=4)
+    c.set_lnW(0, lnW)
+    n = 12
+    c.reserve_timeseries(n)
+    c.sweep_iter(n, record=True)
+    spins, tal = c.get_state(0)
+    ts = c.get_timeseries(0)
+    assert c.get_config(0)[0] == 4
+    c.close()
+    thr = oracle.build_table(L, T, 0, V, lnW)
+    for w in range(W):
+        sp = oracle.init_spins(L, L, w)
+        t = oracle.energies(L, sp).astype(np.int32)
+        ref = oracle.sweeps(L, 0, V, thr, L, w, 0, n, sp, t, record=True)
+        assert np.array_equal(spins[w], sp) and np.array_equal(tal[w], t), w
+        assert np.array_equal(ts[:, :, w], ref), w
