@@ -13,21 +13,16 @@
 // site's two thresholds are independent loads, so the work becomes
 // throughput-bound integer arithmetic.
 //
-// Layout of the work.  A block is one warp; P lanes serve one walker (the
-// walker's L / 4 packed words of a row are split into P runs of M = L / (4 P)
-// consecutive words, one run per lane), so a warp serves 32 / P walkers.
-// Per row, every lane:
-//   - has the old spins of its words and of their y / z neighbours in
-//     registers (loaded one row ahead; the y-1 neighbour of rows y > 0 is
-//     the row just finished, kept in registers), and the row's Philox words
-//     (drawn one row ahead);
-//   - forms its words' move descriptors byte-parallel (scan_core.cuh), the
-//     two table columns of each site, and the masks of its d != 0 sites;
-//   - loads the two thresholds of each of its sites from the walker's table
-//     row E0 and turns the compares into bits;
-// the lanes then OR their bits into row masks (shuffles), and each lane runs
-// the same scan and break test on the whole row.  New spins, their store
-// and the energy changes follow from the final acceptance mask.
+// Layout of the work.  A block is one warp of 32 / S walkers of one group;
+// a walker's L / 4 packed words of a row are split into runs of M
+// consecutive words, one run per lane of its segment of S lanes (scan_seg,
+// scan_words in muca_internal.h).  Per row, every lane forms its run's move
+// descriptors byte-parallel (scan_core.cuh), loads the two thresholds of
+// each of its sites from the walker's table row E0, and scans its own
+// sites' acceptance bits for an unknown input; the lanes' maps are then
+// composed through two ballots, and the first accepted move that changes
+// E_Delta is found through three.  New spins, their store and the energy
+// changes follow from the final acceptance bits of each lane.
 // Table rows: each walker keeps a ring of R table rows around its E_Delta
 // in shared memory, re-centred after a row with cp.async; a row whose E0 is
 // not among the rows known to be complete reads the global table instead.
