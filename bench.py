@@ -472,6 +472,15 @@ def reweight_bench(torch, muca):
         res[p] = r
         out[f"fp{p}_pts_per_s"] = len(grid) / dt_s
         out[f"fp{p}_ms"] = dt_s * 1e3
+    # stage A alone (exact integer sums per bin and the per-bin statistics):
+    # the same call with an empty Delta grid
+    muca.reweight(dj, dd, dm, lnW, 0, beta, V, grid[:0], 32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        muca.reweight(dj, dd, dm, lnW, 0, beta, V, grid[:0], 32)
+    out["stage_a_ms"] = (time.perf_counter() - t0) / 10 * 1e3
+    out["stage_a_input_bytes"] = int(12 * ed.size)
     scale = np.maximum(np.abs(res[64]), 1e-3 * np.abs(res[64]).max(axis=0, keepdims=True))
     err = (np.abs(res[32] - res[64]) / np.where(scale == 0, 1, scale)).max(axis=0)
     out["fp32_vs_fp64_max_rel_err"] = dict(zip(["E_J", "E_Delta", "C", "chi", "U4"],
