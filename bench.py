@@ -17,10 +17,12 @@ T=1.4182 run (Delta-grid points per second).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle on the host cores instead (bounded
-walker samples of the same workload).  Under torchrun (N > 1) every rank runs
-an independent replica of the workload (walkers are independent given the
-weights; the histogram merge would be one integer all-reduce and is not
-needed for replicas), timed with a barrier and the maximum over ranks.
+walker samples of the same workload).  Under torchrun (N > 1) the ranks run
+one simulation of N x 4096 walkers at L=48, T=0.9, each rank holding 4096 of
+them (weak scaling): after every iteration the ranks' integer histograms are
+summed with an NCCL all-reduce on device buffers and every rank runs the same
+FP64 weight update (the parallel scheme of Sec. II over GPUs).  Timed with a
+barrier and the maximum over ranks.
 """
 import argparse
 import json
@@ -66,10 +68,11 @@ def traffic_per_launch(res, sweeps):
     return None if b is None else b * sweeps
 
 
-def replica_seed(seed, rank):
-    """With N GPUs every rank runs an independent replica of the workload: the
-    same sizes, its own Philox seed."""
-    return seed + 7919 * rank
+def shard_group(L, T, walkers_per_rank, world):
+    """With N GPUs the ranks run one simulation of N x walkers_per_rank
+    walkers, each rank holding its shard (weak scaling); returns the group
+    and the shard option of the context."""
+    return {"L": L, "T": T, "n_walkers": walkers_per_rank * world}
 
 
 def job_rate(ms_local, units_per_rank, world, dist=None, device="cpu"):
@@ -240,14 +243,29 @@ def run_ours(args, rank, world, local_rank):
     grid = wl.delta_grid(2.964)  # the first-order transition field at T=0.9 (Sec. III)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ctx = muca.Context([{"L": L, "T": T, "n_walkers": W}], seed=replica_seed(s["seed"], rank))
+    from paper_1502_07214_gb300 import shard
+
+    # one simulation over all ranks: each holds 4096 walkers of the group and
+    # the histograms are summed over the ranks (NCCL, device buffers) after
+    # every iteration; one rank runs the same workload unsharded
+    ctx = muca.Context([shard_group(L, T, W, world)], seed=s["seed"],
+                       shard=(rank, world) if world > 1 else (0, 0))
     ctx.reserve_timeseries(meas)
     res, wpb, lanes = ctx.get_config(0)
     launches_per_sweep_call = 1
+
+    def iteration():
+        if world > 1:
+            # the all-reduce sits between the sweeps and the weight update,
+            # so the sharded iteration is not one graph
+            ctx.sweep_iter(sweeps)
+            shard.merge_update(ctx, dist.all_reduce, device=True)
+        else:
+            ctx.run_graph(1, sweeps)
     attempts_step = W * V * (sweeps + meas)
 
     def step_batched():
-        ctx.run_graph(1, sweeps)
+        iteration()
         ctx.reserve_timeseries(meas)  # rewind
         ctx.sweep_iter(meas, record=True)
         return muca.reweight_context(ctx, 0, grid, 32, stream=stream)
@@ -282,7 +300,10 @@ def run_ours(args, rank, world, local_rank):
         ctx.sweep_iter(sweeps)
         b.record(stream)
         ev.append((a, b, sweeps))
-        ctx.merge_update()
+        if world > 1:
+            shard.merge_update(ctx, dist.all_reduce, device=True)
+        else:
+            ctx.merge_update()
         ctx.reserve_timeseries(meas)
         ctx.sweep_iter(meas, record=True)
         muca.reweight_context(ctx, 0, grid, 32, stream=stream)
@@ -300,7 +321,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     q0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.run_graph(1, sweeps)
+        iteration()
         ctx.reserve_timeseries(meas)
         ctx.sweep_iter(meas, record=True)
         muca.reweight_context(ctx, 0, grid, 32, stream=stream)
@@ -314,6 +335,8 @@ def run_ours(args, rank, world, local_rank):
     nE = V + 1
     h2d = (nE + 4) * 40 * 4  # table upload of the merge (table rows incl. guards x 40 words)
     d2h = nE * 8 + meas * 3 * W * 4 + nE * 8 + grid.size * 5 * 8  # hist, series, lnW, results
+    if world > 1:  # the shard's histogram goes through device buffers, not the host
+        d2h -= nE * 8
 
     # reweighting sub-benchmark (FP32 vs FP64), rank 0 only
     rw = mixed = wu = None

@@ -101,6 +101,13 @@ typedef struct {
     int32_t lanes_per_walker;  /* 0 = automatic; else 1, 2, 4 or 8 threads serve one
                                   walker (they share its random numbers); fixed by L
                                   (1 .. 16) for MUCA_RES_SCAN */
+    int32_t shard_rank;        /* walker sharding over contexts (e.g. one per GPU):
+                                  with shard_count = N > 1 the context holds shard
+                                  shard_rank (0 .. N-1) of every group, walkers
+                                  [floor(W r / N), floor(W (r + 1) / N)) of its W
+                                  (n_walkers is the group's total), with the global
+                                  walker ids of the unsharded context; 0 / 0 = all */
+    int32_t shard_count;
 } muca_options;
 
 /* ---------------------------------------------------------------- lifetime */
@@ -181,6 +188,18 @@ int muca_run_graph(muca_ctx *ctx, int n_iters, int sweeps_per_iter);
  * MUCA_ERR_INVALID_ARG for an unknown kind, n_e < 1 or a missing array. */
 int muca_weight_update(int32_t kind, int32_t n_e, const uint64_t *hist, double *lnW,
                        double *acc);
+
+/* The acceptance-threshold table of a weight function on the host; no device
+ * work, no context (the table that muca_merge_update builds and uploads).
+ *   L, T, e_min, e_max   the group (window [e_min, e_max], e_max >= e_min)
+ *   lnW                  host FP64 [e_max - e_min + 1]
+ *   out                  host uint32 [n_e][3][MUCA_NK], index
+ *                        [E_Delta - e_min][d + 1][dE_J + 12] (the layout of
+ *                        muca_get_table; every entry follows the formula, also
+ *                        for (d, dE_J) pairs that no move produces)
+ * MUCA_ERR_INVALID_ARG for a bad size or window or a NULL array. */
+int muca_build_table(int32_t L, double T, int32_t e_min, int32_t e_max, const double *lnW,
+                     uint32_t *out);
 
 /* Select the weight recursion of every group of ctx (MUCA_REC_*) and clear
  * the accumulated pair weights (muca_set_lnW clears a group's as well). */
@@ -336,6 +355,19 @@ int muca_set_table(muca_ctx *ctx, int group, const uint32_t *in);
 int muca_get_hist(muca_ctx *ctx, int group, uint64_t *out);
 int muca_set_hist(muca_ctx *ctx, int group, const uint64_t *in);
 
+/* The same with device buffers (uint64 [n_e] on the context's device), for
+ * merging the histograms of walker shards with a device all-reduce (Sec. II:
+ * the walkers' histograms are summed after every iteration).  get copies the
+ * histogram into dev_out and synchronises the context's stream; set copies
+ * dev_in over the histogram on the context's stream (dev_in must be complete
+ * when it is called, e.g. the caller's all-reduce stream synchronised). */
+int muca_get_hist_device(muca_ctx *ctx, int group, uint64_t *dev_out);
+int muca_set_hist_device(muca_ctx *ctx, int group, const uint64_t *dev_in);
+
+/* Walkers of group g held by this context (its shard) and the global Philox
+ * id of the first of them; either output may be NULL. */
+int muca_get_walkers(muca_ctx *ctx, int group, int32_t *n_local, uint32_t *first_id);
+
 /* Walker state of group g: spins host int8 [n_walkers][L^3] (site i =
  * x + L (y + L z)), tallies host int32 [n_walkers][3] = (E_J, E_Delta, M).
  * Either output may be NULL.  set_state uploads spins and recomputes the
@@ -357,9 +389,10 @@ int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walke
 /* Checkpoint / restore: spins, tallies, lnW, histograms, the weight
  * recursion with its accumulated pair weights, sweep counters and the seed,
  * to / from a file.  Philox is counter-based, so a restored run continues
- * bit-identically.  restore requires a context with the same groups; it also
- * reads files of the earlier format without the recursion (plain recursion,
- * no accumulated weights). */
+ * bit-identically.  restore requires a context with the same groups and the
+ * same shard (muca_options.shard_rank / shard_count); it also reads files of
+ * the earlier formats without the shard record (every walker of a group) or
+ * without the recursion (plain recursion, no accumulated weights). */
 int muca_checkpoint(muca_ctx *ctx, const char *path);
 int muca_restore(muca_ctx *ctx, const char *path);
 

@@ -125,12 +125,17 @@ inline uint32_t thr_of(double x)
     return t >= 2147483648.0 ? 0x80000000u : (uint32_t)t;
 }
 
-inline uint32_t thr_entry(const Group &g, int e, int d, int dej)
+inline uint32_t table_entry(double beta, const double *lnW, int nE, int e, int d, int dej)
 {
     const int en = e + d;
-    if (en < 0 || en >= g.nE) return 0u;
-    const double x = -(g.beta * (double)dej) + (g.lnW[en] - g.lnW[e]);
+    if (en < 0 || en >= nE) return 0u;
+    const double x = -(beta * (double)dej) + (lnW[en] - lnW[e]);
     return thr_of(x);
+}
+
+inline uint32_t thr_entry(const Group &g, int e, int d, int dej)
+{
+    return table_entry(g.beta, g.lnW.data(), g.nE, e, d, dej);
 }
 
 template <class F>
@@ -772,6 +777,12 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
         opt->lanes_per_walker != 4 && opt->lanes_per_walker != 8 && opt->lanes_per_walker != 16)
         return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad lanes_per_walker %d",
                     opt->lanes_per_walker);
+    const int shards = opt->shard_count > 1 ? opt->shard_count : 1;
+    const int srank = opt->shard_count > 1 ? opt->shard_rank : 0;
+    if (opt->shard_count < 0 || opt->shard_rank < 0 || (opt->shard_count <= 1 && opt->shard_rank) ||
+        srank >= shards)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "muca_init: bad shard %d of %d",
+                    opt->shard_rank, opt->shard_count);
     int64_t total_w = 0;
     for (int i = 0; i < n_groups; ++i) {
         const muca_group &s = groups[i];
@@ -782,6 +793,10 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
             return fail(nullptr, MUCA_ERR_INVALID_ARG, "group %d: T must be > 0", i);
         if (s.n_walkers < 1)
             return fail(nullptr, MUCA_ERR_INVALID_ARG, "group %d: n_walkers < 1", i);
+        if ((int64_t)s.n_walkers * (srank + 1) / shards - (int64_t)s.n_walkers * srank / shards < 1)
+            return fail(nullptr, MUCA_ERR_INVALID_ARG,
+                        "group %d: %d walkers leave shard %d of %d empty", i, s.n_walkers, srank,
+                        shards);
         const int V = s.L * s.L * s.L;
         const int emax = s.e_max < 0 ? V : s.e_max;
         if (s.e_min < 0 || emax > V || s.e_min > emax)
@@ -821,7 +836,11 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
             g.spec = groups[i];
             g.L = groups[i].L;
             g.V = g.L * g.L * g.L;
-            g.W = groups[i].n_walkers;
+            // this context's shard of the group's walkers, numbered as in the
+            // unsharded context
+            const int64_t tot = groups[i].n_walkers;
+            const int64_t lo = tot * srank / shards, hi = tot * (srank + 1) / shards;
+            g.W = (int)(hi - lo);
             g.Wpad = ((g.W + 31) / 32) * 32;
             g.Lw = (g.L + 3) / 4;
             g.e_min = groups[i].e_min;
@@ -830,8 +849,8 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
             g.nE = g.e_max - g.e_min + 1;
             g.T = groups[i].T;
             g.beta = 1.0 / g.T;
-            g.walker0 = w0;
-            w0 += (uint32_t)g.W;
+            g.walker0 = w0 + (uint32_t)lo;
+            w0 += (uint32_t)tot;
             g.lnW.assign(g.nE, 0.0);
             g.acc.assign((size_t)std::max(g.nE - 1, 1), 0.0);
             const size_t sbytes = (size_t)g.L * g.L * g.Lw * g.Wpad * sizeof(uint32_t);
@@ -1200,6 +1219,56 @@ int muca_set_hist(muca_ctx *ctx, int group, const uint64_t *in)
     return MUCA_OK;
 }
 
+int muca_get_hist_device(muca_ctx *ctx, int group, uint64_t *dev_out)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!dev_out) return fail(ctx, MUCA_ERR_INVALID_ARG, "dev_out is NULL");
+    Group &g = ctx->g[group];
+    CK(cudaMemcpyAsync(dev_out, g.hist, (size_t)g.nE * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_set_hist_device(muca_ctx *ctx, int group, const uint64_t *dev_in)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!dev_in) return fail(ctx, MUCA_ERR_INVALID_ARG, "dev_in is NULL");
+    Group &g = ctx->g[group];
+    CK(cudaMemcpyAsync(g.hist, dev_in, (size_t)g.nE * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_get_walkers(muca_ctx *ctx, int group, int32_t *n_local, uint32_t *first_id)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (n_local) *n_local = ctx->g[group].W;
+    if (first_id) *first_id = ctx->g[group].walker0;
+    return MUCA_OK;
+}
+
+int muca_build_table(int32_t L, double T, int32_t e_min, int32_t e_max, const double *lnW,
+                     uint32_t *out)
+{
+    if (L < 2 || L > MUCA_MAX_L || !(T > 0.0) || !std::isfinite(T))
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "build_table: L=%d, T=%g", L, T);
+    if (e_min < 0 || e_max < e_min || e_max > L * L * L || !lnW || !out)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "build_table: window [%d, %d] or NULL array",
+                    e_min, e_max);
+    const int nE = e_max - e_min + 1;
+    const double beta = 1.0 / T;
+    for (int e = 0; e < nE; ++e)
+        for (int d = -1; d <= 1; ++d)
+            for (int dej = -12; dej <= 12; ++dej)
+                out[((size_t)e * 3 + (d + 1)) * MUCA_NK + (dej + 12)] =
+                    table_entry(beta, lnW, nE, e, d, dej);
+    return MUCA_OK;
+}
+
 int muca_get_state(muca_ctx *ctx, int group, int8_t *spins, int32_t *tallies)
 {
     int rc = check_group_index(ctx, group);
@@ -1296,10 +1365,13 @@ int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walke
 }
 
 // Checkpoint file: magic with the format version, seed, sweep, n_groups, per
-// group the spec, per group the weight recursion (int32), then per group
-// lnW[nE], acc[max(nE - 1, 1)], hist[nE], tallies[3][Wpad], spins[V][Wpad].
-// Format 01 (still read) has neither the recursion nor acc.
-static const char kMagic[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '2'};
+// group the spec, per group the weight recursion (int32), per group the
+// global id of its first walker and the walkers held (int32 x 2, the shard),
+// then per group lnW[nE], acc[max(nE - 1, 1)], hist[nE], tallies[3][Wpad],
+// spins[V][Wpad].  Formats 02 (no shard record: every walker of the group)
+// and 01 (neither the shard, the recursion nor acc) are still read.
+static const char kMagic[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '3'};
+static const char kMagic02[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '2'};
 static const char kMagic01[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '1'};
 
 int muca_checkpoint(muca_ctx *ctx, const char *path)
@@ -1318,6 +1390,10 @@ int muca_checkpoint(muca_ctx *ctx, const char *path)
     for (auto &g : ctx->g) {
         const int32_t rec = g.recursion;
         ok = ok && std::fwrite(&rec, sizeof rec, 1, f) == 1;
+    }
+    for (auto &g : ctx->g) {
+        const int32_t shard[2] = {(int32_t)g.walker0, g.W};
+        ok = ok && std::fwrite(shard, sizeof shard, 1, f) == 1;
     }
     for (auto &g : ctx->g) {
         if (!ok) break;
@@ -1353,7 +1429,8 @@ int muca_restore(muca_ctx *ctx, const char *path)
     uint64_t sweep = 0;
     int32_t ng = 0;
     bool ok = std::fread(magic, 1, 8, f) == 8;
-    const bool v2 = ok && std::memcmp(magic, kMagic, 8) == 0;
+    const bool v3 = ok && std::memcmp(magic, kMagic, 8) == 0;
+    const bool v2 = v3 || (ok && std::memcmp(magic, kMagic02, 8) == 0);
     ok = ok && (v2 || std::memcmp(magic, kMagic01, 8) == 0);
     ok = ok && std::fread(&seed, sizeof seed, 1, f) == 1;
     ok = ok && std::fread(&sweep, sizeof sweep, 1, f) == 1;
@@ -1369,6 +1446,13 @@ int muca_restore(muca_ctx *ctx, const char *path)
         for (auto &r : recs)
             ok = ok && std::fread(&r, sizeof r, 1, f) == 1 &&
                  (r == MUCA_REC_PLAIN || r == MUCA_REC_ACCUMULATED);
+    // the walkers of each group: written by format 03; earlier formats held
+    // every walker of the group
+    for (auto &g : ctx->g) {
+        int32_t shard[2] = {0, g.spec.n_walkers};
+        if (v3) ok = ok && std::fread(shard, sizeof shard, 1, f) == 1;
+        ok = ok && shard[1] == g.W && (!v3 || (uint32_t)shard[0] == g.walker0);
+    }
     if (!ok) {
         std::fclose(f);
         return fail(ctx, MUCA_ERR_INVALID_ARG, "restore: %s does not match this context", path);

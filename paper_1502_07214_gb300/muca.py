@@ -45,7 +45,8 @@ class Group(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint32), ("debug_flags", ctypes.c_int32),
                 ("residency", ctypes.c_int32), ("walkers_per_block", ctypes.c_int32),
-                ("lanes_per_walker", ctypes.c_int32)]
+                ("lanes_per_walker", ctypes.c_int32), ("shard_rank", ctypes.c_int32),
+                ("shard_count", ctypes.c_int32)]
 
 
 _lib = None
@@ -82,6 +83,10 @@ SIGNATURES = {
     "muca_set_table": [_P, ctypes.c_int, _P],
     "muca_get_hist": [_P, ctypes.c_int, _P],
     "muca_set_hist": [_P, ctypes.c_int, _P],
+    "muca_get_hist_device": [_P, ctypes.c_int, _P],
+    "muca_set_hist_device": [_P, ctypes.c_int, _P],
+    "muca_get_walkers": [_P, ctypes.c_int, _P, _P],
+    "muca_build_table": [_I32, _D, _I32, _I32, _P, _P],
     "muca_get_state": [_P, ctypes.c_int, _P, _P],
     "muca_set_state": [_P, ctypes.c_int, _P],
     "muca_check_tallies": [_P],
@@ -131,6 +136,18 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
 
 
+def build_table(L, T, e_min, e_max, lnW):
+    """The acceptance-threshold table of a weight function, built on the host
+    (``muca_build_table``): uint32 [n_e][3][NK]."""
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    n_e = e_max - e_min + 1
+    assert lnW.shape == (n_e,)
+    out = np.zeros((n_e, 3, NK), dtype=np.uint32)
+    _ck(lib().muca_build_table(int(L), float(T), int(e_min), int(e_max), _np_ptr(lnW),
+                               _np_ptr(out)))
+    return out
+
+
 def weight_update(kind, hist, lnW, acc=None):
     """One host-side weight update (muca_weight_update): lnW (float64) and,
     for REC_ACCUMULATED, the pair weights acc (float64, len(hist) - 1) are
@@ -148,7 +165,11 @@ class Context:
     """A set of (L, T) walker groups on one GPU (``muca_init`` .. ``muca_destroy``)."""
 
     def __init__(self, groups, seed=0, debug_flags=0, residency=RES_AUTO, walkers_per_block=0,
-                 lanes_per_walker=0, stream=None):
+                 lanes_per_walker=0, stream=None, shard=(0, 0)):
+        """groups: dicts with L, T, n_walkers (and optionally e_min, e_max);
+        shard = (rank, count): with count > 1 the context holds shard `rank`
+        of every group's n_walkers walkers (the ``n_walkers`` of ``specs`` is
+        then the shard's own count)."""
         L = lib()
         self.specs = []
         arr = (Group * len(groups))()
@@ -161,11 +182,19 @@ class Context:
             self.specs.append({"L": int(g["L"]), "T": float(g["T"]), "n_walkers": int(g["n_walkers"]),
                                "e_min": int(g.get("e_min", 0)),
                                "e_max": V if e_max < 0 else int(e_max), "V": V})
-        opt = Options(seed, debug_flags, residency, walkers_per_block, lanes_per_walker)
+        opt = Options(seed, debug_flags, residency, walkers_per_block, lanes_per_walker,
+                      int(shard[0]), int(shard[1]))
         self._stream = _stream_ptr(stream)
         self._ctx = ctypes.c_void_p()
         _ck(L.muca_init(ctypes.cast(arr, _P), len(groups), ctypes.byref(opt), self._stream,
                         ctypes.byref(self._ctx)))
+        for g, sp in enumerate(self.specs):
+            n = ctypes.c_int32()
+            w0 = ctypes.c_uint32()
+            self._c(L.muca_get_walkers(self._ctx, g, ctypes.byref(n), ctypes.byref(w0)))
+            sp["n_walkers_total"] = sp["n_walkers"]
+            sp["n_walkers"] = n.value
+            sp["first_walker"] = w0.value
 
     # -- lifetime
     def close(self):
@@ -278,6 +307,17 @@ class Context:
         a = np.ascontiguousarray(h, dtype=np.uint64)
         assert a.shape == (self.n_e(g),)
         self._c(lib().muca_set_hist(self._ctx, g, _np_ptr(a)))
+
+    def get_hist_device(self, g, out):
+        """Copy group g's histogram into a CUDA tensor of n_e 64-bit integers."""
+        assert out.is_cuda and out.numel() == self.n_e(g) and out.element_size() == 8
+        self._c(lib().muca_get_hist_device(self._ctx, g, ctypes.c_void_p(out.data_ptr())))
+
+    def set_hist_device(self, g, t):
+        """Replace group g's histogram by a CUDA tensor of n_e 64-bit integers
+        (complete on the device when called)."""
+        assert t.is_cuda and t.numel() == self.n_e(g) and t.element_size() == 8
+        self._c(lib().muca_set_hist_device(self._ctx, g, ctypes.c_void_p(t.data_ptr())))
 
     def get_state(self, g):
         self.n_e(g)

@@ -67,18 +67,29 @@ def test_iterate_until_flat(rec):
     np.testing.assert_array_equal(lnW, ref_n["lnW"])
 
 
-def checkpoint_v01(src, dst, n_e):
-    """The same checkpoint in the earlier format (one group): magic 01, no
-    recursion field, no accumulated pair weights."""
+def _head(b):
     import ctypes
 
+    assert b[:8] == b"MUCABC03"
+    return 8 + 4 + 8 + 4 + ctypes.sizeof(muca().Group)  # magic, seed, sweep, n_groups, group
+
+
+def checkpoint_v01(src, dst, n_e):
+    """The same checkpoint in the earliest format (one group): magic 01, no
+    recursion field, no shard record, no accumulated pair weights."""
     b = open(src, "rb").read()
-    assert b[:8] == b"MUCABC02"
-    head = 8 + 4 + 8 + 4 + ctypes.sizeof(muca().Group)  # magic, seed, sweep, n_groups, group
-    rest = b[head + 4:]        # without the recursion field
+    head = _head(b)
+    rest = b[head + 4 + 8:]    # without the recursion field and the shard record
     lnw = rest[:8 * n_e]
     rest = rest[8 * n_e + 8 * max(n_e - 1, 1):]  # without acc
     open(dst, "wb").write(b"MUCABC01" + b[8:head] + lnw + rest)
+
+
+def checkpoint_v02(src, dst):
+    """The same checkpoint in format 02 (one group): no shard record."""
+    b = open(src, "rb").read()
+    head = _head(b)
+    open(dst, "wb").write(b"MUCABC02" + b[8:head + 4] + b[head + 4 + 8:])
 
 
 def test_checkpoint_carries_the_recursion(tmp_path):
@@ -124,6 +135,17 @@ def test_checkpoint_carries_the_recursion(tmp_path):
         d.merge_update()
     np.testing.assert_array_equal(d.get_lnW(0), plain_lnW)
     d.close()
+    # format 02 (no shard record: every walker of the group) restores the run
+    v2 = str(tmp_path / "acc02.ckpt")
+    checkpoint_v02(path, v2)
+    e = m.Context(g, seed=seed)
+    e.restore(v2)
+    for _ in range(2):
+        e.sweep_iter(30)
+        e.merge_update()
+    np.testing.assert_array_equal(e.get_lnW(0), want_lnW)
+    np.testing.assert_array_equal(e.get_state(0)[0], want_spins)
+    e.close()
 
 
 def test_recursion_errors():

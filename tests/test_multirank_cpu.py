@@ -1,6 +1,8 @@
-"""The N-GPU form of the benchmark runs one independent replica per rank and
-reports the whole job's rate over the slowest rank.  Its cross-rank steps run
-here as two gloo ranks on the CPU (no GPU involved)."""
+"""The N-GPU form of the benchmark and the walker-sharded merge (Sec. II's
+parallel scheme over ranks).  Their cross-rank steps run here as two gloo
+ranks on the CPU (no GPU involved): the whole job's rate over the slowest
+rank, and a sharded run whose merged histograms, weights and tables equal one
+rank holding all the walkers."""
 import os
 import socket
 
@@ -30,7 +32,7 @@ def _rank(rank, world, port, out):
     try:
         # rank r times 10 (r + 1) ms for 1000 units
         rate, ms = bench.job_rate(10.0 * (rank + 1), 1000, world, dist)
-        out[rank] = (rate, ms, bench.replica_seed(3, rank))
+        out[rank] = (rate, ms, bench.shard_group(48, 0.9, 4096, world)["n_walkers"])
     finally:
         dist.destroy_process_group()
 
@@ -46,7 +48,7 @@ def test_two_ranks_rate_over_the_slowest_rank():
         rate, ms, seed = res[r]
         assert ms == 20.0  # the slower rank's time, on every rank
         assert rate == pytest.approx(2 * 1000 / 0.020)
-    assert res[0][2] != res[1][2]  # independent replicas
+    assert res[0][2] == res[1][2] == 2 * 4096  # one simulation of both ranks' walkers
 
 
 def test_one_rank_needs_no_process_group():
@@ -57,3 +59,74 @@ def test_one_rank_needs_no_process_group():
 
     rate, ms = bench.job_rate(12.5, 500, 1)
     assert ms == 12.5 and rate == pytest.approx(500 / 0.0125)
+
+
+def _shard_rank(rank, world, port, out):
+    """One rank of a sharded run: the oracle sweeps this rank's walkers (the
+    test's stand-in for a GPU), the product's sharded host merge sums the
+    histograms over the ranks and updates lnW, and the product's host table
+    build gives the next iteration's table."""
+    import sys
+
+    sys.path.insert(0, os.path.dirname(HERE))
+    import numpy as np
+
+    import oracle
+    from paper_1502_07214_gb300 import muca, shard
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        L, T, W, seed, n_iter, sweeps = SHARD_RUN
+        V = L ** 3
+        lo, hi = shard.shard_range(W, rank, world)
+        spins = {w: oracle.init_spins(L, seed, w) for w in range(lo, hi)}
+        tal = {w: oracle.energies(L, spins[w]).astype(np.int32) for w in spins}
+        lnW = np.zeros(V + 1)
+        table = muca.build_table(L, T, 0, V, lnW)
+        merged = []
+        for it in range(n_iter):
+            H = np.zeros(V + 1, dtype=np.uint64)
+            for w in spins:
+                oracle.sweeps(L, 0, V, table, seed, w, it * sweeps, sweeps, spins[w], tal[w],
+                              hist=H)
+            merged.append(shard.host_merge_update(H, lnW, dist.all_reduce))
+            table = muca.build_table(L, T, 0, V, lnW)
+        out[rank] = (np.array(merged), lnW, table, {w: spins[w] for w in spins})
+    finally:
+        dist.destroy_process_group()
+
+
+# L, T, walkers, seed, iterations, sweeps per iteration of the sharded run
+SHARD_RUN = (4, 1.0, 13, 5, 4, 30)
+
+
+def test_two_ranks_sharded_merge_equals_one_rank():
+    """Walkers sharded over two gloo ranks (6 and 7 of 13): after every
+    iteration the all-reduced histogram equals the merged histogram of one
+    oracle run holding all the walkers, and the weights, the tables and every
+    walker's spins are bit-identical to that run."""
+    import sys
+
+    sys.path.insert(0, os.path.dirname(HERE))
+    import numpy as np
+
+    import oracle
+
+    L, T, W, seed, n_iter, sweeps = SHARD_RUN
+    V = L ** 3
+    ref = oracle.muca_run(L, T, W, seed, n_iter, sweeps)
+    world = 2
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_shard_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    for r in range(world):
+        merged, lnW, table, spins = res[r]
+        assert np.array_equal(merged, ref["hist"]), r
+        assert np.array_equal(lnW, ref["lnW"]), r
+        assert np.array_equal(table, oracle.build_table(L, T, 0, V, ref["lnW"])), r
+        for w, s in spins.items():
+            assert np.array_equal(s, ref["spins"][w]), (r, w)
+    assert sorted(w for r in range(world) for w in res[r][3]) == list(range(W))

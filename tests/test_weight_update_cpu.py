@@ -52,3 +52,14 @@ def test_weight_update_errors():
     assert e.value.code == m.ERR_INVALID_ARG
     m.weight_update(m.REC_PLAIN, H, lnW)  # the plain one does not
     np.testing.assert_array_equal(lnW, np.zeros(5))
+
+
+@pytest.mark.parametrize("L,T,e_min,e_max", [(2, 1.0, 0, 8), (4, 0.9, 0, 64), (5, 2.0, 30, 90)])
+def test_host_table_build_equals_oracle(L, T, e_min, e_max):
+    """muca_build_table (host, no context) against the oracle's table on the
+    same weights, entry for entry."""
+    from paper_1502_07214_gb300 import workloads as wl
+
+    lnW = wl.random_lnW(e_max - e_min + 1, seed=L, scale=2.0, slope=-2.8 / T)
+    got = m.build_table(L, T, e_min, e_max, lnW)
+    assert np.array_equal(got, oracle.build_table(L, T, e_min, e_max, lnW))
