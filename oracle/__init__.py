@@ -37,6 +37,8 @@ def lib():
                                   P, P, P, P, P, i32, i32]
         L.or_muca_run_rec.argtypes = [i32, dbl, i32, i32, i32, u32, u32, i32, i32, i32,
                                       P, P, P, P, P, i32, i32, i32, P]
+        L.or_muca_run_win.argtypes = [i32, dbl, i32, i32, i32, u32, u32, i32, i32, i32,
+                                      P, P, P, P, P, i32, i32, i32, P, i32, i32, dbl, i32, P]
         L.or_reweight.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
         L.or_reweight_q.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
         L.or_find_peak.argtypes = [P, P, i64, i32, P, i32, i32, dbl, dbl, dbl, i32, i32, i32, P]
@@ -44,6 +46,7 @@ def lib():
                                       i32, P]
         for f in ("or_init_spins", "or_energies", "or_build_table", "or_sweeps",
                   "or_update_lnW", "or_update_lnW_acc", "or_muca_run", "or_muca_run_rec",
+                  "or_muca_run_win",
                   "or_reweight", "or_reweight_q",
                   "or_find_peak", "or_equal_height"):
             getattr(L, f).restype = ctypes.c_int
@@ -136,28 +139,35 @@ def flatness(H):
 
 def muca_run(L, T, n_walkers, seed, n_iter, sweeps_per_iter, n_meas=0, e_min=0, e_max=None,
              walker_id0=0, lnW=None, check=False, n_threads=None, want_spins=True, recursion=0,
-             acc=None):
+             acc=None, window=None, grow_flat=0.0, grow_step=0):
     """A whole run of one (L, T) group; returns a dict of numpy arrays.
     recursion 0: lnW -= ln H; 1: the accumulated recursion, whose pair
-    weights start from acc (zeros by default) and are returned as "acc"."""
+    weights start from acc (zeros by default) and are returned as "acc".
+    window (lo, hi): the walkers' active E_Delta window (reading R15 of
+    muca_oracle.c), growing by grow_step bins on each side after an iteration
+    whose histogram has min H / mean H >= grow_flat over it; "windows" holds
+    the window after every iteration.  Default: [e_min, e_max], fixed."""
     V = L ** 3
     if e_max is None:
         e_max = V
     nE = e_max - e_min + 1
+    lo, hi = (e_min, e_max) if window is None else window
     lnW = np.zeros(nE) if lnW is None else np.array(lnW, dtype=np.float64, copy=True)
     acc = np.zeros(max(nE - 1, 1)) if acc is None else np.array(acc, dtype=np.float64, copy=True)
     hist = np.zeros((max(n_iter, 1), nE), dtype=np.uint64)
+    wins = np.zeros((max(n_iter, 1), 2), dtype=np.int32)
     spins = np.zeros((n_walkers, V), dtype=np.int8) if want_spins else None
     tal = np.zeros((n_walkers, 3), dtype=np.int32)
     ts = np.zeros((n_walkers, n_meas, 3), dtype=np.int32) if n_meas > 0 else None
     if n_threads is None:
         n_threads = os.cpu_count() or 1
-    _ck(lib().or_muca_run_rec(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
+    _ck(lib().or_muca_run_win(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
                               sweeps_per_iter, n_meas, _p(lnW), _p(hist), _p(spins), _p(tal),
-                              _p(ts), int(check), n_threads, int(recursion), _p(acc)),
+                              _p(ts), int(check), n_threads, int(recursion), _p(acc), int(lo),
+                              int(hi), float(grow_flat), int(grow_step), _p(wins)),
         "muca_run")
     return {"lnW": lnW, "hist": hist[:n_iter], "spins": spins, "tallies": tal, "ts": ts,
-            "acc": acc}
+            "acc": acc, "windows": wins[:n_iter]}
 
 
 def _rw(fn, e_j, e_d, m, lnW, e_min, beta, V, grid, n_threads):

@@ -49,6 +49,7 @@
  *   R9, R10 (rounding of the reweighting) are stated where they are used.
  *   R13 the accumulated, error-weighted form of the weight recursion and its
  *       rule for empty bins are stated at or_update_lnW_acc.
+ *   R15 the adaptive E_Delta window is stated at or_muca_run_win.
  */
 #include "muca_oracle.h"
 
@@ -396,12 +397,52 @@ int or_muca_run_rec(int L, double T, int n_walkers, int e_min, int e_max, uint32
                     int32_t *tallies_out, int32_t *ts, int check, int n_threads,
                     int recursion, double *acc)
 {
+    return or_muca_run_win(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
+                           sweeps_per_iter, n_meas, lnW, hist_iter, spins_out, tallies_out, ts,
+                           check, n_threads, recursion, acc, e_min, e_max, 0.0, 0, NULL);
+}
+
+/* Reading R15, the adaptive E_Delta window (the paper samples one range,
+ * [0, V], and gives no rule for moving a window; the weight iterations of the
+ * recursions it cites start from where the walkers are).  The walkers move in
+ * an active window [a, b] inside [e_min, e_max]: a proposal whose E_Delta + d
+ * leaves [a, b] is rejected, as R4 rejects one leaving [e_min, e_max].  After
+ * the iteration's merge and weight update (over all of [e_min, e_max]), if
+ * grow_flat > 0 and the merged histogram over [a, b] has
+ * min H / mean H >= grow_flat (mean H = sum H / (b - a + 1)), the window grows
+ * by grow_step bins on each side, clamped to [e_min, e_max].  A new bin starts
+ * from the weight of the old edge next to it (lnW copied outward from a and
+ * from b), and the accumulated pair weights (R13) of the pairs that contain a
+ * new bin start from 0: nothing has been measured there. */
+static double window_flatness(const uint64_t *H, int a, int b)
+{
+    uint64_t lo = H[a], sum = 0;
+    for (int e = a; e <= b; ++e) {
+        if (H[e] < lo) lo = H[e];
+        sum += H[e];
+    }
+    if (sum == 0) return 0.0;
+    const double mean = (double)sum / (double)(b - a + 1);
+    return (double)lo / mean;
+}
+
+int or_muca_run_win(int L, double T, int n_walkers, int e_min, int e_max, uint32_t seed,
+                    uint32_t walker_id0, int n_iter, int sweeps_per_iter, int n_meas,
+                    double *lnW, uint64_t *hist_iter, int8_t *spins_out,
+                    int32_t *tallies_out, int32_t *ts, int check, int n_threads,
+                    int recursion, double *acc, int win_lo, int win_hi, double grow_flat,
+                    int grow_step, int32_t *win_iter)
+{
     if (L < 2 || !(T > 0.0) || n_walkers < 1 || n_iter < 0 || sweeps_per_iter < 0 ||
         n_meas < 0 || !lnW || recursion < 0 || recursion > 1 || (recursion == 1 && !acc))
         return OR_ERR_ARG;
     int64_t V = (int64_t)L * L * L;
     if (e_min < 0 || e_max > V || e_min > e_max) return OR_ERR_ARG;
+    if (win_lo < e_min || win_hi > e_max || win_lo > win_hi) return OR_ERR_ARG;
+    if (grow_flat < 0.0 || (grow_flat > 0.0 && grow_step < 1)) return OR_ERR_ARG;
     int nE = e_max - e_min + 1;
+    /* the active window [a, b], relative to e_min */
+    int a = win_lo - e_min, b = win_hi - e_min;
     int8_t *spins = (int8_t *)malloc((size_t)n_walkers * (size_t)V);
     int32_t *tal = (int32_t *)malloc((size_t)n_walkers * 3 * sizeof(int32_t));
     uint32_t *thr = (uint32_t *)malloc((size_t)nE * 3 * OR_NK * sizeof(uint32_t));
@@ -416,7 +457,7 @@ int or_muca_run_rec(int L, double T, int n_walkers, int e_min, int e_max, uint32
         or_init_spins(L, seed, walker_id0 + (uint32_t)w, s);
         int64_t e[3];
         or_energies(L, s, e);
-        if (e[1] < e_min || e[1] > e_max) {
+        if (e[1] < e_min + a || e[1] > e_min + b) {
             rc = OR_ERR_WINDOW;
             goto done;
         }
@@ -428,37 +469,58 @@ int or_muca_run_rec(int L, double T, int n_walkers, int e_min, int e_max, uint32
     sweep_job proto;
     memset(&proto, 0, sizeof proto);
     proto.L = L;
-    proto.e_min = e_min;
-    proto.e_max = e_max;
     proto.check = check;
     proto.thr = thr;
     proto.seed = seed;
     proto.walker_id0 = walker_id0;
     proto.spins = spins;
     proto.tallies = tal;
-    or_build_table(L, T, e_min, e_max, lnW, thr);
+    /* the sweeps see the window [a, b] only: its table rows, built from its
+     * slice of lnW, and its slice of the histogram */
+    proto.e_min = e_min + a;
+    proto.e_max = e_min + b;
+    or_build_table(L, T, e_min + a, e_min + b, lnW + a, thr);
     for (int it = 0; it < n_iter; ++it) {
         memset(hist, 0, (size_t)nE * sizeof(uint64_t));
         proto.sweep0 = sweep;
         proto.n_sweeps = sweeps_per_iter;
         proto.ts = NULL;
-        rc = sweep_all(n_walkers, n_threads, nE, proto, hist);
+        rc = sweep_all(n_walkers, n_threads, b - a + 1, proto, hist + a);
         if (rc != OR_OK) goto done;
         sweep += (uint64_t)sweeps_per_iter;
         if (hist_iter) memcpy(hist_iter + (size_t)it * nE, hist, (size_t)nE * sizeof(uint64_t));
+        const double flat = window_flatness(hist, a, b);
         if (recursion == 1) {
             rc = or_update_lnW_acc(nE, hist, lnW, acc);
             if (rc != OR_OK) goto done;
         } else {
             or_update_lnW(nE, hist, lnW);
         }
-        or_build_table(L, T, e_min, e_max, lnW, thr);
+        if (grow_flat > 0.0 && flat >= grow_flat && (a > 0 || b < nE - 1)) {
+            const int na = a - grow_step > 0 ? a - grow_step : 0;
+            const int nb = b + grow_step < nE - 1 ? b + grow_step : nE - 1;
+            for (int e = na; e < a; ++e) lnW[e] = lnW[a];
+            for (int e = b + 1; e <= nb; ++e) lnW[e] = lnW[b];
+            if (recursion == 1) {
+                for (int e = na; e < a; ++e) acc[e] = 0.0;
+                for (int e = b; e < nb; ++e) acc[e] = 0.0;
+            }
+            a = na;
+            b = nb;
+            proto.e_min = e_min + a;
+            proto.e_max = e_min + b;
+        }
+        if (win_iter) {
+            win_iter[2 * it + 0] = e_min + a;
+            win_iter[2 * it + 1] = e_min + b;
+        }
+        or_build_table(L, T, e_min + a, e_min + b, lnW + a, thr);
     }
     if (n_meas > 0) {
         proto.sweep0 = sweep;
         proto.n_sweeps = n_meas;
         proto.ts = ts;
-        rc = sweep_all(n_walkers, n_threads, nE, proto, NULL);
+        rc = sweep_all(n_walkers, n_threads, b - a + 1, proto, NULL);
         if (rc != OR_OK) goto done;
     }
     if (spins_out) memcpy(spins_out, spins, (size_t)n_walkers * (size_t)V);

@@ -91,6 +91,20 @@ int or_muca_run_rec(int L, double T, int n_walkers, int e_min, int e_max, uint32
                     int32_t *tallies_out, int32_t *ts, int check, int n_threads,
                     int recursion, double *acc);
 
+/* The same run in an adaptive E_Delta window (reading R15 in the .c file):
+ * the walkers move in [win_lo, win_hi] (inside [e_min, e_max]; every initial
+ * E_Delta must lie in it, else OR_ERR_WINDOW), which grows by grow_step bins
+ * on each side after every iteration whose merged histogram has
+ * min H / mean H >= grow_flat over it (grow_flat = 0: a fixed window).
+ * win_iter [n_iter][2] receives the window after each iteration (the window
+ * of the next one), or NULL.  lnW, acc and hist_iter cover [e_min, e_max]. */
+int or_muca_run_win(int L, double T, int n_walkers, int e_min, int e_max, uint32_t seed,
+                    uint32_t walker_id0, int n_iter, int sweeps_per_iter, int n_meas,
+                    double *lnW, uint64_t *hist_iter, int8_t *spins_out,
+                    int32_t *tallies_out, int32_t *ts, int check, int n_threads,
+                    int recursion, double *acc, int win_lo, int win_hi, double grow_flat,
+                    int grow_step, int32_t *win_iter);
+
 /* Time-series reweighting (Eq. 3) to each Delta_k of grid[n_grid], FP64 with
  * compensated sums.  Samples: e_j[n], e_d[n], m[n].  lnW[nE] indexed by
  * E_Delta - e_min.  out[n_grid][5] = <E_J>, <E_Delta>, C (Eq. 6),
