@@ -61,6 +61,31 @@ TRAFFIC_PER_SWEEP = {3: (926.811392e6 + 848.504064e6) / 2,
                      4: (1938.680e6 + 881.562624e6) / 2}
 
 
+# L2 bytes (32-byte sectors through the L2, lts__t_sectors.sum) per sweep from
+# the same captures: split kernel 216.3 M sectors, row-scan kernel 337.2 M
+# sectors per 2-sweep launch.  Same validity rule as the DRAM traffic.
+L2_PER_SWEEP = {3: 216.3e6 * 32 / 2, 4: 337.2e6 * 32 / 2}
+
+PROBE_KINDS = {0: "IMAD a=a*a+b", 1: "IADD3 a=a+b+c", 2: "LOP3 a=(a&b)^c",
+               3: "half IMAD, half IADD3"}
+
+
+def device_probes(torch, muca, iters=4096, l2_reps=64):
+    """Ceilings of this device that the driver's peak file does not hold,
+    measured with the library's probe kernels (best of five launches): the
+    32-bit integer instruction rate of each probe kind and the L2 read
+    bandwidth of a 32 MiB buffer; the SM count from the device properties."""
+    props = torch.cuda.get_device_properties(0)
+    out = {"sm_count": props.multi_processor_count, "int_ops_per_s": {}}
+    for k, name in PROBE_KINDS.items():
+        ops, ms = muca.probe_int(k, iters=iters)
+        out["int_ops_per_s"][name] = ops
+    bw, ms = muca.probe_l2_read(32 << 20, reps=l2_reps)
+    out["l2_read_gbs"] = bw / 1e9
+    out["l2_buffer_bytes"] = 32 << 20
+    return out
+
+
 def traffic_per_launch(res, sweeps):
     """DRAM traffic of one launch of `sweeps` sweeps, scaled from the ncu
     capture (traffic grows in proportion to the sweeps), or None."""
@@ -341,6 +366,7 @@ def run_ours(args, rank, world, local_rank):
     # reweighting sub-benchmark (FP32 vs FP64), rank 0 only
     rw = mixed = wu = None
     if rank == 0:
+        probes = device_probes(torch, muca)
         rw = reweight_bench(torch, muca)
         mixed = mixed_bench(torch, muca, stream)
         wu = weight_update_bench(muca)
@@ -350,9 +376,12 @@ def run_ours(args, rank, world, local_rank):
         # the sweep is bound by the per-walker dependency chain and integer issue;
         # the ALU roofline counts the algorithmic integer operations per attempt
         ops_per_attempt = ALGO_INT_OPS
-        sm_clock = (clk or {}).get("sm_mhz") or 2070.0
-        int_peak = 152 * 128 * sm_clock * 1e6  # INT32 lanes x clock (ops/s)
+        # the ceiling is the measured rate of the best integer probe kind
+        int_kind, int_peak = max(probes["int_ops_per_s"].items(), key=lambda kv: kv[1])
         achieved_ops = ops_per_attempt * attempts_launch / (kern_avg_ms / 1e3)
+        l2_bytes = L2_PER_SWEEP.get(res)
+        achieved_l2 = (None if l2_bytes is None
+                       else l2_bytes * (attempts_launch / (W * L ** 3)) / (kern_avg_ms / 1e3) / 1e9)
         hbm_peak = float(pk.get("hbm_gbs", 6800.0))
         achieved_hbm = 2.0 * attempts_launch / (kern_avg_ms / 1e3) / 1e9
         line = {
@@ -374,12 +403,22 @@ def run_ours(args, rank, world, local_rank):
                                     3: "sweep_ws_kernel<false, true>",
                                     4: f"sweep_scan_kernel<{L}>"}.get(res, str(res)),
                          "ops_per_attempt": ops_per_attempt,
-                         "peak_source": f"152 SMs x 128 INT32 lanes x median SM clock "
-                                        f"{sm_clock:.0f} MHz",
+                         "peak_source": f"measured: muca_probe_int, {int_kind}, "
+                                        f"{probes['sm_count']} SMs x 8 blocks x 256 threads "
+                                        "(best of the four probe kinds)",
                          "kernel_ms": kern_avg_ms, "attempts_per_launch": attempts_launch,
                          "hbm": {"achieved_gbs": achieved_hbm, "peak_gbs": hbm_peak,
                                  "frac": achieved_hbm / hbm_peak,
-                                 "peak_kind": pk_kind, "bytes_per_attempt": 2}},
+                                 "peak_kind": pk_kind, "bytes_per_attempt": 2},
+                         "l2": {"achieved_gbs": achieved_l2, "peak_gbs": probes["l2_read_gbs"],
+                                "frac": None if achieved_l2 is None
+                                else achieved_l2 / probes["l2_read_gbs"],
+                                "bytes_per_sweep": l2_bytes,
+                                "peak_source": "measured: muca_probe_l2_read, 32 MiB read "
+                                               "64 times per launch",
+                                "bytes_source": "ncu lts__t_sectors.sum x 32 B of the "
+                                                "kernel's capture"}},
+            "probes": probes,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (launches_per_sweep_call * 2 + 3),
@@ -585,11 +624,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--profile", choices=["sweep", "reweight"],
+    ap.add_argument("--profile", choices=["sweep", "reweight", "probes"],
                     help="run a short untimed case for a profiler capture and exit")
     ap.add_argument("--profile-config", default="1,4,8",
                     help="sweep kernel configuration of --profile sweep")
     args = ap.parse_args()
+    if args.profile == "probes":
+        # the device probes alone, printed as JSON (short runs for a capture)
+        import torch
+
+        from paper_1502_07214_gb300 import muca
+
+        print(json.dumps(device_probes(torch, muca, iters=256, l2_reps=4)))
+        return
     if args.profile:
         run_profile_case(args.profile, args.profile_config)
         return

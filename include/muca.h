@@ -145,11 +145,12 @@ int muca_sync(muca_ctx *ctx);
 int muca_sweep_iter(muca_ctx *ctx, int n_sweeps, int record);
 
 /* The merge and weight update of one MUCA iteration for every group (Sec. II):
- * the merged histogram H is read back, lnW is updated in FP64 on the host by
- * the context's weight recursion (muca_set_recursion; by default
- * lnW[E] -= ln H[E] wherever H[E] > 0), the flatness of H is recorded
- * (muca_get_flatness), the threshold table is rebuilt in FP64 and uploaded,
- * and H is cleared.  Synchronises the stream. */
+ * the merged histogram H is read back, the flatness of H over the group's
+ * active window is recorded (muca_get_flatness), lnW is updated in FP64 on
+ * the host by the context's weight recursion (muca_set_recursion; by default
+ * lnW[E] -= ln H[E] wherever H[E] > 0), an adaptive window grows if H was
+ * flat over it (muca_set_window), the threshold table is rebuilt in FP64 and
+ * uploaded, and H is cleared.  Synchronises the stream. */
 int muca_merge_update(muca_ctx *ctx);
 
 /* The batched form: n_iters x (sweeps_per_iter sweeps of all groups in one
@@ -206,15 +207,41 @@ int muca_build_table(int32_t L, double T, int32_t e_min, int32_t e_max, const do
 int muca_set_recursion(muca_ctx *ctx, int32_t kind);
 
 /* Flatness of the histogram H merged by the last weight update of group g
- * (muca_merge_update, muca_run_graph or muca_iterate) over its n_e bins:
- * out host FP64 [3] = (min H / mean H, max H / mean H, number of bins with
- * H > 0), mean H = (sum H) / n_e; zeros before the first update or when H
- * was empty. */
+ * (muca_merge_update, muca_run_graph or muca_iterate) over the bins of the
+ * active window it was sampled in (all n_e bins unless muca_set_window
+ * restricted it): out host FP64 [3] = (min H / mean H, max H / mean H,
+ * number of bins with H > 0), mean H = (sum H) / bins; zeros before the
+ * first update or when H was empty. */
 int muca_get_flatness(muca_ctx *ctx, int group, double *out);
+
+/* The adaptive E_Delta window of the weight iteration.  The paper samples
+ * one range, E_Delta in [0, V], and gives no rule for moving a window; this
+ * is the library's reading of one.  The walkers of group g move in the active
+ * window [lo, hi] inside [e_min, e_max]: a proposal whose E_Delta + d leaves
+ * it is rejected (its thresholds are 0), as one leaving [e_min, e_max] is.
+ * After each merge and weight update, if grow_flat > 0 and the merged
+ * histogram had min H / mean H >= grow_flat over the window, the window grows
+ * by grow_step bins on each side, clamped to [e_min, e_max]; each new bin
+ * starts from the weight lnW of the old edge next to it, and the accumulated
+ * pair weights (MUCA_REC_ACCUMULATED) of the pairs that contain a new bin
+ * start from 0.  grow_flat = 0 keeps the window fixed.  Every walker's
+ * current E_Delta must lie in [lo, hi] (else MUCA_ERR_WINDOW and nothing
+ * changes), so a window set at the start usually spans the walkers' initial
+ * E_Delta; a sharded run sets the same window, over all shards' walkers, on
+ * every shard.  The table is rebuilt and uploaded; lnW is not changed.
+ * MUCA_ERR_INVALID_ARG for lo > hi, a window outside [e_min, e_max], a
+ * negative or non-finite grow_flat, or grow_flat > 0 with grow_step < 1.
+ * Synchronises the stream.  get_window: out host int32 [2] = the current
+ * (lo, hi). */
+int muca_set_window(muca_ctx *ctx, int group, int32_t lo, int32_t hi, double grow_flat,
+                    int32_t grow_step);
+int muca_get_window(muca_ctx *ctx, int group, int32_t *out);
 
 /* Weight iteration until the histograms are flat: up to max_iters iterations
  * of sweeps_per_iter sweeps followed by muca_merge_update; stops after the
- * first iteration at which min H / mean H >= flat_min for every group.
+ * first iteration at which min H / mean H >= flat_min for every group and
+ * every group's histogram was taken over its whole [e_min, e_max] (its active
+ * window was already full when the iteration ran).
  * *n_done receives the number of iterations run (host int32; max_iters if the
  * histograms never became flat, which is not an error).  Synchronises the
  * stream. */
@@ -372,7 +399,8 @@ int muca_get_walkers(muca_ctx *ctx, int group, int32_t *n_local, uint32_t *first
  * x + L (y + L z)), tallies host int32 [n_walkers][3] = (E_J, E_Delta, M).
  * Either output may be NULL.  set_state uploads spins and recomputes the
  * tallies on the device; fails with MUCA_ERR_WINDOW if an E_Delta leaves the
- * window, MUCA_ERR_INVALID_ARG if a spin is not in {-1, 0, +1}. */
+ * active window (muca_set_window), MUCA_ERR_INVALID_ARG if a spin is not in
+ * {-1, 0, +1}. */
 int muca_get_state(muca_ctx *ctx, int group, int8_t *spins, int32_t *tallies);
 int muca_set_state(muca_ctx *ctx, int group, const int8_t *spins);
 
@@ -387,12 +415,14 @@ int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walke
                     int32_t *lanes_per_walker);
 
 /* Checkpoint / restore: spins, tallies, lnW, histograms, the weight
- * recursion with its accumulated pair weights, sweep counters and the seed,
- * to / from a file.  Philox is counter-based, so a restored run continues
- * bit-identically.  restore requires a context with the same groups and the
- * same shard (muca_options.shard_rank / shard_count); it also reads files of
- * the earlier formats without the shard record (every walker of a group) or
- * without the recursion (plain recursion, no accumulated weights). */
+ * recursion with its accumulated pair weights, the active window with its
+ * growth rule, sweep counters and the seed, to / from a file.  Philox is
+ * counter-based, so a restored run continues bit-identically.  restore
+ * requires a context with the same groups and the same shard
+ * (muca_options.shard_rank / shard_count); it also reads files of the earlier
+ * formats without the window (the fixed window [e_min, e_max]), without the
+ * shard record (every walker of a group) or without the recursion (plain
+ * recursion, no accumulated weights). */
 int muca_checkpoint(muca_ctx *ctx, const char *path);
 int muca_restore(muca_ctx *ctx, const char *path);
 

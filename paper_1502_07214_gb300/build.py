@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmuca.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["sweep.cu", "scan.cu", "reweight.cu", "reweight_noalloc.cu", "peak.cu", "runtime.cu"]
+SOURCES = ["sweep.cu", "scan.cu", "reweight.cu", "reweight_noalloc.cu", "peak.cu", "runtime.cu",
+           "probe.cu"]
 HEADERS = ["muca_internal.h", "philox.cuh", "scan_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
@@ -26,8 +27,8 @@ def _nvcc():
 
 
 def _deps():
-    inc = os.path.join(os.path.dirname(HERE), "include", "muca.h")
-    return [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [inc, __file__]
+    inc = [os.path.join(os.path.dirname(HERE), "include", h) for h in ("muca.h", "muca_probe.h")]
+    return [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + inc + [__file__]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

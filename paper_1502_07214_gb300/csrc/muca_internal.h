@@ -66,6 +66,10 @@ cudaError_t launch_sweeps(const GroupDev *groups_dev, const BlockDesc *blocks_de
                           int threads, size_t smem_bytes, bool smem_kernel, uint32_t seed,
                           uint64_t sweep0, int n_sweeps, int64_t ts_pos, bool record,
                           cudaStream_t st);
+// Raise the dynamic shared-memory limit of a kernel on the current device to
+// at least smem_bytes; the limit is shared by every context of the process and
+// never lowered.
+cudaError_t raise_smem_limit(const void *func, size_t smem_bytes);
 cudaError_t prepare_smem_kernel(size_t smem_bytes);
 cudaError_t prepare_global_kernel(size_t smem_bytes);
 // Warp-specialised launch (blocks of one chain warp and helper warps;

@@ -1,0 +1,174 @@
+// probe.cu -- measurement probes for roofline denominators of this device
+// that a plain copy and a bf16 GEMM do not give: the issue rate of 32-bit
+// integer instructions and the read bandwidth of the L2 cache.  They are not
+// part of the method; the benchmark reports the sweep kernel's integer rate
+// and L2 traffic against them.
+//
+// Integer probe: every thread keeps eight 32-bit accumulators and updates
+// each from itself and the next two (cyclically), so that every update is one
+// machine instruction that no compiler can merge with the next one (the
+// result of two updates needs five distinct inputs, more than one
+// instruction takes) and no update can be folded away (each feeds the next
+// step).  Kinds: multiply-add a = a * a + b (the FMA pipe), three-input add
+// a = a + b + c and three-input logic a = (a & b) ^ c (the ALU pipe), and the
+// multiply-add on four accumulators with the add on the other four (both
+// pipes, the mix of the sweep kernels).  The grid holds eight 256-thread
+// blocks per SM, enough warps to hide each update's latency.
+//
+// L2 probe: a buffer smaller than the L2 is read whole, repeatedly, by every
+// SM with 16-byte loads that bypass L1 (ld.global.cg), after one untimed pass
+// that brings it into L2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "../../include/muca_probe.h"
+
+namespace {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeBlocksPerSm = 8;
+constexpr int kAcc = 8;
+constexpr int kUnroll = 4;
+
+template <int KIND>
+__device__ __forceinline__ uint32_t step(uint32_t a, uint32_t b, uint32_t c, int j)
+{
+    if (KIND == 0 || (KIND == 3 && (j & 1) == 0)) return a * a + b;
+    if (KIND == 1 || KIND == 3) return a + b + c;
+    return (a & b) ^ c;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kProbeThreads) int_probe_kernel(uint32_t seed, int iters,
+                                                                  uint32_t magic, uint32_t *sink)
+{
+    uint32_t a[kAcc];
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kAcc; ++j) a[j] = seed ^ (t * 0x9E3779B9u + (uint32_t)j * 0x85EBCA6Bu);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int j = 0; j < kAcc; ++j)
+                a[j] = step<KIND>(a[j], a[(j + 1) % kAcc], a[(j + 2) % kAcc], j);
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int j = 0; j < kAcc; ++j) x ^= a[j];
+    if (x == magic) sink[0] = x;
+}
+
+__global__ void __launch_bounds__(512) l2_probe_kernel(const uint4 *__restrict__ buf, int64_t n16,
+                                                      int reps, uint32_t magic, uint32_t *sink)
+{
+    uint32_t x = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+            const uint4 v = __ldcg(buf + i);
+            x ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    if (x == magic) sink[0] = x;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
+}
+
+template <class Launch>
+int time_best(Launch launch, cudaStream_t st, int n_runs, double *best_ms)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return MUCA_PROBE_ERR_CUDA;
+    }
+    int rc = MUCA_PROBE_OK;
+    *best_ms = 0.0;
+    launch();  // untimed: loads the module, warms the clocks and the cache
+    for (int r = 0; r < n_runs && rc == MUCA_PROBE_OK; ++r) {
+        float ms = 0.f;
+        if (cudaEventRecord(e0, st) != cudaSuccess) rc = MUCA_PROBE_ERR_CUDA;
+        launch();
+        if (rc == MUCA_PROBE_OK && (cudaGetLastError() != cudaSuccess ||
+                                    cudaEventRecord(e1, st) != cudaSuccess ||
+                                    cudaEventSynchronize(e1) != cudaSuccess ||
+                                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = MUCA_PROBE_ERR_CUDA;
+        if (rc == MUCA_PROBE_OK && (r == 0 || ms < *best_ms)) *best_ms = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int muca_probe_int(int32_t kind, int32_t iters, double *ops_per_s, double *ms, void *stream)
+{
+    if (kind < 0 || kind > 3 || iters < 1 || !ops_per_s) return MUCA_PROBE_ERR_INVALID_ARG;
+    const int nsm = sm_count();
+    if (nsm <= 0) return MUCA_PROBE_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t *sink = nullptr;
+    if (cudaMalloc(&sink, sizeof(uint32_t)) != cudaSuccess) return MUCA_PROBE_ERR_CUDA;
+    const int blocks = nsm * kProbeBlocksPerSm;
+    auto launch = [&]() {
+        const uint32_t seed = 12345u, magic = 0x2F6A3C1Du;
+        switch (kind) {
+        case 0: int_probe_kernel<0><<<blocks, kProbeThreads, 0, st>>>(seed, iters, magic, sink); break;
+        case 1: int_probe_kernel<1><<<blocks, kProbeThreads, 0, st>>>(seed, iters, magic, sink); break;
+        case 2: int_probe_kernel<2><<<blocks, kProbeThreads, 0, st>>>(seed, iters, magic, sink); break;
+        default: int_probe_kernel<3><<<blocks, kProbeThreads, 0, st>>>(seed, iters, magic, sink); break;
+        }
+    };
+    double best = 0.0;
+    int rc = time_best(launch, st, 5, &best);
+    cudaFree(sink);
+    if (rc != MUCA_PROBE_OK) return rc;
+    const double ops = (double)blocks * kProbeThreads * (double)iters * kUnroll * kAcc;
+    *ops_per_s = best > 0.0 ? ops / (best * 1e-3) : 0.0;
+    if (ms) *ms = best;
+    return MUCA_PROBE_OK;
+}
+
+int muca_probe_l2_read(int64_t bytes, int32_t reps, double *bytes_per_s, double *ms, void *stream)
+{
+    if (bytes < 16 || (bytes & 15) || reps < 1 || !bytes_per_s) return MUCA_PROBE_ERR_INVALID_ARG;
+    const int nsm = sm_count();
+    if (nsm <= 0) return MUCA_PROBE_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint4 *buf = nullptr;
+    uint32_t *sink = nullptr;
+    if (cudaMalloc(&buf, (size_t)bytes) != cudaSuccess) return MUCA_PROBE_ERR_CUDA;
+    if (cudaMalloc(&sink, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemsetAsync(buf, 0x5A, (size_t)bytes, st) != cudaSuccess) {
+        cudaFree(buf);
+        if (sink) cudaFree(sink);
+        return MUCA_PROBE_ERR_CUDA;
+    }
+    const int64_t n16 = bytes / 16;
+    const int blocks = nsm * 4;
+    auto launch = [&]() {
+        l2_probe_kernel<<<blocks, 512, 0, st>>>(buf, n16, reps, 0x6B1D2E3Fu, sink);
+    };
+    double best = 0.0;
+    int rc = time_best(launch, st, 5, &best);
+    cudaFree(buf);
+    cudaFree(sink);
+    if (rc != MUCA_PROBE_OK) return rc;
+    *bytes_per_s = best > 0.0 ? (double)bytes * reps / (best * 1e-3) : 0.0;
+    if (ms) *ms = best;
+    return MUCA_PROBE_OK;
+}
+
+}  // extern "C"

@@ -40,10 +40,16 @@ struct Group {
     int recursion = MUCA_REC_PLAIN;  // weight recursion (muca_set_recursion)
     std::vector<double> acc;         // its accumulated pair weights, max(nE - 1, 1)
     double flat[3] = {0.0, 0.0, 0.0};  // flatness of the histogram of the last update
+    // the active E_Delta window [win_lo, win_hi] (bins, relative to e_min) that
+    // the walkers move in, and its growth rule (muca_set_window; grow_flat = 0:
+    // fixed)
+    int win_lo = 0, win_hi = 0, grow_step = 0;
+    double grow_flat = 0.0;
+    bool flat_full = false;  // the last update's histogram was taken over all nE bins
     std::vector<uint32_t> injected;  // logical table given by muca_set_table (empty if none)
     uint32_t *h_thr = nullptr;       // pinned copy of the table allocation
     unsigned long long *h_hist = nullptr;  // pinned [nE]
-    // every walker's E_Delta lies in [e_min, e_max] (required before sweeping)
+    // every walker's E_Delta lies in the active window (required before sweeping)
     bool in_window = false;
     // kernel configuration
     int residency = MUCA_RES_GLOBAL;
@@ -113,7 +119,8 @@ int fail(muca_ctx *ctx, int code, const char *fmt, ...)
 // ---------------------------------------------------------------------------
 // Acceptance thresholds (Sec. II weights, built in FP64):
 //   x = -beta dE_J + (lnW[E + d] - lnW[E]);  thr = 2^31 if x >= 0,
-//   else floor(exp(x) 2^31); thr = 0 when E + d leaves the window.
+//   else floor(exp(x) 2^31); thr = 0 when E + d leaves the window (the
+//   group's active window [lo, hi], bins relative to e_min).
 // The arithmetic is written out exactly as it must round (the library is built
 // with -ffp-contract=off, so no multiply-add is fused).
 // ---------------------------------------------------------------------------
@@ -125,17 +132,17 @@ inline uint32_t thr_of(double x)
     return t >= 2147483648.0 ? 0x80000000u : (uint32_t)t;
 }
 
-inline uint32_t table_entry(double beta, const double *lnW, int nE, int e, int d, int dej)
+inline uint32_t table_entry(double beta, const double *lnW, int lo, int hi, int e, int d, int dej)
 {
     const int en = e + d;
-    if (en < 0 || en >= nE) return 0u;
+    if (en < lo || en > hi) return 0u;
     const double x = -(beta * (double)dej) + (lnW[en] - lnW[e]);
     return thr_of(x);
 }
 
 inline uint32_t thr_entry(const Group &g, int e, int d, int dej)
 {
-    return table_entry(g.beta, g.lnW.data(), g.nE, e, d, dej);
+    return table_entry(g.beta, g.lnW.data(), g.win_lo, g.win_hi, e, d, dej);
 }
 
 template <class F>
@@ -162,7 +169,8 @@ void build_packed(Group &g)
     std::memset(T, 0, table_rows(g.nE) * kRow * sizeof(uint32_t));
     uint32_t *E0 = T + (size_t)kGuard * kRow;
     uint32_t d0[kBlk];
-    for (int k = 0; k < kBlk; ++k) d0[k] = thr_entry(g, 0, 0, 2 * k - 12);
+    // d = 0 keeps E_Delta: the same entries in every row (taken in the window)
+    for (int k = 0; k < kBlk; ++k) d0[k] = thr_entry(g, g.win_lo, 0, 2 * k - 12);
     parallel_rows(g.nE, [&g, E0, &d0](int b, int e_end) {
         for (int e = b; e < e_end; ++e) {
             uint32_t *row = E0 + (size_t)e * kRow;
@@ -238,13 +246,20 @@ void weight_update(int kind, int nE, const unsigned long long *H, double *lnW, d
     for (int e = 0; e + 1 < nE; ++e) lnW[e + 1] = lnW[e] + r[e];
 }
 
-// The weight update of one iteration of group g on its merged histogram,
-// after recording the histogram's flatness.
+// The weight update of one iteration of group g on its merged histogram:
+// the histogram's flatness over the active window is recorded, the weight
+// recursion runs over all nE bins, and then the adaptive window grows when
+// the histogram was flat over it.  Growth (the adaptive window of the weight
+// iteration): by grow_step bins on each side, clamped to [e_min, e_max],
+// after an iteration with min H / mean H >= grow_flat over the window
+// (mean H = sum H / bins); a new bin starts from the weight of the old edge
+// next to it, and the accumulated weights of the pairs that contain a new
+// bin start from 0.
 void update_lnW(Group &g)
 {
     unsigned long long lo = ~0ull, hi = 0, sum = 0;
     int64_t hit = 0;
-    for (int e = 0; e < g.nE; ++e) {
+    for (int e = g.win_lo; e <= g.win_hi; ++e) {
         const unsigned long long h = g.h_hist[e];
         lo = std::min(lo, h);
         hi = std::max(hi, h);
@@ -254,12 +269,26 @@ void update_lnW(Group &g)
     if (sum == 0) {
         g.flat[0] = g.flat[1] = g.flat[2] = 0.0;
     } else {
-        const double mean = (double)sum / g.nE;
+        const double mean = (double)sum / (double)(g.win_hi - g.win_lo + 1);
         g.flat[0] = (double)lo / mean;
         g.flat[1] = (double)hi / mean;
         g.flat[2] = (double)hit;
     }
     weight_update(g.recursion, g.nE, g.h_hist, g.lnW.data(), g.acc.data());
+    const bool full = g.win_lo == 0 && g.win_hi == g.nE - 1;
+    g.flat_full = full;
+    if (g.grow_flat > 0.0 && !full && g.flat[0] >= g.grow_flat) {
+        const int lo_new = std::max(0, g.win_lo - g.grow_step);
+        const int hi_new = std::min(g.nE - 1, g.win_hi + g.grow_step);
+        for (int e = lo_new; e < g.win_lo; ++e) g.lnW[e] = g.lnW[g.win_lo];
+        for (int e = g.win_hi + 1; e <= hi_new; ++e) g.lnW[e] = g.lnW[g.win_hi];
+        if (g.recursion == MUCA_REC_ACCUMULATED) {
+            for (int e = lo_new; e < g.win_lo; ++e) g.acc[e] = 0.0;
+            for (int e = g.win_hi; e < hi_new; ++e) g.acc[e] = 0.0;
+        }
+        g.win_lo = lo_new;
+        g.win_hi = hi_new;
+    }
 }
 
 GroupDev dev_of(const Group &g)
@@ -847,6 +876,8 @@ int muca_init(const muca_group *groups, int n_groups, const muca_options *opt, v
             g.e_max = groups[i].e_max < 0 ? g.V : groups[i].e_max;
             g.spec.e_max = g.e_max;
             g.nE = g.e_max - g.e_min + 1;
+            g.win_lo = 0;
+            g.win_hi = g.nE - 1;
             g.T = groups[i].T;
             g.beta = 1.0 / g.T;
             g.walker0 = w0 + (uint32_t)lo;
@@ -985,6 +1016,52 @@ int muca_get_flatness(muca_ctx *ctx, int group, double *out)
     return MUCA_OK;
 }
 
+int muca_set_window(muca_ctx *ctx, int group, int32_t lo, int32_t hi, double grow_flat,
+                    int32_t grow_step)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    Group &g = ctx->g[group];
+    if (lo < g.e_min || hi > g.e_max || lo > hi)
+        return fail(ctx, MUCA_ERR_INVALID_ARG, "set_window: [%d, %d] not inside [%d, %d]", lo, hi,
+                    g.e_min, g.e_max);
+    if (!(grow_flat >= 0.0) || !std::isfinite(grow_flat) || (grow_flat > 0.0 && grow_step < 1))
+        return fail(ctx, MUCA_ERR_INVALID_ARG, "set_window: grow_flat %g, grow_step %d", grow_flat,
+                    grow_step);
+    std::vector<int32_t> t((size_t)3 * g.Wpad);
+    CK(cudaStreamSynchronize(ctx->stream));  // a graph's host node may still update
+    CK(cudaMemcpy(t.data(), g.tal, t.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int w = 0; w < g.W; ++w) {
+        const int ed = t[(size_t)g.Wpad + w];
+        if (ed < lo || ed > hi)
+            return fail(ctx, MUCA_ERR_WINDOW, "set_window: walker %d has E_Delta=%d outside [%d, %d]",
+                        w, ed, lo, hi);
+    }
+    g.win_lo = lo - g.e_min;
+    g.win_hi = hi - g.e_min;
+    g.grow_flat = grow_flat;
+    g.grow_step = grow_flat > 0.0 ? grow_step : 0;
+    g.in_window = true;
+    g.injected.clear();
+    build_packed(g);
+    rc = upload_table(ctx, g);
+    if (rc != MUCA_OK) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int muca_get_window(muca_ctx *ctx, int group, int32_t *out)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (!out) return fail(ctx, MUCA_ERR_INVALID_ARG, "out is NULL");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const Group &g = ctx->g[group];
+    out[0] = g.e_min + g.win_lo;
+    out[1] = g.e_min + g.win_hi;
+    return MUCA_OK;
+}
+
 int muca_iterate(muca_ctx *ctx, int32_t max_iters, int32_t sweeps_per_iter, double flat_min,
                  int32_t *n_done)
 {
@@ -1002,7 +1079,7 @@ int muca_iterate(muca_ctx *ctx, int32_t max_iters, int32_t sweeps_per_iter, doub
         if (rc != MUCA_OK) return rc;
         *n_done = it + 1;
         bool flat = true;
-        for (const auto &g : ctx->g) flat = flat && g.flat[0] >= flat_min;
+        for (const auto &g : ctx->g) flat = flat && g.flat[0] >= flat_min && g.flat_full;
         if (flat) break;
     }
     return MUCA_OK;
@@ -1265,7 +1342,7 @@ int muca_build_table(int32_t L, double T, int32_t e_min, int32_t e_max, const do
         for (int d = -1; d <= 1; ++d)
             for (int dej = -12; dej <= 12; ++dej)
                 out[((size_t)e * 3 + (d + 1)) * MUCA_NK + (dej + 12)] =
-                    table_entry(beta, lnW, nE, e, d, dej);
+                    table_entry(beta, lnW, 0, nE - 1, e, d, dej);
     return MUCA_OK;
 }
 
@@ -1332,7 +1409,7 @@ int muca_set_state(muca_ctx *ctx, int group, const int8_t *spins)
     CK(cudaStreamSynchronize(ctx->stream));
     for (int w = 0; w < g.W; ++w) {
         const int ed = t[(size_t)g.Wpad + w];
-        if (ed < g.e_min || ed > g.e_max) {
+        if (ed < g.e_min + g.win_lo || ed > g.e_min + g.win_hi) {
             // put the previous state back
             CK(cudaMemcpyAsync(g.spins, old_spins.data(), old_spins.size() * sizeof(uint32_t),
                                cudaMemcpyHostToDevice, ctx->stream));
@@ -1340,7 +1417,7 @@ int muca_set_state(muca_ctx *ctx, int group, const int8_t *spins)
                                cudaMemcpyHostToDevice, ctx->stream));
             CK(cudaStreamSynchronize(ctx->stream));
             return fail(ctx, MUCA_ERR_WINDOW, "walker %d: E_Delta=%d outside [%d, %d]", w, ed,
-                        g.e_min, g.e_max);
+                        g.e_min + g.win_lo, g.e_min + g.win_hi);
         }
     }
     g.in_window = true;
@@ -1370,7 +1447,8 @@ int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walke
 // then per group lnW[nE], acc[max(nE - 1, 1)], hist[nE], tallies[3][Wpad],
 // spins[V][Wpad].  Formats 02 (no shard record: every walker of the group)
 // and 01 (neither the shard, the recursion nor acc) are still read.
-static const char kMagic[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '3'};
+static const char kMagic[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '4'};
+static const char kMagic03[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '3'};
 static const char kMagic02[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '2'};
 static const char kMagic01[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '1'};
 
@@ -1394,6 +1472,11 @@ int muca_checkpoint(muca_ctx *ctx, const char *path)
     for (auto &g : ctx->g) {
         const int32_t shard[2] = {(int32_t)g.walker0, g.W};
         ok = ok && std::fwrite(shard, sizeof shard, 1, f) == 1;
+    }
+    for (auto &g : ctx->g) {
+        const int32_t win[3] = {g.e_min + g.win_lo, g.e_min + g.win_hi, g.grow_step};
+        ok = ok && std::fwrite(win, sizeof win, 1, f) == 1;
+        ok = ok && std::fwrite(&g.grow_flat, sizeof g.grow_flat, 1, f) == 1;
     }
     for (auto &g : ctx->g) {
         if (!ok) break;
@@ -1429,7 +1512,8 @@ int muca_restore(muca_ctx *ctx, const char *path)
     uint64_t sweep = 0;
     int32_t ng = 0;
     bool ok = std::fread(magic, 1, 8, f) == 8;
-    const bool v3 = ok && std::memcmp(magic, kMagic, 8) == 0;
+    const bool v4 = ok && std::memcmp(magic, kMagic, 8) == 0;
+    const bool v3 = v4 || (ok && std::memcmp(magic, kMagic03, 8) == 0);
     const bool v2 = v3 || (ok && std::memcmp(magic, kMagic02, 8) == 0);
     ok = ok && (v2 || std::memcmp(magic, kMagic01, 8) == 0);
     ok = ok && std::fread(&seed, sizeof seed, 1, f) == 1;
@@ -1453,6 +1537,23 @@ int muca_restore(muca_ctx *ctx, const char *path)
         if (v3) ok = ok && std::fread(shard, sizeof shard, 1, f) == 1;
         ok = ok && shard[1] == g.W && (!v3 || (uint32_t)shard[0] == g.walker0);
     }
+    // the active window and its growth rule: written by format 04; earlier
+    // formats ran in the fixed window [e_min, e_max]
+    struct Win {
+        int32_t lo, hi, step;
+        double flat;
+    };
+    std::vector<Win> wins;
+    for (auto &g : ctx->g) {
+        int32_t w3[3] = {g.e_min, g.e_max, 0};
+        double flat = 0.0;
+        if (v4)
+            ok = ok && std::fread(w3, sizeof w3, 1, f) == 1 &&
+                 std::fread(&flat, sizeof flat, 1, f) == 1;
+        ok = ok && w3[0] >= g.e_min && w3[1] <= g.e_max && w3[0] <= w3[1] && flat >= 0.0 &&
+             std::isfinite(flat) && (flat == 0.0 || w3[2] >= 1);
+        wins.push_back({w3[0], w3[1], w3[2], flat});
+    }
     if (!ok) {
         std::fclose(f);
         return fail(ctx, MUCA_ERR_INVALID_ARG, "restore: %s does not match this context", path);
@@ -1475,7 +1576,12 @@ int muca_restore(muca_ctx *ctx, const char *path)
         g.lnW = lnW;
         g.acc = acc;
         g.recursion = recs[gi];
+        g.win_lo = wins[gi].lo - g.e_min;
+        g.win_hi = wins[gi].hi - g.e_min;
+        g.grow_step = wins[gi].step;
+        g.grow_flat = wins[gi].flat;
         g.flat[0] = g.flat[1] = g.flat[2] = 0.0;
+        g.flat_full = false;
         g.injected.clear();
         g.in_window = true;
         if (cudaMemcpy(g.hist, h.data(), h.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||

@@ -515,7 +515,7 @@ cudaError_t prepare_scan_kernel(int L, size_t smem_bytes)
 {
     const ScanKernel k = scan_kernel_of(L);
     if (!k) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    return raise_smem_limit((const void *)k, smem_bytes);
 }
 
 cudaError_t launch_sweeps_scan(int L, const GroupDev *groups_dev, const BlockDesc *blocks_dev,

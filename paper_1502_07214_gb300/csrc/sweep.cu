@@ -43,6 +43,9 @@
 //      (its y-1 neighbour is the row just finished).
 // Sizes with L % 4 == 0 up to 48 use this path; any other L uses a plain
 // per-site path with the same results.
+#include <map>
+#include <mutex>
+#include <utility>
 #include <cstdint>
 
 #include "muca_internal.h"
@@ -1323,36 +1326,49 @@ int max_smem_per_block()
     return v;
 }
 
+// A kernel's dynamic shared-memory limit belongs to the process (per device),
+// not to a context: every context that launches the kernel needs a limit at
+// least as large as its own blocks use, so the limit is only ever raised.
+cudaError_t raise_smem_limit(const void *func, size_t smem_bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = set[{dev, func}];
+    if (smem_bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e == cudaSuccess) cur = smem_bytes;
+    return e;
+}
+
 cudaError_t prepare_smem_kernel(size_t smem_bytes)
 {
-    cudaError_t e = cudaFuncSetAttribute(sweep_smem_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
+    cudaError_t e = raise_smem_limit((const void *)sweep_smem_kernel<true>, smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sweep_smem_kernel<false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    return raise_smem_limit((const void *)sweep_smem_kernel<false>, smem_bytes);
 }
 
 cudaError_t prepare_global_kernel(size_t smem_bytes)
 {
-    cudaError_t e = cudaFuncSetAttribute(sweep_global_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
+    cudaError_t e = raise_smem_limit((const void *)sweep_global_kernel<true>, smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(sweep_global_kernel<false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    return raise_smem_limit((const void *)sweep_global_kernel<false>, smem_bytes);
 }
 
 size_t ws_bytes_for(int slots) { return (size_t)slots * kWsWords * sizeof(uint32_t); }
 
 cudaError_t prepare_ws_kernel(size_t smem_bytes, bool wide)
 {
-    cudaError_t e = cudaFuncSetAttribute(wide ? sweep_ws_kernel<true, true> : sweep_ws_kernel<true, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
+    cudaError_t e = raise_smem_limit(
+        wide ? (const void *)sweep_ws_kernel<true, true> : (const void *)sweep_ws_kernel<true, false>,
+        smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(wide ? sweep_ws_kernel<false, true> : sweep_ws_kernel<false, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    return raise_smem_limit(wide ? (const void *)sweep_ws_kernel<false, true>
+                                 : (const void *)sweep_ws_kernel<false, false>,
+                            smem_bytes);
 }
 
 cudaError_t launch_sweeps_ws(const GroupDev *groups_dev, const BlockDesc *blocks_dev, int n_blocks,

@@ -66,6 +66,10 @@ SIGNATURES = {
     "muca_set_recursion": [_P, _I32],
     "muca_get_flatness": [_P, ctypes.c_int, _P],
     "muca_iterate": [_P, _I32, _I32, _D, _P],
+    "muca_set_window": [_P, ctypes.c_int, _I32, _I32, _D, _I32],
+    "muca_probe_int": [_I32, _I32, _P, _P, _P],
+    "muca_probe_l2_read": [_I64, _I32, _P, _P, _P],
+    "muca_get_window": [_P, ctypes.c_int, _P],
     "muca_reweight": [_P, _P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _P, _I32, _I32,
                       _P, _P],
     "muca_reweight_noalloc": [_P, _P, _P, _I64, _I32, _I64, _P, _I32, _I32, _D, _I32, _P, _I32,
@@ -134,6 +138,28 @@ def _stream_ptr(stream):
         import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def probe_int(kind, iters=2048, stream=None):
+    """Integer instruction rate of one probe kind (``muca_probe_int``):
+    (updates per second, best launch in ms)."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib().muca_probe_int(int(kind), int(iters), ctypes.byref(ops), ctypes.byref(ms),
+                              _stream_ptr(stream))
+    if rc != 0:
+        raise MucaError(ERR_CUDA if rc == -2 else ERR_INVALID_ARG, f"muca_probe_int: {rc}")
+    return ops.value, ms.value
+
+
+def probe_l2_read(n_bytes=32 << 20, reps=64, stream=None):
+    """L2 read bandwidth over a buffer of n_bytes (``muca_probe_l2_read``):
+    (bytes per second, best launch in ms)."""
+    bw, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib().muca_probe_l2_read(int(n_bytes), int(reps), ctypes.byref(bw), ctypes.byref(ms),
+                                  _stream_ptr(stream))
+    if rc != 0:
+        raise MucaError(ERR_CUDA if rc == -2 else ERR_INVALID_ARG, f"muca_probe_l2_read: {rc}")
+    return bw.value, ms.value
 
 
 def build_table(L, T, e_min, e_max, lnW):
@@ -239,14 +265,33 @@ class Context:
 
     def get_flatness(self, g):
         """(min H / mean H, max H / mean H, bins hit) of the histogram merged
-        by the last weight update of group g."""
+        by the last weight update of group g, over its active window."""
         out = np.zeros(3)
         self._c(lib().muca_get_flatness(self._ctx, g, _np_ptr(out)))
         return out
 
+    def set_window(self, g, lo, hi, grow_flat=0.0, grow_step=0):
+        """Active E_Delta window [lo, hi] of group g, growing by grow_step bins
+        on each side after an iteration whose histogram has min H / mean H >=
+        grow_flat over it (``muca_set_window``; grow_flat = 0: fixed)."""
+        self._c(lib().muca_set_window(self._ctx, g, int(lo), int(hi), float(grow_flat),
+                                      int(grow_step)))
+
+    def get_window(self, g):
+        out = np.zeros(2, dtype=np.int32)
+        self._c(lib().muca_get_window(self._ctx, g, _np_ptr(out)))
+        return int(out[0]), int(out[1])
+
+    def walker_range(self, g):
+        """(min, max) of the current E_Delta of group g's walkers."""
+        tal = np.zeros((self.specs[g]["n_walkers"], 3), dtype=np.int32)
+        self._c(lib().muca_get_state(self._ctx, g, None, _np_ptr(tal)))
+        return int(tal[:, 1].min()), int(tal[:, 1].max())
+
     def iterate(self, max_iters, sweeps_per_iter, flat_min):
         """Weight iterations until every group's min H / mean H >= flat_min
-        (at most max_iters); returns the number of iterations run."""
+        over a window that is its whole [e_min, e_max] (at most max_iters);
+        returns the number of iterations run."""
         n = ctypes.c_int32(0)
         self._c(lib().muca_iterate(self._ctx, int(max_iters), int(sweeps_per_iter),
                                    float(flat_min), ctypes.byref(n)))

@@ -55,6 +55,19 @@ def host_merge_update(hist_local, lnW, all_reduce, kind=muca.REC_PLAIN, acc=None
     return merged
 
 
+def walker_range(ctx, g, all_reduce_max):
+    """(min, max) of the current E_Delta over the walkers of group g on every
+    rank: the window that an adaptive run (``Context.set_window``) starts from
+    must be the same on every shard.  ``all_reduce_max`` takes the maximum of
+    a CPU int64 tensor in place over the ranks."""
+    import torch
+
+    lo, hi = ctx.walker_range(g)
+    t = torch.tensor([-lo, hi], dtype=torch.int64)
+    all_reduce_max(t)
+    return -int(t[0]), int(t[1])
+
+
 def shard_range(n_walkers, rank, count):
     """Walkers [lo, hi) of a group of n_walkers held by shard rank of count
     (the rule of ``muca_options.shard_rank / shard_count``)."""

@@ -1,5 +1,5 @@
-"""The C ABI library loads and exports every symbol include/muca.h declares
-(no GPU needed: only dlopen/dlsym, no compute call)."""
+"""The C ABI library loads and exports every symbol the headers in include/
+declare (no GPU needed: only dlopen/dlsym, no compute call)."""
 import ctypes
 import os
 import re
@@ -9,16 +9,25 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
+HEADERS = ("muca.h", "muca_probe.h")
+
+
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "muca.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(muca_[a-z_0-9]+)\s*\(", text)))
+    assert sorted(HEADERS) == sorted(f for f in os.listdir(os.path.join(ROOT, "include"))
+                                     if f.endswith(".h"))
+    names = set()
+    for h in HEADERS:
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(muca_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared_symbols()
     for n in ("muca_init", "muca_sweep_iter", "muca_merge_update", "muca_reweight",
-              "muca_run_graph", "muca_destroy"):
+              "muca_run_graph", "muca_destroy", "muca_set_window", "muca_probe_int",
+              "muca_probe_l2_read"):
         assert n in names
 
 

@@ -70,26 +70,38 @@ def test_iterate_until_flat(rec):
 def _head(b):
     import ctypes
 
-    assert b[:8] == b"MUCABC03"
+    assert b[:8] == b"MUCABC04"
     return 8 + 4 + 8 + 4 + ctypes.sizeof(muca().Group)  # magic, seed, sweep, n_groups, group
+
+
+# one group's records after the header in format 04: recursion (int32), shard
+# (2 x int32), window (3 x int32 + FP64)
+REC, SHARD, WIN = 4, 8, 20
 
 
 def checkpoint_v01(src, dst, n_e):
     """The same checkpoint in the earliest format (one group): magic 01, no
-    recursion field, no shard record, no accumulated pair weights."""
+    recursion field, no shard or window record, no accumulated pair weights."""
     b = open(src, "rb").read()
     head = _head(b)
-    rest = b[head + 4 + 8:]    # without the recursion field and the shard record
+    rest = b[head + REC + SHARD + WIN:]  # without the recursion, shard and window records
     lnw = rest[:8 * n_e]
     rest = rest[8 * n_e + 8 * max(n_e - 1, 1):]  # without acc
     open(dst, "wb").write(b"MUCABC01" + b[8:head] + lnw + rest)
 
 
 def checkpoint_v02(src, dst):
-    """The same checkpoint in format 02 (one group): no shard record."""
+    """The same checkpoint in format 02 (one group): no shard or window record."""
     b = open(src, "rb").read()
     head = _head(b)
-    open(dst, "wb").write(b"MUCABC02" + b[8:head + 4] + b[head + 4 + 8:])
+    open(dst, "wb").write(b"MUCABC02" + b[8:head + REC] + b[head + REC + SHARD + WIN:])
+
+
+def checkpoint_v03(src, dst):
+    """The same checkpoint in format 03 (one group): no window record."""
+    b = open(src, "rb").read()
+    head = _head(b)
+    open(dst, "wb").write(b"MUCABC03" + b[8:head + REC + SHARD] + b[head + REC + SHARD + WIN:])
 
 
 def test_checkpoint_carries_the_recursion(tmp_path):
@@ -135,17 +147,20 @@ def test_checkpoint_carries_the_recursion(tmp_path):
         d.merge_update()
     np.testing.assert_array_equal(d.get_lnW(0), plain_lnW)
     d.close()
-    # format 02 (no shard record: every walker of the group) restores the run
-    v2 = str(tmp_path / "acc02.ckpt")
-    checkpoint_v02(path, v2)
-    e = m.Context(g, seed=seed)
-    e.restore(v2)
-    for _ in range(2):
-        e.sweep_iter(30)
-        e.merge_update()
-    np.testing.assert_array_equal(e.get_lnW(0), want_lnW)
-    np.testing.assert_array_equal(e.get_state(0)[0], want_spins)
-    e.close()
+    # formats 02 (no shard record: every walker of the group) and 03 (no
+    # window record: the fixed window [e_min, e_max]) restore the run
+    for name, conv in (("acc02.ckpt", checkpoint_v02), ("acc03.ckpt", checkpoint_v03)):
+        v = str(tmp_path / name)
+        conv(path, v)
+        e = m.Context(g, seed=seed)
+        e.restore(v)
+        assert e.get_window(0) == (0, L ** 3)
+        for _ in range(2):
+            e.sweep_iter(30)
+            e.merge_update()
+        np.testing.assert_array_equal(e.get_lnW(0), want_lnW)
+        np.testing.assert_array_equal(e.get_state(0)[0], want_spins)
+        e.close()
 
 
 def test_recursion_errors():
