@@ -154,10 +154,11 @@ int muca_sweep_iter(muca_ctx *ctx, int n_sweeps, int record);
 int muca_merge_update(muca_ctx *ctx);
 
 /* The batched form: n_iters x (sweeps_per_iter sweeps of all groups in one
- * launch, then merge + update of every group) captured once as a CUDA graph
- * (the FP64 update runs in a host node) and replayed.  Results are bit-identical
- * to calling muca_sweep_iter + muca_merge_update n_iters times.
- * Synchronises the stream. */
+ * launch, then merge + update of every group) captured by each call as one
+ * CUDA graph (the FP64 update runs in a host node) and launched once; the
+ * graph is destroyed before the call returns (its kernels carry the call's
+ * sweep counter).  Results are bit-identical to calling muca_sweep_iter +
+ * muca_merge_update n_iters times.  Synchronises the stream. */
 int muca_run_graph(muca_ctx *ctx, int n_iters, int sweeps_per_iter);
 
 /* ------------------------------------------------ weight-iteration variants */

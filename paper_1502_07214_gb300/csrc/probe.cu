@@ -16,8 +16,8 @@
 // blocks per SM, enough warps to hide each update's latency.
 //
 // L2 probe: a buffer smaller than the L2 is read whole, repeatedly, by every
-// SM with 16-byte loads that bypass L1 (ld.global.cg), after one untimed pass
-// that brings it into L2.
+// SM with 16-byte loads that bypass L1 (ld.global.cg), four in flight per
+// thread, after one untimed pass that brings it into L2.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,13 +64,23 @@ __global__ void __launch_bounds__(kProbeThreads) int_probe_kernel(uint32_t seed,
 __global__ void __launch_bounds__(512) l2_probe_kernel(const uint4 *__restrict__ buf, int64_t n16,
                                                       int reps, uint32_t magic, uint32_t *sink)
 {
+    // four independent 16-byte loads in flight per thread and step
     uint32_t x = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int r = 0; r < reps; ++r)
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int r = 0; r < reps; ++r) {
+        int64_t i = t;
+        for (; i + 3 * stride < n16; i += 4 * stride) {
+            const uint4 v0 = __ldcg(buf + i), v1 = __ldcg(buf + i + stride);
+            const uint4 v2 = __ldcg(buf + i + 2 * stride), v3 = __ldcg(buf + i + 3 * stride);
+            x ^= (v0.x ^ v0.y ^ v0.z ^ v0.w) ^ (v1.x ^ v1.y ^ v1.z ^ v1.w) ^
+                 (v2.x ^ v2.y ^ v2.z ^ v2.w) ^ (v3.x ^ v3.y ^ v3.z ^ v3.w);
+        }
+        for (; i < n16; i += stride) {
             const uint4 v = __ldcg(buf + i);
             x ^= v.x ^ v.y ^ v.z ^ v.w;
         }
+    }
     if (x == magic) sink[0] = x;
 }
 
