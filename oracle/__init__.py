@@ -39,6 +39,13 @@ def lib():
                                       P, P, P, P, P, i32, i32, i32, P]
         L.or_muca_run_win.argtypes = [i32, dbl, i32, i32, i32, u32, u32, i32, i32, i32,
                                       P, P, P, P, P, i32, i32, i32, P, i32, i32, dbl, i32, P]
+        L.or_energies_bonds.argtypes = [i32, P, P, P]
+        L.or_build_table_bonds.argtypes = [i32, dbl, i32, i32, i32, P, P]
+        L.or_sweeps_bonds.argtypes = [i32, P, i32, i32, i32, P, u32, u32, u64, i32, P, P, P, P,
+                                      i32]
+        L.or_muca_run_bonds.argtypes = [i32, dbl, i32, i32, i32, u32, u32, i32, i32, i32,
+                                        P, P, P, P, P, i32, i32, i32, P, i32, i32, dbl, i32, P,
+                                        P, i32]
         L.or_reweight.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
         L.or_reweight_q.argtypes = [P, P, P, i64, P, i32, i32, dbl, i32, P, i32, i32, P]
         L.or_find_peak.argtypes = [P, P, i64, i32, P, i32, i32, dbl, dbl, dbl, i32, i32, i32, P]
@@ -46,7 +53,8 @@ def lib():
                                       i32, P]
         for f in ("or_init_spins", "or_energies", "or_build_table", "or_sweeps",
                   "or_update_lnW", "or_update_lnW_acc", "or_muca_run", "or_muca_run_rec",
-                  "or_muca_run_win",
+                  "or_muca_run_win", "or_energies_bonds", "or_build_table_bonds",
+                  "or_sweeps_bonds", "or_muca_run_bonds",
                   "or_reweight", "or_reweight_q",
                   "or_find_peak", "or_equal_height"):
             getattr(L, f).restype = ctypes.c_int
@@ -111,6 +119,47 @@ def sweeps(L, e_min, e_max, thr, seed, walker_id, sweep0, n_sweeps, spins, talli
     return ts
 
 
+def _bonds(L, J, jmax=None):
+    J = np.ascontiguousarray(J, dtype=np.int8).reshape(L ** 3, 3)
+    if jmax is None:
+        jmax = max(1, int(np.abs(J.astype(np.int64)).max()))
+    return J, int(jmax)
+
+
+def energies_bonds(L, spins, J):
+    """(E_J, E_Delta, M) of the disordered model (reading R16 of muca_oracle.c);
+    J int8 [L^3][3]: couplings of the forward x, y, z bonds of each site."""
+    J, _ = _bonds(L, J)
+    spins = np.ascontiguousarray(spins, dtype=np.int8)
+    out = np.zeros(3, dtype=np.int64)
+    _ck(lib().or_energies_bonds(L, _p(spins), _p(J), _p(out)), "energies_bonds")
+    return out
+
+
+def build_table_bonds(L, T, jmax, e_min, e_max, lnW):
+    """Table [nE][3][24 jmax + 1] of the disordered model, index dE_J + 12 jmax."""
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    nE = e_max - e_min + 1
+    assert lnW.shape == (nE,)
+    thr = np.zeros((nE, 3, 24 * jmax + 1), dtype=np.uint32)
+    _ck(lib().or_build_table_bonds(L, T, jmax, e_min, e_max, _p(lnW), _p(thr)), "build_table_bonds")
+    return thr
+
+
+def sweeps_bonds(L, J, jmax, e_min, e_max, thr, seed, walker_id, sweep0, n_sweeps, spins,
+                 tallies, hist=None, record=False, check=False):
+    """or_sweeps of the disordered model; spins and tallies updated in place."""
+    J, jmax = _bonds(L, J, jmax)
+    assert spins.dtype == np.int8 and spins.flags.c_contiguous
+    assert tallies.dtype == np.int32 and tallies.flags.c_contiguous
+    thr = np.ascontiguousarray(thr, dtype=np.uint32)
+    ts = np.zeros((n_sweeps, 3), dtype=np.int32) if record else None
+    _ck(lib().or_sweeps_bonds(L, _p(J), jmax, e_min, e_max, _p(thr), seed, walker_id, sweep0,
+                              n_sweeps, _p(spins), _p(tallies), _p(hist), _p(ts), int(check)),
+        "sweeps_bonds")
+    return ts
+
+
 def update_lnW(H, lnW):
     H = np.ascontiguousarray(H, dtype=np.uint64)
     assert lnW.dtype == np.float64 and lnW.flags.c_contiguous
@@ -139,14 +188,16 @@ def flatness(H):
 
 def muca_run(L, T, n_walkers, seed, n_iter, sweeps_per_iter, n_meas=0, e_min=0, e_max=None,
              walker_id0=0, lnW=None, check=False, n_threads=None, want_spins=True, recursion=0,
-             acc=None, window=None, grow_flat=0.0, grow_step=0):
+             acc=None, window=None, grow_flat=0.0, grow_step=0, bonds=None, jmax=None):
     """A whole run of one (L, T) group; returns a dict of numpy arrays.
     recursion 0: lnW -= ln H; 1: the accumulated recursion, whose pair
     weights start from acc (zeros by default) and are returned as "acc".
     window (lo, hi): the walkers' active E_Delta window (reading R15 of
     muca_oracle.c), growing by grow_step bins on each side after an iteration
     whose histogram has min H / mean H >= grow_flat over it; "windows" holds
-    the window after every iteration.  Default: [e_min, e_max], fixed."""
+    the window after every iteration.  Default: [e_min, e_max], fixed.
+    bonds int8 [L^3][3]: the disordered model's couplings (reading R16), with
+    the table width of jmax (default: the largest |J|); None: the clean model."""
     V = L ** 3
     if e_max is None:
         e_max = V
@@ -161,10 +212,12 @@ def muca_run(L, T, n_walkers, seed, n_iter, sweeps_per_iter, n_meas=0, e_min=0, 
     ts = np.zeros((n_walkers, n_meas, 3), dtype=np.int32) if n_meas > 0 else None
     if n_threads is None:
         n_threads = os.cpu_count() or 1
-    _ck(lib().or_muca_run_win(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
-                              sweeps_per_iter, n_meas, _p(lnW), _p(hist), _p(spins), _p(tal),
-                              _p(ts), int(check), n_threads, int(recursion), _p(acc), int(lo),
-                              int(hi), float(grow_flat), int(grow_step), _p(wins)),
+    J, jm = (None, 0) if bonds is None else _bonds(L, bonds, jmax)
+    _ck(lib().or_muca_run_bonds(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
+                                sweeps_per_iter, n_meas, _p(lnW), _p(hist), _p(spins), _p(tal),
+                                _p(ts), int(check), n_threads, int(recursion), _p(acc), int(lo),
+                                int(hi), float(grow_flat), int(grow_step), _p(wins), _p(J),
+                                jm),
         "muca_run")
     return {"lnW": lnW, "hist": hist[:n_iter], "spins": spins, "tallies": tal, "ts": ts,
             "acc": acc, "windows": wins[:n_iter]}

@@ -50,6 +50,8 @@
  *   R13 the accumulated, error-weighted form of the weight recursion and its
  *       rule for empty bins are stated at or_update_lnW_acc.
  *   R15 the adaptive E_Delta window is stated at or_muca_run_win.
+ *   R16 the disordered model (quenched bond couplings) is stated at
+ *       or_energies_bonds.
  */
 #include "muca_oracle.h"
 
@@ -257,6 +259,147 @@ int or_sweeps(int L, int e_min, int e_max, const uint32_t *thr, uint32_t seed,
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Reading R16, the disordered model.  The paper's outlook applies the method */
+/* to the Blume-Capel model with bond disorder (its random-bond version) and  */
+/* names no distribution or strength.  Here every bond carries its own        */
+/* quenched coupling: E_J = -sum_<ij> J_ij s_i s_j, with J[3 i + mu] the       */
+/* coupling of the forward bond from site i in direction mu (x, y, z) and     */
+/* every J an integer in [-jmax, jmax] (jmax <= 8).  Integer couplings keep   */
+/* E_J an integer; a ratio r = J2 / J1 of a bimodal distribution is reached   */
+/* by scaling: couplings q J at temperature q T and field q Delta are the     */
+/* model at (J, T, Delta).  E_Delta, the weights W(E_Delta) and the           */
+/* reweighting in Delta are those of the clean model; all walkers of a group  */
+/* share one realisation.  J = 1 everywhere is the clean model.               */
+/* The acceptance table of R4 is indexed by dE_J in [-12 jmax, 12 jmax]:      */
+/* thr[(E - e_min) * 3 + d + 1][dE_J + 12 jmax], row length 24 jmax + 1.      */
+/* ------------------------------------------------------------------------ */
+static int bonds_ok(int L, const int8_t *J, int jmax)
+{
+    if (!J || jmax < 1 || jmax > OR_MAX_JMAX) return 0;
+    int64_t V = (int64_t)L * L * L;
+    for (int64_t k = 0; k < 3 * V; ++k)
+        if (J[k] < -jmax || J[k] > jmax) return 0;
+    return 1;
+}
+
+/* Coupling-weighted sum of the six neighbours of (x, y, z): the three forward
+ * bonds of the site and the forward bonds of its three backward neighbours. */
+static int bond_field(int L, const int8_t *s, const int8_t *J, int x, int y, int z)
+{
+    int64_t i = site_of(L, x, y, z);
+    int64_t xm = site_of(L, wrap(x - 1, L), y, z);
+    int64_t ym = site_of(L, x, wrap(y - 1, L), z);
+    int64_t zm = site_of(L, x, y, wrap(z - 1, L));
+    int h = 0;
+    h += J[3 * i + 0] * s[site_of(L, wrap(x + 1, L), y, z)];
+    h += J[3 * xm + 0] * s[xm];
+    h += J[3 * i + 1] * s[site_of(L, x, wrap(y + 1, L), z)];
+    h += J[3 * ym + 1] * s[ym];
+    h += J[3 * i + 2] * s[site_of(L, x, y, wrap(z + 1, L))];
+    h += J[3 * zm + 2] * s[zm];
+    return h;
+}
+
+int or_energies_bonds(int L, const int8_t *s, const int8_t *J, int64_t out[3])
+{
+    if (L < 2 || !s || !J || !out) return OR_ERR_ARG;
+    int64_t ej = 0, ed = 0, m = 0;
+    for (int z = 0; z < L; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                int64_t i = site_of(L, x, y, z);
+                int si = s[i];
+                ej -= J[3 * i + 0] * si * s[site_of(L, wrap(x + 1, L), y, z)];
+                ej -= J[3 * i + 1] * si * s[site_of(L, x, wrap(y + 1, L), z)];
+                ej -= J[3 * i + 2] * si * s[site_of(L, x, y, wrap(z + 1, L))];
+                ed += si * si;
+                m += si;
+            }
+    out[0] = ej;
+    out[1] = ed;
+    out[2] = m;
+    return OR_OK;
+}
+
+int or_build_table_bonds(int L, double T, int jmax, int e_min, int e_max, const double *lnW,
+                         uint32_t *thr)
+{
+    if (L < 2 || !(T > 0.0) || !lnW || !thr || jmax < 1 || jmax > OR_MAX_JMAX) return OR_ERR_ARG;
+    int64_t V = (int64_t)L * L * L;
+    if (e_min < 0 || e_max > V || e_min > e_max) return OR_ERR_ARG;
+    double beta = 1.0 / T;
+    int nE = e_max - e_min + 1, nj = 24 * jmax + 1;
+    for (int e = 0; e < nE; ++e)
+        for (int d = -1; d <= 1; ++d)
+            for (int dej = -12 * jmax; dej <= 12 * jmax; ++dej) {
+                uint32_t t;
+                int en = e + d;
+                if (en < 0 || en >= nE) {
+                    t = 0u;
+                } else {
+                    double x = -(beta * (double)dej) + (lnW[en] - lnW[e]);
+                    t = threshold_of(x);
+                }
+                thr[((int64_t)e * 3 + (d + 1)) * nj + (dej + 12 * jmax)] = t;
+            }
+    return OR_OK;
+}
+
+int or_sweeps_bonds(int L, const int8_t *J, int jmax, int e_min, int e_max, const uint32_t *thr,
+                    uint32_t seed, uint32_t walker_id, uint64_t sweep0, int n_sweeps,
+                    int8_t *spins, int32_t tallies[3], uint64_t *hist, int32_t *ts, int check)
+{
+    if (L < 2 || !thr || !spins || !tallies || n_sweeps < 0 || !bonds_ok(L, J, jmax))
+        return OR_ERR_ARG;
+    int nj = 24 * jmax + 1;
+    int64_t ej = tallies[0], ed = tallies[1], m = tallies[2];
+    if (ed < e_min || ed > e_max) return OR_ERR_WINDOW;
+    for (int k = 0; k < n_sweeps; ++k) {
+        uint64_t sweep = sweep0 + (uint64_t)k;
+        for (int z = 0; z < L; ++z)
+            for (int y = 0; y < L; ++y)
+                for (int x = 0; x < L; ++x) {
+                    int64_t i = site_of(L, x, y, z);
+                    uint32_t w = site_word(seed, walker_id, sweep, i, 0u);
+                    uint32_t b = w >> 31;
+                    uint32_t u = w & 0x7FFFFFFFu;
+                    int s = spins[i];
+                    int other[2], n = 0;
+                    for (int v = -1; v <= 1; ++v)
+                        if (v != s) other[n++] = v;
+                    int sp = other[b];
+                    int h = bond_field(L, spins, J, x, y, z);
+                    int dej = -(sp - s) * h;
+                    int d = sp * sp - s * s;
+                    int64_t en = ed + d;
+                    if (en < e_min || en > e_max) continue;
+                    uint32_t t = thr[((ed - e_min) * 3 + (d + 1)) * nj + (dej + 12 * jmax)];
+                    if (u < t) {
+                        spins[i] = (int8_t)sp;
+                        ej += dej;
+                        ed = en;
+                        m += sp - s;
+                    }
+                }
+        if (hist) hist[ed - e_min] += 1;
+        if (ts) {
+            ts[3 * (int64_t)k + 0] = (int32_t)ej;
+            ts[3 * (int64_t)k + 1] = (int32_t)ed;
+            ts[3 * (int64_t)k + 2] = (int32_t)m;
+        }
+        if (check) {
+            int64_t e[3];
+            or_energies_bonds(L, spins, J, e);
+            if (e[0] != ej || e[1] != ed || e[2] != m) return OR_ERR_TALLY;
+        }
+    }
+    tallies[0] = (int32_t)ej;
+    tallies[1] = (int32_t)ed;
+    tallies[2] = (int32_t)m;
+    return OR_OK;
+}
+
 int or_update_lnW(int nE, const uint64_t *H, double *lnW)
 {
     if (nE <= 0 || !H || !lnW) return OR_ERR_ARG;
@@ -317,6 +460,8 @@ int or_update_lnW_acc(int nE, const uint64_t *H, double *lnW, double *acc)
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int L, e_min, e_max, check;
+    const int8_t *J; /* couplings of the disordered model (R16), or NULL */
+    int jmax;
     const uint32_t *thr;
     uint32_t seed, walker_id0;
     uint64_t sweep0;
@@ -335,10 +480,14 @@ static void *sweep_job_run(void *arg)
     int64_t V = (int64_t)j->L * j->L * j->L;
     j->status = OR_OK;
     for (int w = j->w_begin; w < j->w_end; ++w) {
-        int rc = or_sweeps(j->L, j->e_min, j->e_max, j->thr, j->seed,
-                           j->walker_id0 + (uint32_t)w, j->sweep0, j->n_sweeps,
-                           j->spins + (int64_t)w * V, j->tallies + 3 * (int64_t)w, j->hist,
-                           j->ts ? j->ts + (int64_t)w * j->n_sweeps * 3 : NULL, j->check);
+        int8_t *sp = j->spins + (int64_t)w * V;
+        int32_t *tl = j->tallies + 3 * (int64_t)w;
+        int32_t *ts = j->ts ? j->ts + (int64_t)w * j->n_sweeps * 3 : NULL;
+        uint32_t id = j->walker_id0 + (uint32_t)w;
+        int rc = j->J ? or_sweeps_bonds(j->L, j->J, j->jmax, j->e_min, j->e_max, j->thr, j->seed,
+                                        id, j->sweep0, j->n_sweeps, sp, tl, j->hist, ts, j->check)
+                      : or_sweeps(j->L, j->e_min, j->e_max, j->thr, j->seed, id, j->sweep0,
+                                  j->n_sweeps, sp, tl, j->hist, ts, j->check);
         if (rc != OR_OK) {
             j->status = rc;
             return NULL;
@@ -433,9 +582,33 @@ int or_muca_run_win(int L, double T, int n_walkers, int e_min, int e_max, uint32
                     int recursion, double *acc, int win_lo, int win_hi, double grow_flat,
                     int grow_step, int32_t *win_iter)
 {
+    return or_muca_run_bonds(L, T, n_walkers, e_min, e_max, seed, walker_id0, n_iter,
+                             sweeps_per_iter, n_meas, lnW, hist_iter, spins_out, tallies_out, ts,
+                             check, n_threads, recursion, acc, win_lo, win_hi, grow_flat,
+                             grow_step, win_iter, NULL, 0);
+}
+
+/* The table of the run: the clean one (R4) or the disordered one (R16). */
+static void run_table(int L, double T, const int8_t *J, int jmax, int lo, int hi,
+                      const double *lnW, uint32_t *thr)
+{
+    if (J)
+        or_build_table_bonds(L, T, jmax, lo, hi, lnW, thr);
+    else
+        or_build_table(L, T, lo, hi, lnW, thr);
+}
+
+int or_muca_run_bonds(int L, double T, int n_walkers, int e_min, int e_max, uint32_t seed,
+                      uint32_t walker_id0, int n_iter, int sweeps_per_iter, int n_meas,
+                      double *lnW, uint64_t *hist_iter, int8_t *spins_out,
+                      int32_t *tallies_out, int32_t *ts, int check, int n_threads,
+                      int recursion, double *acc, int win_lo, int win_hi, double grow_flat,
+                      int grow_step, int32_t *win_iter, const int8_t *J, int jmax)
+{
     if (L < 2 || !(T > 0.0) || n_walkers < 1 || n_iter < 0 || sweeps_per_iter < 0 ||
         n_meas < 0 || !lnW || recursion < 0 || recursion > 1 || (recursion == 1 && !acc))
         return OR_ERR_ARG;
+    if (J && !bonds_ok(L, J, jmax)) return OR_ERR_ARG;
     int64_t V = (int64_t)L * L * L;
     if (e_min < 0 || e_max > V || e_min > e_max) return OR_ERR_ARG;
     if (win_lo < e_min || win_hi > e_max || win_lo > win_hi) return OR_ERR_ARG;
@@ -445,7 +618,8 @@ int or_muca_run_win(int L, double T, int n_walkers, int e_min, int e_max, uint32
     int a = win_lo - e_min, b = win_hi - e_min;
     int8_t *spins = (int8_t *)malloc((size_t)n_walkers * (size_t)V);
     int32_t *tal = (int32_t *)malloc((size_t)n_walkers * 3 * sizeof(int32_t));
-    uint32_t *thr = (uint32_t *)malloc((size_t)nE * 3 * OR_NK * sizeof(uint32_t));
+    const int nk = J ? 24 * jmax + 1 : OR_NK;
+    uint32_t *thr = (uint32_t *)malloc((size_t)nE * 3 * (size_t)nk * sizeof(uint32_t));
     uint64_t *hist = (uint64_t *)malloc((size_t)nE * sizeof(uint64_t));
     int rc = OR_OK;
     if (!spins || !tal || !thr || !hist) {
@@ -456,7 +630,10 @@ int or_muca_run_win(int L, double T, int n_walkers, int e_min, int e_max, uint32
         int8_t *s = spins + (int64_t)w * V;
         or_init_spins(L, seed, walker_id0 + (uint32_t)w, s);
         int64_t e[3];
-        or_energies(L, s, e);
+        if (J)
+            or_energies_bonds(L, s, J, e);
+        else
+            or_energies(L, s, e);
         if (e[1] < e_min + a || e[1] > e_min + b) {
             rc = OR_ERR_WINDOW;
             goto done;
@@ -470,6 +647,8 @@ int or_muca_run_win(int L, double T, int n_walkers, int e_min, int e_max, uint32
     memset(&proto, 0, sizeof proto);
     proto.L = L;
     proto.check = check;
+    proto.J = J;
+    proto.jmax = jmax;
     proto.thr = thr;
     proto.seed = seed;
     proto.walker_id0 = walker_id0;
@@ -479,7 +658,7 @@ int or_muca_run_win(int L, double T, int n_walkers, int e_min, int e_max, uint32
      * slice of lnW, and its slice of the histogram */
     proto.e_min = e_min + a;
     proto.e_max = e_min + b;
-    or_build_table(L, T, e_min + a, e_min + b, lnW + a, thr);
+    run_table(L, T, J, jmax, e_min + a, e_min + b, lnW + a, thr);
     for (int it = 0; it < n_iter; ++it) {
         memset(hist, 0, (size_t)nE * sizeof(uint64_t));
         proto.sweep0 = sweep;
@@ -514,7 +693,7 @@ int or_muca_run_win(int L, double T, int n_walkers, int e_min, int e_max, uint32
             win_iter[2 * it + 0] = e_min + a;
             win_iter[2 * it + 1] = e_min + b;
         }
-        or_build_table(L, T, e_min + a, e_min + b, lnW + a, thr);
+        run_table(L, T, J, jmax, e_min + a, e_min + b, lnW + a, thr);
     }
     if (n_meas > 0) {
         proto.sweep0 = sweep;

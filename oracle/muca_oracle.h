@@ -105,6 +105,25 @@ int or_muca_run_win(int L, double T, int n_walkers, int e_min, int e_max, uint32
                     int recursion, double *acc, int win_lo, int win_hi, double grow_flat,
                     int grow_step, int32_t *win_iter);
 
+/* The disordered model (reading R16 in the .c file): couplings J[3 i + mu]
+ * of the forward bonds (integers in [-jmax, jmax], 1 <= jmax <= OR_MAX_JMAX).
+ * The table has rows of 24 jmax + 1 entries, index
+ * [(E_Delta - e_min) * 3 + d + 1][dE_J + 12 jmax].  or_muca_run_bonds is
+ * or_muca_run_win with couplings (J = NULL: the clean model). */
+#define OR_MAX_JMAX 8
+int or_energies_bonds(int L, const int8_t *s, const int8_t *J, int64_t out[3]);
+int or_build_table_bonds(int L, double T, int jmax, int e_min, int e_max, const double *lnW,
+                         uint32_t *thr);
+int or_sweeps_bonds(int L, const int8_t *J, int jmax, int e_min, int e_max, const uint32_t *thr,
+                    uint32_t seed, uint32_t walker_id, uint64_t sweep0, int n_sweeps,
+                    int8_t *spins, int32_t tallies[3], uint64_t *hist, int32_t *ts, int check);
+int or_muca_run_bonds(int L, double T, int n_walkers, int e_min, int e_max, uint32_t seed,
+                      uint32_t walker_id0, int n_iter, int sweeps_per_iter, int n_meas,
+                      double *lnW, uint64_t *hist_iter, int8_t *spins_out,
+                      int32_t *tallies_out, int32_t *ts, int check, int n_threads,
+                      int recursion, double *acc, int win_lo, int win_hi, double grow_flat,
+                      int grow_step, int32_t *win_iter, const int8_t *J, int jmax);
+
 /* Time-series reweighting (Eq. 3) to each Delta_k of grid[n_grid], FP64 with
  * compensated sums.  Samples: e_j[n], e_d[n], m[n].  lnW[nE] indexed by
  * E_Delta - e_min.  out[n_grid][5] = <E_J>, <E_Delta>, C (Eq. 6),

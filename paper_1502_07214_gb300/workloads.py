@@ -82,5 +82,14 @@ def synthetic_series(L=REWEIGHT["L"], T=REWEIGHT["T"], n_walkers=REWEIGHT["n_wal
             delta_t)
 
 
+def random_bonds(L, j1, j2, seed, p2=0.5):
+    """A quenched bimodal bond realisation: int8 [L^3][3], the forward x, y,
+    z bond of every site independently j2 with probability p2, else j1
+    (integer couplings; the random-bond model with ratio r = j2 / j1)."""
+    rng = np.random.default_rng(seed)
+    pick = rng.random((L ** 3, 3)) < p2
+    return np.where(pick, j2, j1).astype(np.int8)
+
+
 def delta_grid(center, half_width=REWEIGHT["half_width"], n=REWEIGHT["n_grid"]):
     return center - half_width + (2.0 * half_width) * np.arange(n) / (n - 1)

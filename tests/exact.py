@@ -43,12 +43,26 @@ def state_energies(st, L):
     return ej, ed, m
 
 
-def joint_distribution(L, beta, lnW, e_min=0, values=(-1, 0, 1)):
-    """Exact P(E_J, E_Delta) of the ensemble exp(-beta E_J) W(E_Delta).
+def state_energies_bonds(st, L, J):
+    """(E_J, E_Delta, M) with a coupling per bond: E_J = -sum over the forward
+    bonds (i, mu) of J[i, mu] s_i s_{i+mu}."""
+    nb = forward_neighbours(L)
+    J = np.asarray(J, dtype=np.int64).reshape(L ** 3, 3)
+    ej = np.zeros(len(st), dtype=np.int64)
+    for mu in range(3):
+        ej -= (J[:, mu] * st * st[:, nb[:, mu]]).sum(axis=1)
+    ed = (st * st).sum(axis=1)
+    m = st.sum(axis=1)
+    return ej, ed, m
+
+
+def joint_distribution(L, beta, lnW, e_min=0, values=(-1, 0, 1), J=None):
+    """Exact P(E_J, E_Delta) of the ensemble exp(-beta E_J) W(E_Delta), with
+    one coupling per bond if J [L^3][3] is given (else J = 1).
 
     Returns a dict {(E_J, E_Delta): probability}."""
     st = all_states(L, values)
-    ej, ed, _ = state_energies(st, L)
+    ej, ed, _ = state_energies(st, L) if J is None else state_energies_bonds(st, L, J)
     logw = -beta * ej + np.asarray(lnW)[ed - e_min]
     w = np.exp(logw - logw.max())
     w /= w.sum()
