@@ -59,6 +59,8 @@ extern "C" {
 
 /* Number of logical threshold entries per (E_Delta, d): dE_J = -12 .. 12. */
 #define MUCA_NK 25
+/* Largest |coupling| of the disordered model (muca_set_bonds). */
+#define MUCA_MAX_JMAX 8
 
 typedef struct muca_ctx muca_ctx;
 
@@ -87,6 +89,9 @@ typedef struct {
                              prefix scan of bit masks, re-run from each accepted
                              move that changes E_Delta (L % 4 == 0, 4 <= L <= 64;
                              other sizes fall back to MUCA_RES_GLOBAL) */
+#define MUCA_RES_BONDS 5  /* the disordered model's kernel (muca_set_bonds): one thread
+                             per walker, couplings per bond; reported by
+                             muca_get_config, not selectable in muca_options */
 
 /* debug_flags bits */
 #define MUCA_DEBUG_TALLY_CHECK 1 /* recompute E_J, E_Delta, M after every sweep call */
@@ -237,6 +242,38 @@ int muca_get_flatness(muca_ctx *ctx, int group, double *out);
 int muca_set_window(muca_ctx *ctx, int group, int32_t lo, int32_t hi, double grow_flat,
                     int32_t grow_step);
 int muca_get_window(muca_ctx *ctx, int group, int32_t *out);
+
+/* The disordered model.  The paper's outlook applies the method to the
+ * Blume-Capel model with bond disorder (its random-bond version) without
+ * fixing a distribution; this is the library's reading of it.  Every bond
+ * carries a quenched integer coupling: E_J = -sum over the forward bonds
+ * (i, mu) of J[3 i + mu] s_i s_{i+mu}, the local field of a site weighs each
+ * of its six neighbours by the coupling of the bond between them.  E_Delta,
+ * W(E_Delta), the histograms, windows, weight recursions and the reweighting
+ * in Delta are the clean model's; every walker of the group shares the one
+ * realisation.  Integer couplings keep E_J an integer; a bimodal ratio
+ * r = J2 / J1 is reached by scaling (couplings q J at temperature q T and
+ * field q Delta are the model at J, T, Delta).
+ *   J      host int8 [L^3][3]: the couplings of the x, y, z forward bonds of
+ *          site i = x + L (y + L z), each in [-jmax, jmax]; NULL returns the
+ *          group to the clean model (J = 1)
+ *   jmax   1 .. MUCA_MAX_JMAX: the acceptance table covers
+ *          dE_J in [-12 jmax, 12 jmax] (rows of 24 jmax + 1 thresholds)
+ * The couplings are copied; the running tallies are recomputed from the
+ * current spins, the table is rebuilt from lnW, and the group's sweeps run
+ * the disordered model's kernel (MUCA_RES_BONDS) from then on.  muca_get_table
+ * and muca_set_table refuse such a group (MUCA_ERR_INVALID_ARG).
+ * MUCA_ERR_INVALID_ARG for a coupling or jmax out of range.  Synchronises the
+ * stream. */
+int muca_set_bonds(muca_ctx *ctx, int group, const int8_t *J, int32_t jmax);
+
+/* The disordered model's acceptance table on the host (no context):
+ *   out host uint32 [n_e][3][24 jmax + 1], index
+ *       [E_Delta - e_min][d + 1][dE_J + 12 jmax]
+ * with the thresholds of muca_build_table.  MUCA_ERR_INVALID_ARG for a bad
+ * size, window, jmax or a NULL array. */
+int muca_build_table_bonds(int32_t L, double T, int32_t jmax, int32_t e_min, int32_t e_max,
+                           const double *lnW, uint32_t *out);
 
 /* Weight iteration until the histograms are flat: up to max_iters iterations
  * of sweeps_per_iter sweeps followed by muca_merge_update; stops after the
@@ -417,11 +454,13 @@ int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walke
 
 /* Checkpoint / restore: spins, tallies, lnW, histograms, the weight
  * recursion with its accumulated pair weights, the active window with its
- * growth rule, sweep counters and the seed, to / from a file.  Philox is
+ * growth rule, the couplings of the disordered model, sweep counters and the
+ * seed, to / from a file.  Philox is
  * counter-based, so a restored run continues bit-identically.  restore
  * requires a context with the same groups and the same shard
  * (muca_options.shard_rank / shard_count); it also reads files of the earlier
- * formats without the window (the fixed window [e_min, e_max]), without the
+ * formats without the couplings (the clean model), without the window (the
+ * fixed window [e_min, e_max]), without the
  * shard record (every walker of a group) or without the recursion (plain
  * recursion, no accumulated weights). */
 int muca_checkpoint(muca_ctx *ctx, const char *path);

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libmuca.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["sweep.cu", "scan.cu", "reweight.cu", "reweight_noalloc.cu", "peak.cu", "runtime.cu",
-           "probe.cu"]
+           "probe.cu", "bonds.cu"]
 HEADERS = ["muca_internal.h", "philox.cuh", "scan_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",

@@ -39,6 +39,12 @@ struct GroupDev {
     unsigned long long *hist;   // [nE]
     const uint32_t *thrE;       // the row of E_Delta = e_min in the table allocation
     int32_t *ts;                // [cap][3][W] or nullptr
+    // the disordered model (couplings per bond), or J = nullptr: couplings
+    // J[3 i + mu] of the forward bonds, |J| <= jmax, and its table
+    // [nE][3][24 jmax + 1], index dE_J + 12 jmax (bonds.cu)
+    const int8_t *J;
+    int jmax;
+    const uint32_t *thrJ;
 };
 
 // A block of the sweep grid: which group, first walker, walkers in the block,
@@ -76,8 +82,9 @@ cudaError_t prepare_global_kernel(size_t smem_bytes);
 // BlockDesc.S walker slots, a power of 2 in [4, 32]).  Two instantiations:
 // rows of up to kWsNarrowMaxL sites (wide = false) and longer rows.
 constexpr int kWsNarrowMaxL = 32;
-// kernel kinds: lanes, shared tile, split narrow, split wide, row scan
-constexpr int kKinds = 5;
+// kernel kinds: lanes, shared tile, split narrow, split wide, row scan,
+// disordered model
+constexpr int kKinds = 6;
 cudaError_t launch_sweeps_ws(const GroupDev *groups_dev, const BlockDesc *blocks_dev, int n_blocks,
                              size_t smem_bytes, uint32_t seed, uint64_t sweep0, int n_sweeps,
                              int64_t ts_pos, bool record, bool wide, cudaStream_t st);
@@ -113,6 +120,11 @@ cudaError_t prepare_scan_kernel(int L, size_t smem_bytes);
 cudaError_t launch_sweeps_scan(int L, const GroupDev *groups_dev, const BlockDesc *blocks_dev,
                                int n_blocks, size_t smem_bytes, uint32_t seed, uint64_t sweep0,
                                int n_sweeps, int64_t ts_pos, bool record, cudaStream_t st);
+// Sweeps of groups with couplings per bond (bonds.cu): blocks of one warp,
+// one thread per walker (BlockDesc.S = 32, P = 1).
+cudaError_t launch_sweeps_bonds(const GroupDev *groups_dev, const BlockDesc *blocks_dev,
+                                int n_blocks, uint32_t seed, uint64_t sweep0, int n_sweeps,
+                                int64_t ts_pos, bool record, cudaStream_t st);
 // Bytes of one walker's lattice (padded rows), of a shared-memory tile, and of
 // the per-row staging area and table windows of `slots` walkers.
 size_t lattice_bytes(int L);

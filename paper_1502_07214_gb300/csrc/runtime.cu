@@ -49,6 +49,13 @@ struct Group {
     std::vector<uint32_t> injected;  // logical table given by muca_set_table (empty if none)
     uint32_t *h_thr = nullptr;       // pinned copy of the table allocation
     unsigned long long *h_hist = nullptr;  // pinned [nE]
+    // the disordered model (muca_set_bonds): couplings of the forward bonds on
+    // the device, |J| <= jmax (0: the clean model), and its table
+    // [nE][3][24 jmax + 1] on the device and pinned on the host
+    int8_t *d_J = nullptr;
+    int jmax = 0;
+    std::vector<int8_t> J;
+    uint32_t *thrJ = nullptr, *h_thrJ = nullptr;
     // every walker's E_Delta lies in the active window (required before sweeping)
     bool in_window = false;
     // kernel configuration
@@ -162,9 +169,40 @@ void parallel_rows(int n, F f)
     for (auto &x : th) x.join();
 }
 
-// Packed table of group g from its lnW into the pinned host buffer.
+// The disordered model's table [nE][3][24 jmax + 1] (index dE_J + 12 jmax)
+// from lnW into its pinned host buffer: every entry of the formula, including
+// dE_J that no move of the given couplings produces.
+void build_bonds_table(Group &g)
+{
+    const int nj = 24 * g.jmax + 1, off = 12 * g.jmax;
+    uint32_t *T = g.h_thrJ;
+    parallel_rows(g.nE, [&g, T, nj, off](int b, int e_end) {
+        for (int e = b; e < e_end; ++e)
+            for (int d = -1; d <= 1; ++d)
+                for (int dej = -off; dej <= off; ++dej)
+                    T[((size_t)e * 3 + (d + 1)) * nj + (dej + off)] = thr_entry(g, e, d, dej);
+    });
+}
+
+size_t bonds_table_words(const Group &g) { return (size_t)g.nE * 3 * (24 * g.jmax + 1); }
+
+// The table a group's sweeps read: its bytes, host copy and device copy.
+size_t table_bytes(const Group &g)
+{
+    return g.jmax ? bonds_table_words(g) * sizeof(uint32_t)
+                  : table_rows(g.nE) * kRow * sizeof(uint32_t);
+}
+const uint32_t *table_host(const Group &g) { return g.jmax ? g.h_thrJ : g.h_thr; }
+uint32_t *table_dev(const Group &g) { return g.jmax ? g.thrJ : g.thr; }
+
+// Packed table of group g from its lnW into the pinned host buffer (the
+// disordered model's table for a group with couplings).
 void build_packed(Group &g)
 {
+    if (g.jmax) {
+        build_bonds_table(g);
+        return;
+    }
     uint32_t *T = g.h_thr;
     std::memset(T, 0, table_rows(g.nE) * kRow * sizeof(uint32_t));
     uint32_t *E0 = T + (size_t)kGuard * kRow;
@@ -209,8 +247,8 @@ int pack_logical(muca_ctx *ctx, Group &g, const uint32_t *lg)
 
 int upload_table(muca_ctx *ctx, Group &g)
 {
-    CK(cudaMemcpyAsync(g.thr, g.h_thr, table_rows(g.nE) * kRow * sizeof(uint32_t),
-                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(table_dev(g), table_host(g), table_bytes(g), cudaMemcpyHostToDevice,
+                       ctx->stream));
     return MUCA_OK;
 }
 
@@ -307,6 +345,9 @@ GroupDev dev_of(const Group &g)
     d.hist = g.hist;
     d.thrE = g.thr ? g.thr + (size_t)kGuard * kRow : nullptr;
     d.ts = g.ts;
+    d.J = g.jmax ? g.d_J : nullptr;
+    d.jmax = g.jmax;
+    d.thrJ = g.jmax ? g.thrJ : nullptr;
     return d;
 }
 
@@ -321,6 +362,7 @@ int upload_groups(muca_ctx *ctx)
 // Kernel kind of a group's configuration.
 int kind_of(const Group &g)
 {
+    if (g.jmax) return 5;
     if (g.residency == MUCA_RES_SCAN) return 4;
     if (g.residency == MUCA_RES_SPLIT) return g.L > kWsNarrowMaxL ? 3 : 2;
     return g.residency == MUCA_RES_SMEM ? 1 : 0;
@@ -343,10 +385,12 @@ int build_blocks(muca_ctx *ctx)
         const size_t need = k == 0   ? stage_bytes_for(g.wpb)
                             : k == 1 ? smem_bytes_for(g.L, g.wpb) + stage_bytes_for(g.wpb)
                             : k == 4 ? scan_bytes_for(g.L)
+                            : k == 5 ? 0
                                      : ws_bytes_for(g.wpb);
         sm[k] = std::max(sm[k], need);
-        for (int w0 = 0; w0 < g.W; w0 += g.wpb)
-            b[k].push_back(BlockDesc{(int)gi, w0, std::min(g.wpb, g.W - w0), g.wpb, g.P});
+        const int wpb = k == 5 ? 32 : g.wpb, P = k == 5 ? 1 : g.P;
+        for (int w0 = 0; w0 < g.W; w0 += wpb)
+            b[k].push_back(BlockDesc{(int)gi, w0, std::min(wpb, g.W - w0), wpb, P});
     }
     // Longest blocks first: when a launch needs more than one wave of blocks,
     // the blocks of the largest lattices (work per sweep: walkers x sites)
@@ -407,6 +451,7 @@ int launch_all(muca_ctx *ctx, int n_sweeps, bool record, cudaStream_t st)
 {
     int used = (int)ctx->scan_ranges.size();
     for (int k = 0; k < 4; ++k) used += ctx->n_blocks[k] > 0;
+    used += ctx->n_blocks[5] > 0;
     const bool fork = used > 1;
     if (fork) CK(cudaEventRecord(ctx->ev_fork, st));
     for (size_t i = 0; i < ctx->scan_ranges.size(); ++i) {
@@ -433,6 +478,16 @@ int launch_all(muca_ctx *ctx, int n_sweeps, bool record, cudaStream_t st)
         if (fork) {
             CK(cudaEventRecord(ctx->ev_join[k], s));
             CK(cudaStreamWaitEvent(st, ctx->ev_join[k], 0));
+        }
+    }
+    if (ctx->n_blocks[5] > 0) {
+        cudaStream_t s = fork ? ctx->side[5] : st;
+        if (fork) CK(cudaStreamWaitEvent(s, ctx->ev_fork, 0));
+        CK(launch_sweeps_bonds(ctx->d_groups, ctx->d_blocks[5], ctx->n_blocks[5], ctx->seed,
+                               ctx->sweep, n_sweeps, ctx->ts_len, record, s));
+        if (fork) {
+            CK(cudaEventRecord(ctx->ev_join[5], s));
+            CK(cudaStreamWaitEvent(st, ctx->ev_join[5], 0));
         }
     }
     return MUCA_OK;
@@ -750,6 +805,13 @@ static void free_group(Group &g)
     cudaFree(g.ts);
     cudaFreeHost(g.h_thr);
     cudaFreeHost(g.h_hist);
+    cudaFree(g.d_J);
+    cudaFree(g.thrJ);
+    cudaFreeHost(g.h_thrJ);
+    g.d_J = nullptr;
+    g.thrJ = nullptr;
+    g.h_thrJ = nullptr;
+    g.jmax = 0;
     g.spins = nullptr;
     g.tal = nullptr;
     g.hist = nullptr;
@@ -1062,6 +1124,73 @@ int muca_get_window(muca_ctx *ctx, int group, int32_t *out)
     return MUCA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Give group g the couplings J (host int8 [V][3]) with table width jmax, or
+// take them away (J == nullptr): device copies, the table, the kernel kind;
+// the tallies are recomputed from the current spins when `retally`.
+int apply_bonds(muca_ctx *ctx, int group, const int8_t *J, int jmax, bool retally)
+{
+    Group &g = ctx->g[group];
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(g.d_J);
+    cudaFree(g.thrJ);
+    cudaFreeHost(g.h_thrJ);
+    g.d_J = nullptr;
+    g.thrJ = nullptr;
+    g.h_thrJ = nullptr;
+    g.jmax = 0;
+    g.J.clear();
+    if (J) {
+        g.jmax = jmax;
+        g.J.assign(J, J + (size_t)3 * g.V);
+        CK(cudaMalloc(&g.d_J, (size_t)3 * g.V));
+        CK(cudaMemcpy(g.d_J, J, (size_t)3 * g.V, cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&g.thrJ, bonds_table_words(g) * sizeof(uint32_t)));
+        CK(cudaMallocHost(&g.h_thrJ, bonds_table_words(g) * sizeof(uint32_t)));
+    }
+    g.injected.clear();
+    int rc = upload_groups(ctx);
+    if (rc != MUCA_OK) return rc;
+    rc = build_blocks(ctx);
+    if (rc != MUCA_OK) return rc;
+    if (retally) CK(launch_energies(dev_of(g), 0, ctx->d_err, ctx->stream));
+    build_packed(g);
+    rc = upload_table(ctx, g);
+    if (rc != MUCA_OK) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MUCA_OK;
+}
+
+int check_bonds(muca_ctx *ctx, const Group &g, const int8_t *J, int jmax)
+{
+    if (jmax < 1 || jmax > MUCA_MAX_JMAX)
+        return fail(ctx, MUCA_ERR_INVALID_ARG, "set_bonds: jmax %d outside [1, %d]", jmax,
+                    MUCA_MAX_JMAX);
+    for (size_t k = 0; k < (size_t)3 * g.V; ++k)
+        if (J[k] < -jmax || J[k] > jmax)
+            return fail(ctx, MUCA_ERR_INVALID_ARG, "set_bonds: coupling %d of bond %zu outside "
+                        "[-%d, %d]", (int)J[k], k, jmax, jmax);
+    return MUCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int muca_set_bonds(muca_ctx *ctx, int group, const int8_t *J, int32_t jmax)
+{
+    int rc = check_group_index(ctx, group);
+    if (rc) return rc;
+    if (J) {
+        rc = check_bonds(ctx, ctx->g[group], J, jmax);
+        if (rc) return rc;
+    }
+    return apply_bonds(ctx, group, J, J ? jmax : 0, true);
+}
+
 int muca_iterate(muca_ctx *ctx, int32_t max_iters, int32_t sweeps_per_iter, double flat_min,
                  int32_t *n_done)
 {
@@ -1132,7 +1261,7 @@ extern "C" int muca_run_graph(muca_ctx *ctx, int n_iters, int sweeps_per_iter)
             if (cudaMemcpyAsync(g.h_hist, g.hist, (size_t)g.nE * sizeof(unsigned long long),
                                 cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
                 cudaLaunchHostFunc(cs, host_update, &g) != cudaSuccess ||
-                cudaMemcpyAsync(g.thr, g.h_thr, table_rows(g.nE) * kRow * sizeof(uint32_t),
+                cudaMemcpyAsync(table_dev(g), table_host(g), table_bytes(g),
                                 cudaMemcpyHostToDevice, cs) != cudaSuccess ||
                 cudaMemsetAsync(g.hist, 0, (size_t)g.nE * sizeof(unsigned long long), cs) !=
                     cudaSuccess)
@@ -1245,6 +1374,10 @@ int muca_get_table(muca_ctx *ctx, int group, uint32_t *out)
     if (rc) return rc;
     if (!out) return fail(ctx, MUCA_ERR_INVALID_ARG, "out is NULL");
     const Group &g = ctx->g[group];
+    if (g.jmax)
+        return fail(ctx, MUCA_ERR_INVALID_ARG,
+                    "get_table: group %d has couplings per bond (its table is muca_build_table_bonds')",
+                    group);
     if (!g.injected.empty()) {
         std::memcpy(out, g.injected.data(), g.injected.size() * sizeof(uint32_t));
         return MUCA_OK;
@@ -1262,6 +1395,8 @@ int muca_set_table(muca_ctx *ctx, int group, const uint32_t *in)
     if (rc) return rc;
     if (!in) return fail(ctx, MUCA_ERR_INVALID_ARG, "in is NULL");
     Group &g = ctx->g[group];
+    if (g.jmax)
+        return fail(ctx, MUCA_ERR_INVALID_ARG, "set_table: group %d has couplings per bond", group);
     CK(cudaStreamSynchronize(ctx->stream));
     rc = pack_logical(ctx, g, in);
     if (rc) return rc;
@@ -1342,6 +1477,26 @@ int muca_build_table(int32_t L, double T, int32_t e_min, int32_t e_max, const do
         for (int d = -1; d <= 1; ++d)
             for (int dej = -12; dej <= 12; ++dej)
                 out[((size_t)e * 3 + (d + 1)) * MUCA_NK + (dej + 12)] =
+                    table_entry(beta, lnW, 0, nE - 1, e, d, dej);
+    return MUCA_OK;
+}
+
+int muca_build_table_bonds(int32_t L, double T, int32_t jmax, int32_t e_min, int32_t e_max,
+                           const double *lnW, uint32_t *out)
+{
+    if (L < 2 || L > MUCA_MAX_L || !(T > 0.0) || !std::isfinite(T) || jmax < 1 ||
+        jmax > MUCA_MAX_JMAX)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG, "build_table_bonds: L=%d, T=%g, jmax=%d", L, T,
+                    jmax);
+    if (e_min < 0 || e_max < e_min || e_max > L * L * L || !lnW || !out)
+        return fail(nullptr, MUCA_ERR_INVALID_ARG,
+                    "build_table_bonds: window [%d, %d] or NULL array", e_min, e_max);
+    const int nE = e_max - e_min + 1, nj = 24 * jmax + 1, off = 12 * jmax;
+    const double beta = 1.0 / T;
+    for (int e = 0; e < nE; ++e)
+        for (int d = -1; d <= 1; ++d)
+            for (int dej = -off; dej <= off; ++dej)
+                out[((size_t)e * 3 + (d + 1)) * nj + (dej + off)] =
                     table_entry(beta, lnW, 0, nE - 1, e, d, dej);
     return MUCA_OK;
 }
@@ -1435,19 +1590,24 @@ int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walke
 {
     int rc = check_group_index(ctx, group);
     if (rc) return rc;
-    if (residency) *residency = ctx->g[group].residency;
-    if (walkers_per_block) *walkers_per_block = ctx->g[group].wpb;
-    if (lanes_per_walker) *lanes_per_walker = ctx->g[group].P;
+    const Group &g = ctx->g[group];
+    if (residency) *residency = g.jmax ? MUCA_RES_BONDS : g.residency;
+    if (walkers_per_block) *walkers_per_block = g.jmax ? 32 : g.wpb;
+    if (lanes_per_walker) *lanes_per_walker = g.jmax ? 1 : g.P;
     return MUCA_OK;
 }
 
 // Checkpoint file: magic with the format version, seed, sweep, n_groups, per
 // group the spec, per group the weight recursion (int32), per group the
 // global id of its first walker and the walkers held (int32 x 2, the shard),
-// then per group lnW[nE], acc[max(nE - 1, 1)], hist[nE], tallies[3][Wpad],
-// spins[V][Wpad].  Formats 02 (no shard record: every walker of the group)
-// and 01 (neither the shard, the recursion nor acc) are still read.
-static const char kMagic[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '4'};
+// per group the active window and its growth rule (int32 x 3 + FP64), per
+// group the couplings (int32 jmax, then int8 [V][3] if jmax > 0), then per
+// group lnW[nE], acc[max(nE - 1, 1)], hist[nE], tallies[3][Wpad],
+// spins[V][Wpad].  Formats 04 (no couplings: the clean model), 03 (no
+// window record), 02 (no shard record: every walker of the group) and 01
+// (neither the shard, the recursion nor acc) are still read.
+static const char kMagic[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '5'};
+static const char kMagic04[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '4'};
 static const char kMagic03[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '3'};
 static const char kMagic02[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '2'};
 static const char kMagic01[8] = {'M', 'U', 'C', 'A', 'B', 'C', '0', '1'};
@@ -1477,6 +1637,11 @@ int muca_checkpoint(muca_ctx *ctx, const char *path)
         const int32_t win[3] = {g.e_min + g.win_lo, g.e_min + g.win_hi, g.grow_step};
         ok = ok && std::fwrite(win, sizeof win, 1, f) == 1;
         ok = ok && std::fwrite(&g.grow_flat, sizeof g.grow_flat, 1, f) == 1;
+    }
+    for (auto &g : ctx->g) {
+        const int32_t jm = g.jmax;
+        ok = ok && std::fwrite(&jm, sizeof jm, 1, f) == 1;
+        if (jm) ok = ok && std::fwrite(g.J.data(), 1, g.J.size(), f) == g.J.size();
     }
     for (auto &g : ctx->g) {
         if (!ok) break;
@@ -1512,7 +1677,8 @@ int muca_restore(muca_ctx *ctx, const char *path)
     uint64_t sweep = 0;
     int32_t ng = 0;
     bool ok = std::fread(magic, 1, 8, f) == 8;
-    const bool v4 = ok && std::memcmp(magic, kMagic, 8) == 0;
+    const bool v5 = ok && std::memcmp(magic, kMagic, 8) == 0;
+    const bool v4 = v5 || (ok && std::memcmp(magic, kMagic04, 8) == 0);
     const bool v3 = v4 || (ok && std::memcmp(magic, kMagic03, 8) == 0);
     const bool v2 = v3 || (ok && std::memcmp(magic, kMagic02, 8) == 0);
     ok = ok && (v2 || std::memcmp(magic, kMagic01, 8) == 0);
@@ -1554,6 +1720,20 @@ int muca_restore(muca_ctx *ctx, const char *path)
              std::isfinite(flat) && (flat == 0.0 || w3[2] >= 1);
         wins.push_back({w3[0], w3[1], w3[2], flat});
     }
+    // the couplings: written by format 05; earlier formats hold the clean model
+    std::vector<int32_t> jms(ctx->g.size(), 0);
+    std::vector<std::vector<int8_t>> Js(ctx->g.size());
+    for (size_t gi = 0; gi < ctx->g.size() && ok; ++gi) {
+        if (!v5) break;
+        ok = std::fread(&jms[gi], sizeof(int32_t), 1, f) == 1 && jms[gi] >= 0 &&
+             jms[gi] <= MUCA_MAX_JMAX;
+        if (ok && jms[gi]) {
+            Js[gi].resize((size_t)3 * ctx->g[gi].V);
+            ok = std::fread(Js[gi].data(), 1, Js[gi].size(), f) == Js[gi].size();
+            for (size_t k = 0; ok && k < Js[gi].size(); ++k)
+                ok = Js[gi][k] >= -jms[gi] && Js[gi][k] <= jms[gi];
+        }
+    }
     if (!ok) {
         std::fclose(f);
         return fail(ctx, MUCA_ERR_INVALID_ARG, "restore: %s does not match this context", path);
@@ -1589,6 +1769,14 @@ int muca_restore(muca_ctx *ctx, const char *path)
             cudaMemcpy(g.spins, s.data(), s.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
             std::fclose(f);
             return fail(ctx, MUCA_ERR_CUDA, "restore: device write failed");
+        }
+        if (jms[gi] != g.jmax || (jms[gi] && Js[gi] != g.J)) {
+            const int rb = apply_bonds(ctx, (int)gi, jms[gi] ? Js[gi].data() : nullptr, jms[gi],
+                                       false);
+            if (rb) {
+                std::fclose(f);
+                return rb;
+            }
         }
         build_packed(g);
         int rc = upload_table(ctx, g);

@@ -1253,9 +1253,10 @@ __global__ void init_spins_kernel(GroupDev g, uint32_t seed)
     }
 }
 
-// E_J (three forward bonds per site), E_Delta and M of every walker, one
-// thread per walker.  mode 0 stores them as the running tallies, mode 1
-// compares them with the running tallies and sets *err on a mismatch.
+// E_J (three forward bonds per site, each weighted by its coupling when the
+// group has couplings), E_Delta and M of every walker, one thread per walker.
+// mode 0 stores them as the running tallies, mode 1 compares them with the
+// running tallies and sets *err on a mismatch.
 __global__ void energies_kernel(GroupDev g, int mode, int *err)
 {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1271,9 +1272,12 @@ __global__ void energies_kernel(GroupDev g, int mode, int *err)
             for (int x = 0; x < L; ++x) {
                 const int xp = (x + 1 == L) ? 0 : x + 1;
                 const int s = *site_ptr(lat, st, Lw, z * L + y, x);
-                ej -= s * (*site_ptr(lat, st, Lw, z * L + y, xp) +
-                           *site_ptr(lat, st, Lw, z * L + yp, x) +
-                           *site_ptr(lat, st, Lw, zp * L + y, x));
+                const int i = x + L * (y + L * z);
+                const int jx = g.J ? g.J[3 * i + 0] : 1, jy = g.J ? g.J[3 * i + 1] : 1,
+                          jz = g.J ? g.J[3 * i + 2] : 1;
+                ej -= s * (jx * *site_ptr(lat, st, Lw, z * L + y, xp) +
+                           jy * *site_ptr(lat, st, Lw, z * L + yp, x) +
+                           jz * *site_ptr(lat, st, Lw, zp * L + y, x));
                 ed += s * s;
                 m += s;
             }

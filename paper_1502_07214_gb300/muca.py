@@ -24,11 +24,12 @@ ERR_NOT_SUPPORTED = -6
 ERR_WINDOW = -7
 ERR_IO = -8
 
-RES_AUTO, RES_GLOBAL, RES_SMEM, RES_SPLIT, RES_SCAN = 0, 1, 2, 3, 4
+RES_AUTO, RES_GLOBAL, RES_SMEM, RES_SPLIT, RES_SCAN, RES_BONDS = 0, 1, 2, 3, 4, 5
 REC_PLAIN, REC_ACCUMULATED = 0, 1
 DEBUG_TALLY_CHECK = 1
 NK = 25
 MAX_L = 64  # largest linear size (MUCA_MAX_L)
+MAX_JMAX = 8  # largest |coupling| of the disordered model (MUCA_MAX_JMAX)
 
 
 class MucaError(RuntimeError):
@@ -67,6 +68,8 @@ SIGNATURES = {
     "muca_get_flatness": [_P, ctypes.c_int, _P],
     "muca_iterate": [_P, _I32, _I32, _D, _P],
     "muca_set_window": [_P, ctypes.c_int, _I32, _I32, _D, _I32],
+    "muca_set_bonds": [_P, ctypes.c_int, _P, _I32],
+    "muca_build_table_bonds": [_I32, _D, _I32, _I32, _I32, _P, _P],
     "muca_probe_int": [_I32, _I32, _P, _P, _P],
     "muca_probe_l2_read": [_I64, _I32, _P, _P, _P],
     "muca_get_window": [_P, ctypes.c_int, _P],
@@ -138,6 +141,15 @@ def _stream_ptr(stream):
         import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def build_table_bonds(L, T, jmax, e_min, e_max, lnW):
+    """The disordered model's table [n_e][3][24 jmax + 1] on the host."""
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    out = np.zeros((e_max - e_min + 1, 3, 24 * jmax + 1), dtype=np.uint32)
+    _ck(lib().muca_build_table_bonds(int(L), float(T), int(jmax), int(e_min), int(e_max),
+                                     _np_ptr(lnW), _np_ptr(out)))
+    return out
 
 
 def probe_int(kind, iters=2048, stream=None):
@@ -276,6 +288,18 @@ class Context:
         grow_flat over it (``muca_set_window``; grow_flat = 0: fixed)."""
         self._c(lib().muca_set_window(self._ctx, g, int(lo), int(hi), float(grow_flat),
                                       int(grow_step)))
+
+    def set_bonds(self, g, J, jmax=None):
+        """Couplings per bond of group g (``muca_set_bonds``): J int8
+        [L^3][3] (forward x, y, z bonds), |J| <= jmax (default: the largest
+        |J|, at least 1); None returns the group to the clean model."""
+        if J is None:
+            self._c(lib().muca_set_bonds(self._ctx, g, None, 0))
+            return
+        a = np.ascontiguousarray(J, dtype=np.int8).reshape(self.specs[g]["V"], 3)
+        if jmax is None:
+            jmax = max(1, int(np.abs(a.astype(np.int64)).max()))
+        self._c(lib().muca_set_bonds(self._ctx, g, _np_ptr(a), int(jmax)))
 
     def get_window(self, g):
         out = np.zeros(2, dtype=np.int32)

@@ -70,13 +70,14 @@ def test_iterate_until_flat(rec):
 def _head(b):
     import ctypes
 
-    assert b[:8] == b"MUCABC04"
+    assert b[:8] == b"MUCABC05"
     return 8 + 4 + 8 + 4 + ctypes.sizeof(muca().Group)  # magic, seed, sweep, n_groups, group
 
 
-# one group's records after the header in format 04: recursion (int32), shard
-# (2 x int32), window (3 x int32 + FP64)
-REC, SHARD, WIN = 4, 8, 20
+# one group's records after the header in format 05: recursion (int32), shard
+# (2 x int32), window (3 x int32 + FP64), couplings (int32 jmax = 0: none)
+REC, SHARD, WIN, BONDS = 4, 8, 20, 4
+ALL = REC + SHARD + WIN + BONDS
 
 
 def checkpoint_v01(src, dst, n_e):
@@ -84,24 +85,33 @@ def checkpoint_v01(src, dst, n_e):
     recursion field, no shard or window record, no accumulated pair weights."""
     b = open(src, "rb").read()
     head = _head(b)
-    rest = b[head + REC + SHARD + WIN:]  # without the recursion, shard and window records
+    rest = b[head + ALL:]  # without the recursion, shard, window and coupling records
     lnw = rest[:8 * n_e]
     rest = rest[8 * n_e + 8 * max(n_e - 1, 1):]  # without acc
     open(dst, "wb").write(b"MUCABC01" + b[8:head] + lnw + rest)
 
 
 def checkpoint_v02(src, dst):
-    """The same checkpoint in format 02 (one group): no shard or window record."""
+    """The same checkpoint in format 02 (one group): no shard, window or
+    coupling record."""
     b = open(src, "rb").read()
     head = _head(b)
-    open(dst, "wb").write(b"MUCABC02" + b[8:head + REC] + b[head + REC + SHARD + WIN:])
+    open(dst, "wb").write(b"MUCABC02" + b[8:head + REC] + b[head + ALL:])
 
 
 def checkpoint_v03(src, dst):
-    """The same checkpoint in format 03 (one group): no window record."""
+    """The same checkpoint in format 03 (one group): no window or coupling
+    record."""
     b = open(src, "rb").read()
     head = _head(b)
-    open(dst, "wb").write(b"MUCABC03" + b[8:head + REC + SHARD] + b[head + REC + SHARD + WIN:])
+    open(dst, "wb").write(b"MUCABC03" + b[8:head + REC + SHARD] + b[head + ALL:])
+
+
+def checkpoint_v04(src, dst):
+    """The same checkpoint in format 04 (one group): no coupling record."""
+    b = open(src, "rb").read()
+    head = _head(b)
+    open(dst, "wb").write(b"MUCABC04" + b[8:head + REC + SHARD + WIN] + b[head + ALL:])
 
 
 def test_checkpoint_carries_the_recursion(tmp_path):
@@ -147,9 +157,11 @@ def test_checkpoint_carries_the_recursion(tmp_path):
         d.merge_update()
     np.testing.assert_array_equal(d.get_lnW(0), plain_lnW)
     d.close()
-    # formats 02 (no shard record: every walker of the group) and 03 (no
-    # window record: the fixed window [e_min, e_max]) restore the run
-    for name, conv in (("acc02.ckpt", checkpoint_v02), ("acc03.ckpt", checkpoint_v03)):
+    # formats 02 (no shard record: every walker of the group), 03 (no window
+    # record: the fixed window [e_min, e_max]) and 04 (no couplings: the clean
+    # model) restore the run
+    for name, conv in (("acc02.ckpt", checkpoint_v02), ("acc03.ckpt", checkpoint_v03),
+                       ("acc04.ckpt", checkpoint_v04)):
         v = str(tmp_path / name)
         conv(path, v)
         e = m.Context(g, seed=seed)

@@ -63,3 +63,20 @@ def test_host_table_build_equals_oracle(L, T, e_min, e_max):
     lnW = wl.random_lnW(e_max - e_min + 1, seed=L, scale=2.0, slope=-2.8 / T)
     got = m.build_table(L, T, e_min, e_max, lnW)
     assert np.array_equal(got, oracle.build_table(L, T, e_min, e_max, lnW))
+
+
+@pytest.mark.parametrize("L,T,jmax,e_min,e_max", [(2, 1.0, 1, 0, 8), (4, 3.0, 3, 10, 60),
+                                                  (6, 2.0, 8, 0, 216)])
+def test_host_bonds_table_build_equals_oracle(L, T, jmax, e_min, e_max):
+    """muca_build_table_bonds (the disordered model's table, host, no
+    context) against the oracle's, entry for entry; at jmax = 1 it is the
+    clean table."""
+    from paper_1502_07214_gb300 import workloads as wl
+
+    lnW = wl.random_lnW(e_max - e_min + 1, seed=L + jmax, scale=2.0, slope=-2.8 / T)
+    got = m.build_table_bonds(L, T, jmax, e_min, e_max, lnW)
+    assert np.array_equal(got, oracle.build_table_bonds(L, T, jmax, e_min, e_max, lnW))
+    if jmax == 1:
+        assert np.array_equal(got, m.build_table(L, T, e_min, e_max, lnW))
+    with pytest.raises(m.MucaError):
+        m.build_table_bonds(L, T, 9, e_min, e_max, lnW)
