@@ -55,17 +55,17 @@ def env_int(k, d):
 # DRAM bytes (read + write) per sweep of the benchmark workload, from one ncu
 # capture of each kernel in this configuration (a launch of 2 sweeps after
 # three 1000-sweep weight iterations): split kernel 926.8 MB read + 848.5 MB
-# written, row-scan kernel 1938.7 MB read + 881.6 MB written.  Valid only for
+# written, row-scan kernel 1943.5 MB read + 881.9 MB written.  Valid only for
 # the kernel source the counters were taken on; empty (traffic reported as
 # null) while no capture of the current source exists.
 TRAFFIC_PER_SWEEP = {3: (926.811392e6 + 848.504064e6) / 2,
-                     4: (1938.680e6 + 881.562624e6) / 2}
+                     4: (1943.472e6 + 881.874176e6) / 2}
 
 
 # L2 bytes (32-byte sectors through the L2, lts__t_sectors.sum) per sweep from
-# the same captures: split kernel 216.3 M sectors, row-scan kernel 337.2 M
+# the same captures: split kernel 216.3 M sectors, row-scan kernel 338.3 M
 # sectors per 2-sweep launch.  Same validity rule as the DRAM traffic.
-L2_PER_SWEEP = {3: 216.3e6 * 32 / 2, 4: 337.2e6 * 32 / 2}
+L2_PER_SWEEP = {3: 216.3e6 * 32 / 2, 4: 338.261052e6 * 32 / 2}
 
 PROBE_KINDS = {0: "IMAD a=a*a+b", 1: "IADD3 a=a+b+c", 2: "LOP3 a=(a&b)^c",
                3: "half IMAD, half IADD3"}
@@ -274,8 +274,12 @@ def run_ours(args, rank, world, local_rank):
     # one simulation over all ranks: each holds 4096 walkers of the group and
     # the histograms are summed over the ranks (NCCL, device buffers) after
     # every iteration; one rank runs the same workload unsharded
+    fixed = {}
+    if args.sweep_config:
+        r_, w_, p_ = (int(x) for x in args.sweep_config.split(","))
+        fixed = dict(residency=r_, walkers_per_block=w_, lanes_per_walker=p_)
     ctx = muca.Context([shard_group(L, T, W, world)], seed=s["seed"],
-                       shard=(rank, world) if world > 1 else (0, 0))
+                       shard=(rank, world) if world > 1 else (0, 0), **fixed)
     ctx.reserve_timeseries(meas)
     res, wpb, lanes = ctx.get_config(0)
     launches_per_sweep_call = 1
@@ -645,6 +649,10 @@ def main():
                     help="run a short untimed case for a profiler capture and exit")
     ap.add_argument("--profile-config", default="1,4,8",
                     help="sweep kernel configuration of --profile sweep")
+    ap.add_argument("--sweep-config", default="",
+                    help="residency,walkers per block,lanes per walker of the benchmark's "
+                         "context instead of the autotuner's choice (for profiler runs, whose "
+                         "serialised launches change the autotuner's timings)")
     args = ap.parse_args()
     if args.profile == "probes":
         # the device probes alone, printed as JSON (short runs for a capture)
