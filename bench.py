@@ -380,6 +380,7 @@ def run_ours(args, rank, world, local_rank):
     rw = mixed = wu = None
     if rank == 0:
         probes = device_probes(torch, muca)
+        disordered = disordered_bench(torch, muca, stream)
         rw = reweight_bench(torch, muca)
         mixed = mixed_bench(torch, muca, stream)
         wu = weight_update_bench(muca)
@@ -432,6 +433,7 @@ def run_ours(args, rank, world, local_rank):
                                 "bytes_source": "ncu lts__t_sectors.sum x 32 B of the "
                                                 "kernel's capture"}},
             "probes": probes,
+            "disordered": disordered,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (launches_per_sweep_call * 2 + 3),
@@ -510,6 +512,48 @@ def mixed_bench(torch, muca, stream, n_it=2, n_full=None):
             "batched_configs": [{"residency": {1: "global", 2: "smem", 3: "split", 4: "scan"}.get(c[0], str(c[0])),
                                  "walkers_per_block": c[1], "lanes_per_walker": c[2]}
                                 for c in cfgs]}
+
+
+def disordered_bench(torch, muca, stream):
+    """The disordered model (couplings per bond, its own kernel): 4096
+    walkers of L = 24 with bimodal couplings, one weight iteration of 100
+    sweeps as a graph after a warm-up iteration; attempts/s, the kernel's
+    average launch duration (CUDA events on the launching stream around
+    plain sweep launches) and its HBM roofline at 2 B per attempt."""
+    d = wl.DISORDERED
+    V = d["L"] ** 3
+    J = wl.random_bonds(d["L"], d["j1"], d["j2"], seed=d["bond_seed"])
+    ctx = muca.Context([{"L": d["L"], "T": d["T"], "n_walkers": d["n_walkers"]}], seed=d["seed"])
+    ctx.set_bonds(0, J)
+    ctx.run_graph(1, d["sweeps"])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    ctx.run_graph(1, d["sweeps"])
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = a.elapsed_time(b)
+    ks = []
+    for _ in range(2):
+        a.record(stream)
+        ctx.sweep_iter(d["sweeps"])
+        b.record(stream)
+        torch.cuda.synchronize()
+        ks.append(a.elapsed_time(b))
+        ctx.merge_update()
+    cfg = ctx.get_config(0)
+    ctx.close()
+    attempts = d["n_walkers"] * V * d["sweeps"]
+    k_ms = sum(ks) / len(ks)
+    pk, pk_kind = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    gbs = 2.0 * attempts / (k_ms / 1e3) / 1e9
+    return {"workload": f"L={d['L']} T={d['T']} {d['n_walkers']} walkers, bimodal couplings "
+                        f"{d['j1']}/{d['j2']} (p = 1/2), one iteration of {d['sweeps']} sweeps",
+            "unit": UNIT, "value": attempts / (ms_graph / 1e3), "kernel_ms": k_ms,
+            "kernel": "sweep_bonds_kernel", "residency": cfg[0],
+            "roofline": {"bound": "hbm", "achieved_gbs": gbs, "peak_gbs": hbm,
+                         "frac": gbs / hbm, "peak_kind": pk_kind, "bytes_per_attempt": 2}}
 
 
 def weight_update_bench(muca, reps=20):
@@ -606,9 +650,10 @@ def run_profile_case(what, cfg):
     """Short fixed launches for profiler captures (not timed): the sweep kernel
     of the benchmark workload in a given configuration "residency,walkers per
     block,lanes per walker" (three 1000-sweep weight iterations, the regime of
-    the benchmark's steps, then 2 launches of 2 sweeps; no autotuning trials)
-    or the
-    reweighting of the reweight workload (FP32 then FP64)."""
+    the benchmark's steps, then 2 launches of 2 sweeps; no autotuning trials),
+    the disordered model's workload (one 100-sweep iteration, then 2 launches
+    of 2 sweeps) or the reweighting of the reweight workload (FP32 then
+    FP64)."""
     import torch
 
     from paper_1502_07214_gb300 import muca
@@ -628,6 +673,18 @@ def run_profile_case(what, cfg):
         ctx.sync()
         print("profile case: sweep", ctx.get_config(0))
         ctx.close()
+    elif what == "bonds":
+        d = wl.DISORDERED
+        ctx = muca.Context([{"L": d["L"], "T": d["T"], "n_walkers": d["n_walkers"]}],
+                           seed=d["seed"])
+        ctx.set_bonds(0, wl.random_bonds(d["L"], d["j1"], d["j2"], seed=d["bond_seed"]))
+        ctx.sweep_iter(d["sweeps"])
+        ctx.merge_update()
+        for _ in range(2):
+            ctx.sweep_iter(2)
+        ctx.sync()
+        print("profile case: bonds", ctx.get_config(0))
+        ctx.close()
     else:
         r = wl.REWEIGHT
         ej, ed, m, lnW, dt = wl.synthetic_series()
@@ -645,7 +702,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--profile", choices=["sweep", "reweight", "probes"],
+    ap.add_argument("--profile", choices=["sweep", "reweight", "probes", "bonds"],
                     help="run a short untimed case for a profiler capture and exit")
     ap.add_argument("--profile-config", default="1,4,8",
                     help="sweep kernel configuration of --profile sweep")

@@ -14,10 +14,13 @@
 // that leave the window through zero thresholds, the histogram after every
 // sweep, the recorded series) is the clean model's.
 //
-// One thread per walker; a warp's 32 walkers read 128 contiguous bytes per
-// packed spin word, and the couplings of the site (the same for every walker
-// of the group) are one broadcast load each.  A correctness-first kernel: it
-// reads its neighbours and thresholds through L1/L2 site by site.
+// One thread per walker, a warp of 8 to 32 walkers (about four warps per SM);
+// the walkers of a warp read whole 32-byte sectors per packed spin word, and
+// the couplings of the site (the same for every walker of the group) are one
+// broadcast load each.  A correctness-first kernel: it reads its neighbours
+// and thresholds through L1/L2 site by site, about 180 warp instructions per
+// site, most of them on one dependent chain, so a walker's sweep runs at the
+// latency of that chain whatever the number of walkers per warp.
 #include <cuda_runtime.h>
 
 #include <cstdint>

@@ -121,7 +121,7 @@ cudaError_t launch_sweeps_scan(int L, const GroupDev *groups_dev, const BlockDes
                                int n_blocks, size_t smem_bytes, uint32_t seed, uint64_t sweep0,
                                int n_sweeps, int64_t ts_pos, bool record, cudaStream_t st);
 // Sweeps of groups with couplings per bond (bonds.cu): blocks of one warp,
-// one thread per walker (BlockDesc.S = 32, P = 1).
+// one thread per walker, BlockDesc.nw <= 32 walkers (P = 1).
 cudaError_t launch_sweeps_bonds(const GroupDev *groups_dev, const BlockDesc *blocks_dev,
                                 int n_blocks, uint32_t seed, uint64_t sweep0, int n_sweeps,
                                 int64_t ts_pos, bool record, cudaStream_t st);

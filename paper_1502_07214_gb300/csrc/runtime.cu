@@ -375,6 +375,22 @@ int kind_of(const Group &g)
 //   [4, 32]; kind 2 for rows of up to kWsNarrowMaxL sites, kind 3 above;
 //   kind 4: row-scan kernel, one warp of wpb_g = 32 / P_g walkers per block,
 //   P_g = scan_seg(L) lanes per walker.
+// Walkers per warp of the disordered model's kernel: the walkers are spread
+// over about four warps per SM (a power of 2, at most 32; at least 8 keep
+// whole 32-byte sectors per packed-word load).  Measured at 4096 walkers of
+// L = 24: 8 per warp 1.58e10 attempts/s, 32 per warp 1.45e10 (each warp's
+// per-site chain is the limit either way).
+int bonds_walkers_per_warp(int W)
+{
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+        nsm = 1;
+    int wpb = 8;
+    while (wpb < 32 && (int64_t)W > (int64_t)wpb * nsm * 4) wpb *= 2;
+    return wpb;
+}
+
 int build_blocks(muca_ctx *ctx)
 {
     std::vector<BlockDesc> b[kKinds];
@@ -388,7 +404,7 @@ int build_blocks(muca_ctx *ctx)
                             : k == 5 ? 0
                                      : ws_bytes_for(g.wpb);
         sm[k] = std::max(sm[k], need);
-        const int wpb = k == 5 ? 32 : g.wpb, P = k == 5 ? 1 : g.P;
+        const int wpb = k == 5 ? bonds_walkers_per_warp(g.W) : g.wpb, P = k == 5 ? 1 : g.P;
         for (int w0 = 0; w0 < g.W; w0 += wpb)
             b[k].push_back(BlockDesc{(int)gi, w0, std::min(wpb, g.W - w0), wpb, P});
     }
@@ -1592,7 +1608,7 @@ int muca_get_config(muca_ctx *ctx, int group, int32_t *residency, int32_t *walke
     if (rc) return rc;
     const Group &g = ctx->g[group];
     if (residency) *residency = g.jmax ? MUCA_RES_BONDS : g.residency;
-    if (walkers_per_block) *walkers_per_block = g.jmax ? 32 : g.wpb;
+    if (walkers_per_block) *walkers_per_block = g.jmax ? bonds_walkers_per_warp(g.W) : g.wpb;
     if (lanes_per_walker) *lanes_per_walker = g.jmax ? 1 : g.P;
     return MUCA_OK;
 }

@@ -24,6 +24,10 @@ SMALL = dict(L=8, T=2.0, n_walkers=64, n_iter=10, sweeps=200, seed=0)
 MEDIUM = dict(L=16, T=1.0, n_walkers=1024, n_iter=30, sweeps=500, seed=1)
 MIXED = dict(Ls=(8, 12, 16, 20, 24, 32), Ts=TEMPS, n_walkers=512, n_iter=20, sweeps=300, seed=2)
 LARGE = dict(L=48, T=0.9, n_walkers=4096, n_iter=40, sweeps=1000, n_meas=10000, seed=3)
+# The disordered model: bimodal couplings j1, j2 (ratio 0.6, mean 4) on every
+# bond with probability 1/2 each, at T = 3.6 (T = 0.9 in units of the mean
+# coupling); 4096 walkers of L = 24, one realisation.
+DISORDERED = dict(L=24, T=3.6, n_walkers=4096, j1=5, j2=3, bond_seed=11, sweeps=100, seed=6)
 REWEIGHT = dict(L=32, T=1.4182, n_walkers=4096, n_samples=10000, n_grid=4096, half_width=0.05,
                 seed=4)
 

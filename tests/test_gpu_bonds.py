@@ -188,3 +188,29 @@ def test_bond_errors_and_return_to_the_clean_model():
     assert c.get_config(0)[0] != m.RES_BONDS
     c.get_table(0)
     c.close()
+
+
+def test_disordered_workload_full_size_sampled_walkers():
+    """The benchmark's disordered workload (4096 walkers of L = 24, bimodal
+    couplings 5 / 3) in its launch configuration: three recorded sweeps of
+    every walker on the GPU; sampled walkers (first, last, ragged middle)
+    against the oracle run of the same global walker ids, and the histogram
+    against the recorded series."""
+    d = wl.DISORDERED
+    L, W = d["L"], d["n_walkers"]
+    J = wl.random_bonds(L, d["j1"], d["j2"], seed=d["bond_seed"])
+    c = muca().Context([{"L": L, "T": d["T"], "n_walkers": W}], seed=d["seed"])
+    c.set_bonds(0, J)
+    c.reserve_timeseries(3)
+    c.sweep_iter(3, record=True)
+    spins, tal = c.get_state(0)
+    ts = c.get_timeseries(0)
+    H = c.get_hist(0)
+    assert int(H.sum()) == 3 * W
+    assert np.array_equal(H, np.bincount(ts[:, 1, :].ravel(), minlength=L ** 3 + 1))
+    for w in (0, 1, 1001, 2047, W - 1):
+        ref = oracle.muca_run(L, d["T"], 1, d["seed"], 0, 0, n_meas=3, walker_id0=w, bonds=J)
+        assert np.array_equal(spins[w], ref["spins"][0]), w
+        assert np.array_equal(tal[w], ref["tallies"][0]), w
+        assert np.array_equal(ts[:, :, w], ref["ts"][0]), w
+    c.close()
