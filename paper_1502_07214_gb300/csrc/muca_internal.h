@@ -45,6 +45,10 @@ struct GroupDev {
     const int8_t *J;
     int jmax;
     const uint32_t *thrJ;
+    // the six couplings of every site's bonds packed as int8 bytes of one
+    // word: J[3 i], J[3 (i - x)], J[3 i + 1], J[3 (i - y) + 1], J[3 i + 2],
+    // J[3 (i - z) + 2] (x+1, x-1, y+1, y-1, z+1, z-1 neighbours), bytes 6, 7 zero
+    const unsigned long long *J6;
 };
 
 // A block of the sweep grid: which group, first walker, walkers in the block,
@@ -121,8 +125,9 @@ cudaError_t launch_sweeps_scan(int L, const GroupDev *groups_dev, const BlockDes
                                int n_blocks, size_t smem_bytes, uint32_t seed, uint64_t sweep0,
                                int n_sweeps, int64_t ts_pos, bool record, cudaStream_t st);
 // Sweeps of groups with couplings per bond (bonds.cu): blocks of one warp,
-// one thread per walker, BlockDesc.nw <= 32 walkers (P = 1).
-cudaError_t launch_sweeps_bonds(const GroupDev *groups_dev, const BlockDesc *blocks_dev,
+// one thread per walker, BlockDesc.nw <= 32 walkers (P = 1); one launch per
+// row length L, on blocks that all belong to groups of that L.
+cudaError_t launch_sweeps_bonds(int L, const GroupDev *groups_dev, const BlockDesc *blocks_dev,
                                 int n_blocks, uint32_t seed, uint64_t sweep0, int n_sweeps,
                                 int64_t ts_pos, bool record, cudaStream_t st);
 // Bytes of one walker's lattice (padded rows), of a shared-memory tile, and of

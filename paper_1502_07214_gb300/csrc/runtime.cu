@@ -53,6 +53,7 @@ struct Group {
     // the device, |J| <= jmax (0: the clean model), and its table
     // [nE][3][24 jmax + 1] on the device and pinned on the host
     int8_t *d_J = nullptr;
+    unsigned long long *d_J6 = nullptr;  // per-site pack of the six couplings
     int jmax = 0;
     std::vector<int8_t> J;
     uint32_t *thrJ = nullptr, *h_thrJ = nullptr;
@@ -97,6 +98,8 @@ struct muca_ctx {
         size_t smem;
     };
     std::vector<ScanRange> scan_ranges;
+    // the disordered model's blocks (kind 5), sorted by L: one launch per L
+    std::vector<ScanRange> bond_ranges;
     std::vector<cudaStream_t> scan_streams;
     std::vector<cudaEvent_t> scan_events;
 };
@@ -348,6 +351,7 @@ GroupDev dev_of(const Group &g)
     d.J = g.jmax ? g.d_J : nullptr;
     d.jmax = g.jmax;
     d.thrJ = g.jmax ? g.thrJ : nullptr;
+    d.J6 = g.jmax ? g.d_J6 : nullptr;
     return d;
 }
 
@@ -378,8 +382,8 @@ int kind_of(const Group &g)
 // Walkers per warp of the disordered model's kernel: the walkers are spread
 // over about four warps per SM (a power of 2, at most 32; at least 8 keep
 // whole 32-byte sectors per packed-word load).  Measured at 4096 walkers of
-// L = 24: 8 per warp 1.58e10 attempts/s, 32 per warp 1.45e10 (each warp's
-// per-site chain is the limit either way).
+// L = 24 with the site-by-site kernel: 8 per warp 1.58e10 attempts/s, 32 per
+// warp 1.45e10 (each warp's per-site chain is the limit either way).
 int bonds_walkers_per_warp(int W)
 {
     int dev = 0, nsm = 0;
@@ -415,9 +419,16 @@ int build_blocks(muca_ctx *ctx)
     for (int k = 0; k < kKinds; ++k)
         std::stable_sort(b[k].begin(), b[k].end(), [&](const BlockDesc &x, const BlockDesc &y) {
             const int lx = ctx->g[x.group].L, ly = ctx->g[y.group].L;
-            if (k == 4 && lx != ly) return lx > ly;
+            if ((k == 4 || k == 5) && lx != ly) return lx > ly;
             return (int64_t)x.nw * ctx->g[x.group].V > (int64_t)y.nw * ctx->g[y.group].V;
         });
+    ctx->bond_ranges.clear();
+    for (int i = 0; i < (int)b[5].size(); ++i) {
+        const int L = ctx->g[b[5][i].group].L;
+        if (ctx->bond_ranges.empty() || ctx->bond_ranges.back().L != L)
+            ctx->bond_ranges.push_back({L, i, 0, 0});
+        ++ctx->bond_ranges.back().count;
+    }
     ctx->scan_ranges.clear();
     for (int i = 0; i < (int)b[4].size(); ++i) {
         const int L = ctx->g[b[4][i].group].L;
@@ -499,8 +510,9 @@ int launch_all(muca_ctx *ctx, int n_sweeps, bool record, cudaStream_t st)
     if (ctx->n_blocks[5] > 0) {
         cudaStream_t s = fork ? ctx->side[5] : st;
         if (fork) CK(cudaStreamWaitEvent(s, ctx->ev_fork, 0));
-        CK(launch_sweeps_bonds(ctx->d_groups, ctx->d_blocks[5], ctx->n_blocks[5], ctx->seed,
-                               ctx->sweep, n_sweeps, ctx->ts_len, record, s));
+        for (const auto &rg : ctx->bond_ranges)
+            CK(launch_sweeps_bonds(rg.L, ctx->d_groups, ctx->d_blocks[5] + rg.first, rg.count,
+                                   ctx->seed, ctx->sweep, n_sweeps, ctx->ts_len, record, s));
         if (fork) {
             CK(cudaEventRecord(ctx->ev_join[5], s));
             CK(cudaStreamWaitEvent(st, ctx->ev_join[5], 0));
@@ -822,9 +834,11 @@ static void free_group(Group &g)
     cudaFreeHost(g.h_thr);
     cudaFreeHost(g.h_hist);
     cudaFree(g.d_J);
+    cudaFree(g.d_J6);
     cudaFree(g.thrJ);
     cudaFreeHost(g.h_thrJ);
     g.d_J = nullptr;
+    g.d_J6 = nullptr;
     g.thrJ = nullptr;
     g.h_thrJ = nullptr;
     g.jmax = 0;
@@ -1152,9 +1166,11 @@ int apply_bonds(muca_ctx *ctx, int group, const int8_t *J, int jmax, bool retall
     Group &g = ctx->g[group];
     CK(cudaStreamSynchronize(ctx->stream));
     cudaFree(g.d_J);
+    cudaFree(g.d_J6);
     cudaFree(g.thrJ);
     cudaFreeHost(g.h_thrJ);
     g.d_J = nullptr;
+    g.d_J6 = nullptr;
     g.thrJ = nullptr;
     g.h_thrJ = nullptr;
     g.jmax = 0;
@@ -1164,6 +1180,27 @@ int apply_bonds(muca_ctx *ctx, int group, const int8_t *J, int jmax, bool retall
         g.J.assign(J, J + (size_t)3 * g.V);
         CK(cudaMalloc(&g.d_J, (size_t)3 * g.V));
         CK(cudaMemcpy(g.d_J, J, (size_t)3 * g.V, cudaMemcpyHostToDevice));
+        // the per-site pack: byte 2 mu + 0 the forward bond of the site, byte
+        // 2 mu + 1 the forward bond of its backward neighbour in direction mu
+        std::vector<unsigned long long> j6((size_t)g.V, 0ull);
+        const int L = g.L;
+        for (int z = 0; z < L; ++z)
+            for (int y = 0; y < L; ++y)
+                for (int x = 0; x < L; ++x) {
+                    const int i = x + L * (y + L * z);
+                    const int back[3] = {(x + L - 1) % L + L * (y + L * z),
+                                         x + L * ((y + L - 1) % L + L * z),
+                                         x + L * (y + L * ((z + L - 1) % L))};
+                    unsigned long long w = 0ull;
+                    for (int mu = 0; mu < 3; ++mu) {
+                        w |= (unsigned long long)(uint8_t)J[3 * i + mu] << (16 * mu);
+                        w |= (unsigned long long)(uint8_t)J[3 * back[mu] + mu] << (16 * mu + 8);
+                    }
+                    j6[(size_t)i] = w;
+                }
+        CK(cudaMalloc(&g.d_J6, j6.size() * sizeof(unsigned long long)));
+        CK(cudaMemcpy(g.d_J6, j6.data(), j6.size() * sizeof(unsigned long long),
+                      cudaMemcpyHostToDevice));
         CK(cudaMalloc(&g.thrJ, bonds_table_words(g) * sizeof(uint32_t)));
         CK(cudaMallocHost(&g.h_thrJ, bonds_table_words(g) * sizeof(uint32_t)));
     }
