@@ -98,16 +98,35 @@ __global__ void bin_kernel(const int32_t *__restrict__ ej, const int32_t *__rest
 }
 
 // ------------------------------------------------- stage A through buckets
-// The same integer bin sums, formed without one global atomic per sample:
-// samples are counted per bucket of kBkt consecutive bins, scattered into
-// bucket order as 8-byte records, and each bucket's records are summed in
-// shared memory before one global add per bin and block.  A record holds the
-// bin offset, E_J (|E_J| < 2^20) and |M| (<= 2^18, so M^4 < 2^72); a sample
-// outside those ranges is added straight to the global sums instead and
-// leaves a null record.
-constexpr int kBktBits = 11;
+// The same integer bin sums, formed without one global atomic per sample and
+// without one shared atomic per sum.  Bins are grouped into buckets of kBkt
+// consecutive bins.  Four launches per pass:
+//   1. count: each block counts its samples per bucket and writes one counter
+//      per (bucket, block);
+//   2. scan: one block gives every (bucket, block) segment two places: where
+//      its records are stored (block-major: a block's records of every bucket
+//      in one region, so that a block writes to one neighbourhood of memory)
+//      and where they stand in bucket order (bucket-major), the order the sums
+//      walk in;
+//   3. scatter: each block re-reads the same samples, takes places from its
+//      own shared cursors and writes 8-byte records;
+//   4. sums: each block takes an equal share of the records in bucket order,
+//      gathering a bucket's segments through a table in shared memory,
+//      counting-sorts tiles of them by bin in shared memory (one 32-bit shared
+//      atomic per record), and every thread sums the run of its own bin in
+//      registers; a bucket's sums go to the global bins once per block.
+// A record holds the bin offset, E_J (|E_J| < 2^20) and |M| (<= 2^18, so
+// M^4 <= 2^72); a sample outside those ranges is added straight to the global
+// sums instead and leaves a null record.  Every sum stays an exact integer, so
+// the result does not depend on the order in which records are summed.
+constexpr int kBktBits = 10;
 constexpr int kBkt = 1 << kBktBits;
 constexpr unsigned kNullRec = 0xFFFFFFFFu;
+constexpr int kMaxBk = 1024;      // buckets of the bucketed path (n_e <= 2^20)
+constexpr int kMaxG = 1024;       // blocks of the count and scatter launches
+constexpr int kCsThreads = 1024;  // threads of a count or scatter block
+constexpr int kCsPer = 4;         // samples per thread and chunk
+constexpr int kChunk = kCsThreads * kCsPer;  // samples of one row per chunk
 
 __device__ __forceinline__ void direct_add(const Bins &b, int e, long long j, unsigned long long am)
 {
@@ -122,150 +141,323 @@ __device__ __forceinline__ void direct_add(const Bins &b, int e, long long j, un
     if (m4hi + carry) atomicAdd(b.sm4hi + e, m4hi + carry);
 }
 
-// Samples per bucket; flags a sample outside [e_min, e_min + nE).
-__global__ void bucket_count_kernel(const int32_t *__restrict__ ed, int64_t n_rows, int row_len,
-                                    int64_t row_stride, int e_min, int nE, int nbk,
-                                    unsigned *cnt, int *err)
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned v)
 {
-    extern __shared__ unsigned sc[];
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned u = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += u;
+    }
+    return v;
+}
+
+// Chunks of one block: chunk t is columns [(t % cpr) kChunk, + kChunk) of row
+// t / cpr, and block i takes chunks [n i / G, n (i+1) / G) of the n = rows x
+// cpr chunks.  The count and scatter launches share this partition; a block
+// walks its chunks as (row, chunk of the row) without dividing per chunk.
+struct ChunkWalk {
+    int64_t t, t1, row;
+    int ci;
+    __device__ __forceinline__ ChunkWalk(int64_t n_rows, int cpr)
+    {
+        const int64_t n = n_rows * cpr;
+        t = n * blockIdx.x / gridDim.x;
+        t1 = n * (blockIdx.x + 1) / gridDim.x;
+        row = t / cpr;
+        ci = (int)(t - row * cpr);
+    }
+    __device__ __forceinline__ void next(int cpr)
+    {
+        ++t;
+        if (++ci == cpr) {
+            ci = 0;
+            ++row;
+        }
+    }
+};
+
+// This thread's kCsPer values of one column in columns [col0, col0 + kChunk)
+// of a row (0 past the row's end).
+__device__ __forceinline__ void load_chunk(const int32_t *__restrict__ row, int col0, int row_len,
+                                           int (&v)[kCsPer])
+{
+#pragma unroll
+    for (int q = 0; q < kCsPer; ++q) {
+        const int c = col0 + q * kCsThreads + threadIdx.x;
+        v[q] = c < row_len ? __ldg(row + c) : 0;
+    }
+}
+
+// Samples per (bucket, block), written to cnt[bucket * gridDim.x + block];
+// flags a sample outside [e_min, e_min + nE).
+__global__ void __launch_bounds__(kCsThreads)
+bucket_count_kernel(const int32_t *__restrict__ ed, int64_t n_rows, int row_len,
+                    int64_t row_stride, int e_min, int nE, int nbk, int cpr,
+                    unsigned *__restrict__ cnt, int *err)
+{
+    __shared__ unsigned sc[kMaxBk];
     for (int i = threadIdx.x; i < nbk; i += blockDim.x) sc[i] = 0u;
     __syncthreads();
-    for (int64_t r = blockIdx.y; r < n_rows; r += gridDim.y)
-        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < row_len;
-             c += gridDim.x * blockDim.x) {
-            const int e = bin_offset(__ldg(ed + r * row_stride + c), e_min);
-            if ((unsigned)e >= (unsigned)nE) atomicOr(err, 1);
-            else atomicAdd(&sc[e >> kBktBits], 1u);
+    for (ChunkWalk w(n_rows, cpr); w.t < w.t1; w.next(cpr)) {
+        const int col0 = w.ci * kChunk;
+        int v[kCsPer];
+        load_chunk(ed + w.row * row_stride, col0, row_len, v);
+#pragma unroll
+        for (int q = 0; q < kCsPer; ++q) {
+            const int c = col0 + q * kCsThreads + threadIdx.x;
+            const int e = bin_offset(v[q], e_min);
+            const bool in = c < row_len, ok = in && (unsigned)e < (unsigned)nE;
+            if (in && !ok) atomicOr(err, 1);
+            if (ok) atomicAdd(&sc[(unsigned)e >> kBktBits], 1u);
         }
+    }
     __syncthreads();
-    for (int i = threadIdx.x; i < nbk; i += blockDim.x)
-        if (sc[i]) atomicAdd(cnt + i, sc[i]);
+    for (int i = threadIdx.x; i < nbk; i += blockDim.x) cnt[(size_t)i * gridDim.x + blockIdx.x] = sc[i];
 }
 
-constexpr int kScatterPer = 4;
-
-// Records into bucket order: bucket k occupies [start_k, start_k + cnt_k),
-// start the prefix sums of cnt; cur[k] hands out the blocks' places in it.
+// One block of 1024 threads.  In: cnt[k * g + b], the samples of bucket k in
+// count block b (g <= 1024 blocks).  Out: lst[k * g + b], the segment's first
+// place in bucket order; cnt[k * g + b] (in place), its first place in the
+// record buffer (block b's segments of buckets 0, 1, ... one after another,
+// after those of blocks 0 .. b-1); bstart / bcnt, each bucket's first place in
+// bucket order and its size.
 __global__ void __launch_bounds__(1024)
+bucket_scan_kernel(unsigned *cnt, unsigned *lst, int nbk, int g, unsigned *bstart, unsigned *bcnt)
+{
+    __shared__ unsigned tot[kMaxBk];
+    __shared__ unsigned ws[32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = w; k < nbk; k += 32) {
+        unsigned s = 0u;
+        for (int b = lane; b < g; b += 32) s += cnt[(size_t)k * g + b];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) tot[k] = s;
+    }
+    __syncthreads();
+    // bucket order: exclusive scan of the bucket totals
+    {
+        const unsigned v = (int)threadIdx.x < nbk ? tot[threadIdx.x] : 0u;
+        const unsigned incl = warp_incl_scan(v);
+        if (lane == 31) ws[w] = incl;
+        __syncthreads();
+        const unsigned wv = ws[lane];
+        const unsigned wi = warp_incl_scan(wv);
+        const unsigned wex = __shfl_sync(0xffffffffu, wi - wv, w);
+        __syncthreads();
+        if ((int)threadIdx.x < nbk) {
+            tot[threadIdx.x] = wex + incl - v;
+            bstart[threadIdx.x] = wex + incl - v;
+            bcnt[threadIdx.x] = v;
+        }
+        __syncthreads();
+    }
+    for (int k = w; k < nbk; k += 32) {
+        unsigned run = tot[k];
+        for (int b0 = 0; b0 < g; b0 += 32) {
+            const int b = b0 + lane;
+            const unsigned x = b < g ? cnt[(size_t)k * g + b] : 0u;
+            const unsigned xi = warp_incl_scan(x);
+            if (b < g) lst[(size_t)k * g + b] = run + xi - x;
+            run += __shfl_sync(0xffffffffu, xi, 31);
+        }
+    }
+    // storage order: thread b sums its block's counts, scans them over the
+    // blocks, then lays its segments out bucket after bucket
+    const int b = threadIdx.x;
+    unsigned bt = 0u;
+    if (b < g)
+        for (int k = 0; k < nbk; ++k) bt += cnt[(size_t)k * g + b];
+    const unsigned incl = warp_incl_scan(bt);
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    const unsigned wv = ws[lane];
+    const unsigned wi = warp_incl_scan(wv);
+    unsigned run = __shfl_sync(0xffffffffu, wi - wv, w) + incl - bt;
+    if (b < g)
+        for (int k = 0; k < nbk; ++k) {
+            const unsigned x = cnt[(size_t)k * g + b];
+            cnt[(size_t)k * g + b] = run;
+            run += x;
+        }
+}
+
+// Records: the block's samples of bucket k take places off[k * gridDim.x +
+// block], +1, ... (the scan's storage places), handed out by shared cursors.
+// A record is
+// (bin offset in its bucket | (E_J + 2^20) << kBktBits, |M|).
+__global__ void __launch_bounds__(kCsThreads)
 bucket_scatter_kernel(const int32_t *__restrict__ ej, const int32_t *__restrict__ ed,
                       const int32_t *__restrict__ m, int64_t n_rows, int row_len,
-                      int64_t row_stride, int e_min, int nE, int nbk,
-                      const unsigned *__restrict__ cnt, unsigned *cur, uint2 *rec, Bins b)
+                      int64_t row_stride, int e_min, int nE, int nbk, int cpr,
+                      const unsigned *__restrict__ off, uint2 *__restrict__ rec, Bins b)
 {
-    extern __shared__ unsigned s2[];
-    unsigned *start = s2, *lc = s2 + nbk, *base = s2 + 2 * nbk;
-    if (threadIdx.x == 0) {
-        unsigned acc = 0u;
-        for (int i = 0; i < nbk; ++i) {
-            start[i] = acc;
-            acc += cnt[i];
+    __shared__ unsigned cur[kMaxBk];
+    for (int i = threadIdx.x; i < nbk; i += blockDim.x)
+        cur[i] = off[(size_t)i * gridDim.x + blockIdx.x];
+    __syncthreads();
+    for (ChunkWalk w(n_rows, cpr); w.t < w.t1; w.next(cpr)) {
+        const int col0 = w.ci * kChunk;
+        const int64_t base = w.row * row_stride;
+        int vd[kCsPer], vj[kCsPer], vm[kCsPer];
+        load_chunk(ed + base, col0, row_len, vd);
+        load_chunk(ej + base, col0, row_len, vj);
+        load_chunk(m + base, col0, row_len, vm);
+#pragma unroll
+        for (int q = 0; q < kCsPer; ++q) {
+            const int c = col0 + q * kCsThreads + threadIdx.x;
+            const int e = bin_offset(vd[q], e_min);
+            const bool ok = c < row_len && (unsigned)e < (unsigned)nE;
+            if (!ok) continue;
+            const unsigned pos = atomicAdd(&cur[(unsigned)e >> kBktBits], 1u);
+            const int j = vj[q], mm = vm[q];
+            const unsigned am = mm < 0 ? 0u - (unsigned)mm : (unsigned)mm;
+            uint2 rr;
+            if (j > -(1 << 20) && j < (1 << 20) && am <= (1u << 18)) {
+                rr.x = ((unsigned)e & (kBkt - 1)) | ((unsigned)(j + (1 << 20)) << kBktBits);
+                rr.y = am;
+            } else {
+                direct_add(b, e, j, am);
+                rr.x = 0u;
+                rr.y = kNullRec;
+            }
+            rec[pos] = rr;
         }
     }
-    // a tile is kScatterPer samples per thread of one row
-    const int tile = kScatterPer * blockDim.x;
-    for (int64_t r = blockIdx.y; r < n_rows; r += gridDim.y)
-        for (int c0 = blockIdx.x * tile; c0 < row_len; c0 += gridDim.x * tile) {
-            for (int i = threadIdx.x; i < nbk; i += blockDim.x) lc[i] = 0u;
-            __syncthreads();
-            int e[kScatterPer], bk[kScatterPer];
-            unsigned rank[kScatterPer];
-#pragma unroll
-            for (int q = 0; q < kScatterPer; ++q) {
-                const int c = c0 + q * blockDim.x + threadIdx.x;
-                e[q] = -1;
-                bk[q] = 0;
-                rank[q] = 0u;
-                if (c < row_len) {
-                    const int ee = bin_offset(__ldg(ed + r * row_stride + c), e_min);
-                    if ((unsigned)ee < (unsigned)nE) {
-                        e[q] = ee;
-                        bk[q] = ee >> kBktBits;
-                        rank[q] = atomicAdd(&lc[bk[q]], 1u);
-                    }
-                }
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < nbk; i += blockDim.x)
-                if (lc[i]) base[i] = atomicAdd(cur + i, lc[i]);
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < kScatterPer; ++q) {
-                if (e[q] < 0) continue;
-                const int64_t o = r * row_stride + c0 + q * blockDim.x + threadIdx.x;
-                const int j = __ldg(ej + o), mm = __ldg(m + o);
-                const unsigned am = mm < 0 ? 0u - (unsigned)mm : (unsigned)mm;
-                uint2 rr;
-                if (j > -(1 << 20) && j < (1 << 20) && am <= (1u << 18)) {
-                    rr.x = (unsigned)(e[q] & (kBkt - 1)) | ((unsigned)(j + (1 << 20)) << kBktBits);
-                    rr.y = am;
-                } else {
-                    direct_add(b, e[q], j, am);
-                    rr.x = 0u;
-                    rr.y = kNullRec;
-                }
-                rec[start[bk[q]] + base[bk[q]] + rank[q]] = rr;
-            }
-            __syncthreads();
-        }
 }
 
-// Sums of bucket blockIdx.y's records in shared memory (M^4 as 36-bit limbs,
-// exact for the at most 2^26 records of a pass), then one global add per bin.
-constexpr int kHistThreads = 512;
-constexpr size_t kHistSmem = (size_t)kBkt * (5 * sizeof(unsigned long long) + sizeof(unsigned));
+// Stage A sums.  Block i takes places [total i / G, total (i+1) / G) of
+// bucket order; within each bucket it gathers tiles of kHS records through the
+// bucket's segment table (place in bucket order -> place in the buffer), sorts
+// each tile by bin in shared memory, and thread t sums bin t of the bucket in
+// registers (count, E_J + 2^20, |M|, M^2 and M^4), which go to the global sums
+// at the end of the bucket.  The sort buffers are double buffered, so a tile
+// needs four barriers.
+constexpr int kHT = kBkt;
+constexpr int kHS = 8192;
+constexpr int kHRpt = kHS / kHT;
+constexpr size_t kHistSmem = 2 * (size_t)kHS * sizeof(uint2) + 3 * (size_t)kBkt * sizeof(unsigned) +
+                             32 * sizeof(unsigned) + (2 * (size_t)kMaxG + 1) * sizeof(unsigned);
 
-__global__ void __launch_bounds__(kHistThreads)
-bucket_hist_kernel(const uint2 *__restrict__ rec, const unsigned *__restrict__ cnt, Bins b)
-{
-    extern __shared__ __align__(16) unsigned long long h64[];
-    unsigned long long *sej = h64, *sam = h64 + kBkt, *sm2 = h64 + 2 * kBkt, *l4 = h64 + 3 * kBkt,
-                       *h4 = h64 + 4 * kBkt;
-    unsigned *sc = (unsigned *)(h64 + 5 * kBkt);
-    __shared__ unsigned s_start, s_n;
-    const int bk = blockIdx.y;
-    if (threadIdx.x == 0) {
-        unsigned acc = 0u;
-        for (int i = 0; i < bk; ++i) acc += cnt[i];
-        s_start = acc;
-        s_n = cnt[bk];
+// Sums of one bin.  M^4 is kept as three 64-bit sums of 36-bit products: with
+// M^2 = h 2^18 + l (h, l < 2^18), M^4 = h^2 2^36 + 2 h l 2^18 + l^2, exact for
+// up to 2^28 records; the 128-bit value is formed once, at the flush.
+struct BinAcc {
+    unsigned n = 0u;
+    unsigned long long j = 0ull, a = 0ull, q = 0ull, s0 = 0ull, s1 = 0ull, s2 = 0ull;
+    __device__ __forceinline__ void add(uint2 r)
+    {
+        const unsigned am = r.y;
+        const unsigned long long m2 = (unsigned long long)am * am;
+        const unsigned h = (unsigned)(m2 >> 18), l = (unsigned)m2 & 0x3FFFFu;
+        n += 1u;
+        j += r.x >> kBktBits;
+        a += am;
+        q += m2;
+        s0 += (unsigned long long)l * l;
+        s1 += (unsigned long long)h * l;
+        s2 += (unsigned long long)h * h;
     }
-    __syncthreads();
-    const unsigned start = s_start, n = s_n;
-    if ((unsigned long long)blockIdx.x * blockDim.x >= n) return;
-    for (int i = threadIdx.x; i < kBkt; i += blockDim.x) {
-        sej[i] = sam[i] = sm2[i] = l4[i] = h4[i] = 0ull;
-        sc[i] = 0u;
-    }
-    __syncthreads();
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint2 r = rec[start + i];
-        if (r.y == kNullRec) continue;
-        const int eo = (int)(r.x & (kBkt - 1));
-        const long long j = (long long)(r.x >> kBktBits) - (1 << 20);
-        const unsigned long long am = r.y, m2 = am * am;
-        const unsigned long long m4lo = m2 * m2, m4hi = __umul64hi(m2, m2);
-        atomicAdd(&sc[eo], 1u);
-        atomicAdd(&sej[eo], (unsigned long long)j);
-        atomicAdd(&sam[eo], am);
-        atomicAdd(&sm2[eo], m2);
-        atomicAdd(&l4[eo], m4lo & ((1ull << 36) - 1));
-        const unsigned long long hi = (m4lo >> 36) | (m4hi << 28);
-        if (hi) atomicAdd(&h4[eo], hi);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kBkt; i += blockDim.x) {
-        const unsigned k = sc[i];
-        if (!k) continue;
-        const int e = bk * kBkt + i;
-        atomicAdd(b.cnt + e, (unsigned long long)k);
-        atomicAdd(b.sej + e, sej[i]);
-        atomicAdd(b.sam + e, sam[i]);
-        atomicAdd(b.sm2 + e, sm2[i]);
-        const unsigned __int128 q = ((unsigned __int128)h4[i] << 36) + l4[i];
-        const unsigned long long lo = (unsigned long long)q, hi = (unsigned long long)(q >> 64);
+    __device__ __forceinline__ void flush(const Bins &b, int e)
+    {
+        if (!n) return;
+        atomicAdd(b.cnt + e, (unsigned long long)n);
+        atomicAdd(b.sej + e, j - ((unsigned long long)n << 20));
+        atomicAdd(b.sam + e, a);
+        atomicAdd(b.sm2 + e, q);
+        const unsigned __int128 m4 = ((unsigned __int128)s2 << 36) + ((unsigned __int128)s1 << 19) + s0;
+        const unsigned long long lo = (unsigned long long)m4, hi = (unsigned long long)(m4 >> 64);
         const unsigned long long old = atomicAdd(b.sm4lo + e, lo);
         const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
         if (hi + carry) atomicAdd(b.sm4hi + e, hi + carry);
+        n = 0u;
+        j = a = q = s0 = s1 = s2 = 0ull;
+    }
+};
+
+__global__ void __launch_bounds__(kHT, 1)
+bucket_hist_kernel(const uint2 *__restrict__ rec, const unsigned *__restrict__ pst,
+                   const unsigned *__restrict__ lst, int g, const unsigned *__restrict__ bstart,
+                   const unsigned *__restrict__ bcnt, int nbk, unsigned total, Bins b)
+{
+    extern __shared__ __align__(16) unsigned char hsm[];
+    uint2 *srt0 = (uint2 *)hsm;                                  // [2][kHS]
+    unsigned *scnt0 = (unsigned *)(hsm + 2 * kHS * sizeof(uint2)); // [2][kBkt]
+    unsigned *soff = scnt0 + 2 * kBkt;                           // [kBkt]
+    unsigned *wsum = soff + kBkt;                                // [32]
+    unsigned *segL = wsum + 32;                                  // [g + 1] bucket order
+    unsigned *segP = segL + kMaxG + 1;                           // [g] buffer
+    const unsigned lo = (unsigned)((unsigned long long)total * blockIdx.x / gridDim.x);
+    const unsigned hi = (unsigned)((unsigned long long)total * (blockIdx.x + 1) / gridDim.x);
+    if (lo >= hi) return;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < 2 * kBkt; i += kHT) scnt0[i] = 0u;
+    int k = 0;
+    while (k < nbk && bstart[k] + bcnt[k] <= lo) ++k;
+    BinAcc acc;
+    int buf = 0;
+    for (; k < nbk && bstart[k] < hi; ++k) {
+        const unsigned s_lo = max(lo, bstart[k]), s_hi = min(hi, bstart[k] + bcnt[k]);
+        // the bucket's segment table (the previous bucket's last reads are done)
+        __syncthreads();
+        for (int i = tid; i < g; i += kHT) {
+            segL[i] = lst[(size_t)k * g + i];
+            segP[i] = pst[(size_t)k * g + i];
+        }
+        if (tid == 0) segL[g] = bstart[k] + bcnt[k];
+        __syncthreads();
+        // record j of the tile at s0: place s0 + j kHT + tid in bucket order,
+        // in segment sg (segL[sg] <= place < segL[sg + 1]); places only grow
+        int sg = 0;
+        auto load = [&](unsigned s0, uint2 (&r)[kHRpt]) {
+#pragma unroll
+            for (int q = 0; q < kHRpt; ++q) {
+                const unsigned i = s0 + q * kHT + tid;
+                if (i < s_hi) {
+                    while (segL[sg + 1] <= i) ++sg;
+                    r[q] = rec[segP[sg] + (i - segL[sg])];
+                } else {
+                    r[q] = make_uint2(0u, kNullRec);
+                }
+            }
+        };
+        uint2 r[kHRpt];
+        load(s_lo, r);
+        for (unsigned s0 = s_lo; s0 < s_hi; s0 += kHS) {
+            unsigned *scnt = scnt0 + buf * kBkt;
+            uint2 *srt = srt0 + buf * kHS;
+            unsigned rk[kHRpt];
+#pragma unroll
+            for (int q = 0; q < kHRpt; ++q)
+                rk[q] = r[q].y != kNullRec ? atomicAdd(&scnt[r[q].x & (kBkt - 1)], 1u) : 0u;
+            __syncthreads();
+            const unsigned c = scnt[tid];
+            const unsigned incl = warp_incl_scan(c);
+            if (lane == 31) wsum[w] = incl;
+            __syncthreads();
+            const unsigned wv = wsum[lane];
+            const unsigned wi = warp_incl_scan(wv);
+            const unsigned o = __shfl_sync(0xffffffffu, wi - wv, w) + incl - c;
+            soff[tid] = o;
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kHRpt; ++q)
+                if (r[q].y != kNullRec) srt[soff[r[q].x & (kBkt - 1)] + rk[q]] = r[q];
+            // the next tile's records, loaded while this tile is summed
+            load(s0 + kHS, r);
+            __syncthreads();
+            unsigned i = o;
+            for (; i + 1 < o + c; i += 2) {
+                const uint2 x = srt[i], y = srt[i + 1];
+                acc.add(x);
+                acc.add(y);
+            }
+            if (i < o + c) acc.add(srt[i]);
+            scnt[tid] = 0u;
+            buf ^= 1;
+        }
+        acc.flush(b, k * kBkt + tid);
     }
 }
 
@@ -647,11 +839,16 @@ Scratch scratch_layout(int nE, int n_grid, int precision)
     return s;
 }
 
-// Bytes of the bucket counters at the start of a record buffer (256-byte aligned).
+// Buckets of a window of nE bins.
+int bucket_count_of(int nE) { return (int)(((int64_t)nE + kBkt - 1) >> kBktBits); }
+
+// Bytes of the bucket counters at the start of a record buffer (256-byte
+// aligned): [nbk][kMaxG] storage places, [nbk][kMaxG] places in bucket order,
+// then each bucket's start and size.
 size_t bucket_counter_bytes(int nE)
 {
-    const size_t nbk = ((size_t)nE + kBkt - 1) >> kBktBits;
-    return (2 * nbk * sizeof(unsigned) + 255) & ~(size_t)255;
+    const size_t nbk = (size_t)bucket_count_of(nE);
+    return ((2 * nbk * kMaxG + 2 * nbk) * sizeof(unsigned) + 255) & ~(size_t)255;
 }
 
 }  // namespace
@@ -660,6 +857,8 @@ namespace muca {
 
 size_t reweight_record_bytes(int32_t n_e, int64_t n_samples)
 {
+    // windows of more than kMaxBk buckets take the direct path: no records
+    if (bucket_count_of(n_e) > kMaxBk) return 0;
     const int64_t cap = std::min<int64_t>(n_samples, (int64_t)1 << 26);
     return bucket_counter_bytes(n_e) + (size_t)std::max<int64_t>(cap, 0) * sizeof(uint2);
 }
@@ -695,38 +894,42 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
     } while (0)
     RCK(cudaMemsetAsync(p, 0, L.bins, st));
     RCK(cudaMemsetAsync(d_err, 0, sizeof(int), st));
-    const int nbk = (n_e + kBkt - 1) >> kBktBits;
+    const int nbk = bucket_count_of(n_e);
     const size_t rec_cap =
-        records ? (records_bytes - std::min(records_bytes, bucket_counter_bytes(n_e))) / sizeof(uint2)
-                : 0;
+        (records && nbk <= kMaxBk)
+            ? (records_bytes - std::min(records_bytes, bucket_counter_bytes(n_e))) / sizeof(uint2)
+            : 0;
     if (n_rows > 0 && row_len > 0 && (size_t)row_len <= rec_cap) {
         // stage A through buckets, a pass of at most rec_cap samples at a time
-        unsigned *d_cnt = (unsigned *)records, *d_cur = d_cnt + nbk;
+        unsigned *d_cnt = (unsigned *)records;  // [nbk][g], g <= kMaxG
+        unsigned *d_lst = d_cnt + (size_t)nbk * kMaxG;
+        unsigned *d_bstart = d_lst + (size_t)nbk * kMaxG, *d_bcnt = d_bstart + nbk;
         uint2 *d_rec = (uint2 *)(records + bucket_counter_bytes(n_e));
         int dev = 0, nsm = 152;
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         RCK(cudaFuncSetAttribute(bucket_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kHistSmem));
+        const int cpr = (int)(((int64_t)row_len + kChunk - 1) / kChunk);
         const int64_t rows_pass = std::min<int64_t>(n_rows, (int64_t)(rec_cap / (size_t)row_len));
         for (int64_t r0 = 0; r0 < n_rows; r0 += rows_pass) {
             const int64_t nr = std::min(rows_pass, n_rows - r0);
             const int64_t off = r0 * row_stride;
-            RCK(cudaMemsetAsync(d_cnt, 0, 2 * (size_t)nbk * sizeof(unsigned), st));
-            dim3 g1((unsigned)std::min<int64_t>((row_len + 255) / 256, 1024),
-                    (unsigned)std::min<int64_t>(nr, 4096));
-            bucket_count_kernel<<<g1, 256, nbk * sizeof(unsigned), st>>>(
-                e_d + off, nr, row_len, row_stride, e_min, n_e, nbk, d_cnt, d_err);
+            // one block per SM: fewer (bucket, block) write streams
+            const int g = (int)std::min<int64_t>(nr * cpr, std::min(nsm, kMaxG));
+            bucket_count_kernel<<<g, kCsThreads, 0, st>>>(e_d + off, nr, row_len, row_stride,
+                                                          e_min, n_e, nbk, cpr, d_cnt,
+                                                          d_err);
             RCK(cudaGetLastError());
-            dim3 g2((unsigned)std::min<int64_t>((row_len + 1024 * kScatterPer - 1) /
-                                                    (1024 * kScatterPer), 1024),
-                    (unsigned)std::min<int64_t>(nr, 4096));
-            bucket_scatter_kernel<<<g2, 1024, 3 * nbk * sizeof(unsigned), st>>>(
-                e_j + off, e_d + off, m + off, nr, row_len, row_stride, e_min, n_e, nbk, d_cnt,
-                d_cur, d_rec, b);
+            bucket_scan_kernel<<<1, 1024, 0, st>>>(d_cnt, d_lst, nbk, g, d_bstart, d_bcnt);
             RCK(cudaGetLastError());
-            dim3 g3((unsigned)std::max(1, (2 * nsm + nbk - 1) / nbk), (unsigned)nbk);
-            bucket_hist_kernel<<<g3, kHistThreads, kHistSmem, st>>>(d_rec, d_cnt, b);
+            bucket_scatter_kernel<<<g, kCsThreads, 0, st>>>(
+                e_j + off, e_d + off, m + off, nr, row_len, row_stride, e_min, n_e, nbk, cpr,
+                d_cnt, d_rec, b);
+            RCK(cudaGetLastError());
+            bucket_hist_kernel<<<nsm, kHT, kHistSmem, st>>>(d_rec, d_cnt, d_lst, g, d_bstart,
+                                                           d_bcnt, nbk, (unsigned)(nr * row_len),
+                                                           b);
             RCK(cudaGetLastError());
         }
     } else if (n_rows > 0 && row_len > 0) {

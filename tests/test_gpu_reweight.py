@@ -174,3 +174,69 @@ def test_bucketed_sums_equal_direct_sums():
                             row_len=row_len, row_stride=row_len, no_alloc=True)
         assert np.isfinite(a).all()
         assert np.array_equal(a, b), p
+
+
+def _context_layout(ej, ed, m):
+    """[sample][field][walker] rows (row stride 3 x walkers), as a context records them."""
+    packed = np.stack([ej, ed, m], axis=1).astype(np.int32)
+    return torch.from_numpy(packed.ravel()).cuda()
+
+
+def test_bucketed_sums_ragged_rows_and_wide_windows():
+    """Stage A's bucketed path against the direct sums and the oracle on the
+    shapes its partition has to get right: rows that are not a whole number
+    of 4096-sample chunks in the context's strided layout, every bucket of a
+    32769-bin window (bit-identical to ``muca_reweight_noalloc``), a 262145-bin
+    window (L = 64: 257 buckets, some empty) and one of more than 1024 buckets
+    (summed directly) against the FP64 oracle, and all samples in one bin."""
+    rng = np.random.default_rng(21)
+    beta = 0.7
+    # 32769 bins, rows of 5000 walkers (one full chunk and a ragged one)
+    S, W, n_e = 700, 5000, 32769
+    ed = rng.integers(0, n_e, (S, W))
+    ej = rng.integers(-3 * (n_e - 1), 3 * (n_e - 1) + 1, (S, W))
+    m = rng.integers(-(n_e - 1), n_e, (S, W))
+    buf = _context_layout(ej, ed, m)
+    base = buf.data_ptr()
+    lnW = wl.random_lnW(n_e, seed=5, scale=2.0, slope=-0.3)
+    grid = np.linspace(0.2, 0.6, 9)
+    for p in (64, 32):
+        kw = dict(n_rows=S, row_len=W, row_stride=3 * W)
+        a = muca().reweight(base, base + 4 * W, base + 8 * W, lnW, 0, beta, n_e - 1, grid, p, **kw)
+        b = muca().reweight(base, base + 4 * W, base + 8 * W, lnW, 0, beta, n_e - 1, grid, p,
+                            no_alloc=True, **kw)
+        assert np.isfinite(a).all() and np.array_equal(a, b), p
+    # 262145 bins, samples only in the lower 3/5 of the window (empty buckets above)
+    S, W, n_e = 300, 4100, 64 ** 3 + 1
+    ed = rng.integers(0, (3 * n_e) // 5, (S, W))
+    ej = rng.integers(-3 * (n_e - 1), 3 * (n_e - 1) + 1, (S, W))
+    m = np.clip(rng.integers(-(n_e - 1), n_e, (S, W)), -ed, ed)
+    buf = _context_layout(ej, ed, m)
+    base = buf.data_ptr()
+    lnW = wl.random_lnW(n_e, seed=6, scale=1.0, slope=-0.35)
+    grid = np.linspace(0.3, 0.45, 5)
+    ref = oracle.reweight(ej, ed, m, lnW, 0, beta, n_e - 1, grid)
+    for p in (64, 32):
+        got = muca().reweight(base, base + 4 * W, base + 8 * W, lnW, 0, beta, n_e - 1, grid, p,
+                              n_rows=S, row_len=W, row_stride=3 * W)
+        assert (rel_err(got, ref) <= TOL[p]).all(), (p, rel_err(got, ref).max(axis=0))
+    # a window of 1026 buckets: the direct path
+    n_e, S, W = (1 << 21) + 2049, 64, 1000
+    ed = rng.integers(0, n_e, (S, W))
+    ej = rng.integers(-1000, 1001, (S, W))
+    m = rng.integers(-1000, 1001, (S, W))
+    lnW = wl.random_lnW(n_e, seed=7, scale=0.01, slope=-0.002)
+    grid = np.linspace(0.001, 0.003, 3)
+    ref = oracle.reweight(ej, ed, m, lnW, 0, beta, n_e - 1, grid)
+    got = muca().reweight(dev(ej), dev(ed), dev(m), lnW, 0, beta, n_e - 1, grid, 64)
+    assert (rel_err(got, ref) <= TOL[64]).all(), rel_err(got, ref).max(axis=0)
+    # 3 x 10^6 samples in one bin (one thread sums a whole tile)
+    n = 3_000_000
+    ed = np.full(n, 33)
+    ej = rng.integers(-300, 301, n)
+    m = rng.integers(-64, 65, n)
+    lnW = np.zeros(65)
+    a = muca().reweight(dev(ej), dev(ed), dev(m), lnW, 0, 0.5, 64, [0.5, 3.0], 64)
+    b = muca().reweight(dev(ej), dev(ed), dev(m), lnW, 0, 0.5, 64, [0.5, 3.0], 64, no_alloc=True)
+    assert np.array_equal(a, b)
+    assert np.allclose(a[:, 0], ej.mean(), rtol=1e-12)
