@@ -199,18 +199,29 @@ bucket_count_kernel(const int32_t *__restrict__ ed, int64_t n_rows, int row_len,
     __shared__ unsigned sc[kMaxBk];
     for (int i = threadIdx.x; i < nbk; i += blockDim.x) sc[i] = 0u;
     __syncthreads();
-    for (ChunkWalk w(n_rows, cpr); w.t < w.t1; w.next(cpr)) {
-        const int col0 = w.ci * kChunk;
-        int v[kCsPer];
-        load_chunk(ed + w.row * row_stride, col0, row_len, v);
-#pragma unroll
-        for (int q = 0; q < kCsPer; ++q) {
-            const int c = col0 + q * kCsThreads + threadIdx.x;
-            const int e = bin_offset(v[q], e_min);
-            const bool in = c < row_len, ok = in && (unsigned)e < (unsigned)nE;
-            if (in && !ok) atomicOr(err, 1);
-            if (ok) atomicAdd(&sc[(unsigned)e >> kBktBits], 1u);
+    // two chunks per step, so that twice the loads are in flight
+    for (ChunkWalk w(n_rows, cpr); w.t < w.t1;) {
+        int col[2];
+        int v[2][kCsPer];
+        col[0] = w.ci * kChunk;
+        load_chunk(ed + w.row * row_stride, col[0], row_len, v[0]);
+        w.next(cpr);
+        const bool two = w.t < w.t1;
+        col[1] = two ? w.ci * kChunk : row_len;
+        if (two) {
+            load_chunk(ed + w.row * row_stride, col[1], row_len, v[1]);
+            w.next(cpr);
         }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int q = 0; q < kCsPer; ++q) {
+                const int c = col[h] + q * kCsThreads + threadIdx.x;
+                const int e = bin_offset(v[h][q], e_min);
+                const bool in = c < row_len, ok = in && (unsigned)e < (unsigned)nE;
+                if (in && !ok) atomicOr(err, 1);
+                if (ok) atomicAdd(&sc[(unsigned)e >> kBktBits], 1u);
+            }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nbk; i += blockDim.x) cnt[(size_t)i * gridDim.x + blockIdx.x] = sc[i];
@@ -409,14 +420,21 @@ bucket_hist_kernel(const uint2 *__restrict__ rec, const unsigned *__restrict__ p
         __syncthreads();
         // record j of the tile at s0: place s0 + j kHT + tid in bucket order,
         // in segment sg (segL[sg] <= place < segL[sg + 1]); places only grow
+        // (the segment's end in bucket order and its buffer offset are kept in
+        // registers; unsigned wrap-around makes i + dlt the buffer place)
         int sg = 0;
+        unsigned send = segL[1], dlt = segP[0] - segL[0];
         auto load = [&](unsigned s0, uint2 (&r)[kHRpt]) {
 #pragma unroll
             for (int q = 0; q < kHRpt; ++q) {
                 const unsigned i = s0 + q * kHT + tid;
                 if (i < s_hi) {
-                    while (segL[sg + 1] <= i) ++sg;
-                    r[q] = rec[segP[sg] + (i - segL[sg])];
+                    while (send <= i) {
+                        ++sg;
+                        send = segL[sg + 1];
+                        dlt = segP[sg] - segL[sg];
+                    }
+                    r[q] = rec[i + dlt];
                 } else {
                     r[q] = make_uint2(0u, kNullRec);
                 }
