@@ -16,9 +16,13 @@
 //
 // GPU layout: one pass over the series forms exact integer sums (count, sum
 // E_J) per bin and per jackknife block; each data set's sums are all blocks'
-// sums minus the left-out block's (integers, exact); one thread block per data
-// set then runs the whole bisection, each step three FP64 passes over the
-// bins (largest weight, weighted means, centred moments).
+// sums minus the left-out block's (integers, exact); one thread-block cluster
+// per data set then runs the whole bisection, each step three FP64 passes over
+// the bins (largest weight, weighted means, centred moments), every CTA of the
+// cluster over its own slice of the bins, the CTAs' partial results combined
+// through distributed shared memory in rank order (so that every CTA holds
+// the same numbers and takes the same bisection step).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -30,6 +34,8 @@
 #include "muca_internal.h"
 
 namespace {
+
+namespace cg = cooperative_groups;
 
 // Integer sums per jackknife block: cnt[b][E], sej[b][E].  bnd[i] is the first
 // row of block i (bnd[n_blocks] = n_rows).
@@ -92,9 +98,10 @@ struct KS {  // Kahan-compensated FP64 sum
 
 constexpr int kPkThreads = 256;
 
-// Sum over the block of K compensated sums (every thread gets the results).
+// Sum over the block of K compensated sums: every thread gets each sum as a
+// pair (tot, cc) whose value is tot - cc.
 template <int K>
-__device__ void pk_block_sum(KS (&a)[K], double (&out)[K], double *sh)
+__device__ void pk_block_sum(KS (&a)[K], double (&tot)[K], double (&cc)[K], double *sh)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -115,26 +122,57 @@ __device__ void pk_block_sum(KS (&a)[K], double (&out)[K], double *sh)
             sh[2 * wid + 1] = c;
         }
         __syncthreads();
-        double tot = 0.0, cc = 0.0;
+        double T = 0.0, C = 0.0;
         for (int i = 0; i < nw; ++i) {
-            const double y = sh[2 * i] - cc;
-            const double t = tot + y;
-            cc = (t - tot) - y;
-            tot = t;
-            cc -= sh[2 * i + 1];
+            const double y = sh[2 * i] - C;
+            const double t = T + y;
+            C = (t - T) - y;
+            T = t;
+            C -= sh[2 * i + 1];
         }
-        out[k] = tot - cc;
+        tot[k] = T;
+        cc[k] = C;
+    }
+}
+
+// Partial results of one CTA of a cluster, read by every CTA of the cluster.
+struct PkPart {
+    double av;    // largest exponent over the CTA's bins
+    int aa;       // its bin
+    double s[6];  // weighted sums, (tot, cc) pairs
+    double t[4];  // centred sums, (tot, cc) pairs
+};
+
+// The cluster's sums from its CTAs' (tot, cc) pairs at offset `off` of
+// PkPart (K sums), combined in rank order.
+template <int K>
+__device__ void pk_cluster_sum(cg::cluster_group &cl, PkPart *part, int which, double (&out)[K])
+{
+    const int ncta = (int)cl.num_blocks();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double T = 0.0, C = 0.0;
+        for (int r = 0; r < ncta; ++r) {
+            const PkPart *pr = cl.map_shared_rank(part, r);
+            const double *v = which ? pr->t : pr->s;
+            const double y = v[2 * k] - C;
+            const double t = T + y;
+            C = (t - T) - y;
+            T = t;
+            C += v[2 * k + 1];
+        }
+        out[k] = T - C;
     }
 }
 
 // The bin E* of the largest weight exp(-c E - lnW(E)) among occupied bins
 // (ties to the smaller bin).
-__device__ int pk_argmax(const double *n, const double *lnW, int nE, int e_min, double c, double *sh,
-                         int *shi)
+__device__ int pk_argmax(const double *n, const double *lnW, int e0, int e1, int e_min, double c,
+                         double *sh, int *shi, double &vout)
 {
     double v = -INFINITY;
     int arg = 0x7FFFFFFF;
-    for (int e = threadIdx.x; e < nE; e += blockDim.x)
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += blockDim.x)
         if (n[e] > 0.0) {
             const double a = __dsub_rn(-__dmul_rn(c, (double)(e_min + e)), lnW[e]);
             if (a > v) {
@@ -164,23 +202,43 @@ __device__ int pk_argmax(const double *n, const double *lnW, int nE, int e_min, 
             v = sh[i];
             arg = shi[i];
         }
+    vout = v;
     return arg;
 }
 
 // Covariance <(E_J - <E_J>)(E_Delta - <E_Delta>)> and third moment
-// <(E_J - <E_J>)(E_Delta - <E_Delta>)^2> of the data set at field Delta.
-// wb: this data set's scratch of nE weights; each thread reads back only the
-// weights it wrote, so the second pass needs no synchronisation for them.
-__device__ void pk_moments(const double *n, const double *mj, const double *lnW, int nE, int e_min,
-                           double beta, double delta, double *sh, int *shi, double *wb,
-                           double &cov, double &third)
+// <(E_J - <E_J>)(E_Delta - <E_Delta>)^2> of the data set at field Delta.  This
+// CTA takes bins [e0, e1); the cluster combines the CTAs' partial results
+// (three cluster barriers).  wb: the data set's scratch of nE weights; each
+// thread reads back only the weights it wrote.
+__device__ void pk_moments(cg::cluster_group &cl, PkPart *part, const double *n, const double *mj,
+                           const double *lnW, int nE, int e0, int e1, int e_min, double beta,
+                           double delta, double *sh, int *shi, double *wb, double &cov,
+                           double &third)
 {
     const double c = beta * delta;
-    int es = pk_argmax(n, lnW, nE, e_min, c, sh, shi);
+    double av;
+    int aa = pk_argmax(n, lnW, e0, e1, e_min, c, sh, shi, av);
+    if (threadIdx.x == 0) {
+        part->av = av;
+        part->aa = aa;
+    }
+    cl.sync();
+    double v = -INFINITY;
+    int es = 0x7FFFFFFF;
+    for (int r = 0; r < (int)cl.num_blocks(); ++r) {
+        const PkPart *pr = cl.map_shared_rank(part, r);
+        const double rv = pr->av;
+        const int ra = pr->aa;
+        if (rv > v || (rv == v && ra < es)) {
+            v = rv;
+            es = ra;
+        }
+    }
     if (es >= nE) es = 0;  // no occupied bin: nothing to weigh
     const double lstar = lnW[es];
     KS a[3];
-    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += blockDim.x) {
         const double ne = n[e];
         if (ne <= 0.0) continue;
         const double w =
@@ -190,11 +248,21 @@ __device__ void pk_moments(const double *n, const double *mj, const double *lnW,
         a[1].add(w * mj[e]);
         a[2].add(w * (double)(e_min + e));
     }
+    {
+        double tot[3], cc[3];
+        pk_block_sum<3>(a, tot, cc, sh);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; ++k) {
+                part->s[2 * k] = tot[k];
+                part->s[2 * k + 1] = cc[k];
+            }
+    }
+    cl.sync();
     double S[3];
-    pk_block_sum<3>(a, S, sh);
+    pk_cluster_sum<3>(cl, part, 0, S);
     const double jbar = S[1] / S[0], dbar = S[2] / S[0];
     KS b[2];
-    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += blockDim.x) {
         const double ne = n[e];
         if (ne <= 0.0) continue;
         const double w = wb[e];
@@ -202,13 +270,26 @@ __device__ void pk_moments(const double *n, const double *mj, const double *lnW,
         b[0].add(w * (dj * dd));
         b[1].add(w * (dj * dd * dd));
     }
+    {
+        double tot[2], cc[2];
+        pk_block_sum<2>(b, tot, cc, sh);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 2; ++k) {
+                part->t[2 * k] = tot[k];
+                part->t[2 * k + 1] = cc[k];
+            }
+    }
+    cl.sync();
     double T[2];
-    pk_block_sum<2>(b, T, sh);
+    pk_cluster_sum<2>(cl, part, 1, T);
     cov = T[0] / S[0];
     third = T[1] / S[0];
 }
 
-// One block per data set: bisection on the sign of dC/dDelta in [lo, hi].
+// One cluster per data set: bisection on the sign of dC/dDelta in [lo, hi].
+// Every CTA of a cluster holds the same combined sums, so all take the same
+// steps; a final cluster barrier keeps each CTA's shared memory alive until
+// the others have read it.
 __global__ void __launch_bounds__(kPkThreads)
 peak_kernel(const double *__restrict__ n_all, const double *__restrict__ mj_all,
             const double *__restrict__ lnW, int nE, int e_min, double beta, double lo, double hi,
@@ -216,30 +297,36 @@ peak_kernel(const double *__restrict__ n_all, const double *__restrict__ mj_all,
 {
     __shared__ double sh[64];
     __shared__ int shi[32];
-    const int d = blockIdx.x;
+    __shared__ PkPart part;
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncta = (int)cl.num_blocks(), q = (int)cl.block_rank();
+    const int d = blockIdx.x / ncta;
+    const int e0 = (int)((int64_t)nE * q / ncta), e1 = (int)((int64_t)nE * (q + 1) / ncta);
     const double *n = n_all + (size_t)d * nE, *mj = mj_all + (size_t)d * nE;
     double *wb = wscr + (size_t)d * nE;
     double cov, t_lo, t_hi;
-    pk_moments(n, mj, lnW, nE, e_min, beta, lo, sh, shi, wb, cov, t_lo);
-    pk_moments(n, mj, lnW, nE, e_min, beta, hi, sh, shi, wb, cov, t_hi);
+    pk_moments(cl, &part, n, mj, lnW, nE, e0, e1, e_min, beta, lo, sh, shi, wb, cov, t_lo);
+    pk_moments(cl, &part, n, mj, lnW, nE, e0, e1, e_min, beta, hi, sh, shi, wb, cov, t_hi);
     if (!(t_lo > 0.0 && t_hi < 0.0)) {
-        if (threadIdx.x == 0) bad[d] = 1;
+        if (q == 0 && threadIdx.x == 0) bad[d] = 1;
+        cl.sync();
         return;
     }
     for (int i = 0; i < n_iter; ++i) {
         const double mid = lo + 0.5 * (hi - lo);
         double t;
-        pk_moments(n, mj, lnW, nE, e_min, beta, mid, sh, shi, wb, cov, t);
+        pk_moments(cl, &part, n, mj, lnW, nE, e0, e1, e_min, beta, mid, sh, shi, wb, cov, t);
         if (t > 0.0) lo = mid;
         else hi = mid;
     }
     const double ds = lo + 0.5 * (hi - lo);
     double t;
-    pk_moments(n, mj, lnW, nE, e_min, beta, ds, sh, shi, wb, cov, t);
-    if (threadIdx.x == 0) {
+    pk_moments(cl, &part, n, mj, lnW, nE, e0, e1, e_min, beta, ds, sh, shi, wb, cov, t);
+    if (q == 0 && threadIdx.x == 0) {
         res[2 * d] = ds;
         res[2 * d + 1] = -beta * cov;
     }
+    cl.sync();
 }
 
 // ---------------------------------------------------- equal height, barrier
@@ -452,10 +539,44 @@ extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_
         dim3 g2((unsigned)((n_e + 255) / 256), (unsigned)n_sets);
         jk_stats_kernel<<<g2, 256, 0, st>>>(cnt, sej, n_blocks, n_e, n_all, mj_all);
         PCK(cudaGetLastError());
-        peak_kernel<<<n_sets, kPkThreads, 0, st>>>(n_all, mj_all, d_lnW, n_e, e_min, beta,
-                                                   delta_lo, delta_hi, n_iter, d_res, d_bad + 1,
-                                                   d_w);
-        PCK(cudaGetLastError());
+        // One cluster per data set, one CTA per SM: the CTAs reserve (unused)
+        // dynamic shared memory above half an SM's, and the cluster size is
+        // the largest of 8 .. 1 for which every data set's cluster can be
+        // resident at once (clusters live within a GPC, so the SM count alone
+        // does not tell).
+        int dev = 0, nsm = 152, smem_sm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) {
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        }
+        const size_t one_per_sm = smem_sm > 0 ? (size_t)smem_sm / 2 + 1024 : 0;
+        PCK(cudaFuncSetAttribute(peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)one_per_sm));
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3(kPkThreads);
+        cfg.dynamicSmemBytes = one_per_sm;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncta = std::max(1, std::min(8, nsm / n_sets));
+        for (; ncta > 1; --ncta) {
+            attr[0].val.clusterDim.x = (unsigned)ncta;
+            cfg.gridDim = dim3((unsigned)(n_sets * ncta));
+            int nc = 0;
+            if (cudaOccupancyMaxActiveClusters(&nc, peak_kernel, &cfg) == cudaSuccess &&
+                nc >= n_sets)
+                break;
+        }
+        (void)cudaGetLastError();
+        attr[0].val.clusterDim.x = (unsigned)ncta;
+        cfg.gridDim = dim3((unsigned)(n_sets * ncta));
+        PCK(cudaLaunchKernelEx(&cfg, peak_kernel, (const double *)n_all, (const double *)mj_all,
+                               (const double *)d_lnW, (int)n_e, (int)e_min, beta, delta_lo,
+                               delta_hi, (int)n_iter, d_res, d_bad + 1, d_w));
     }
     PCK(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     PCK(cudaMemcpyAsync(bad.data(), d_bad, bad.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
