@@ -389,16 +389,17 @@ __device__ void eqh_best(double &v, int &a, bool want_max, double *sh, int *shi)
         }
 }
 
-// The two peak bins at Delta (relative to e_min, -1 when a side is empty); returns g.
-__device__ double eqh_peaks(const double *lnn, const double *lnW, int nE, int e_min, int split,
-                            double bd, int &pl, int &pr, double &vl, double &vr, double *sh,
-                            int *shi)
+// The two peak bins at Delta among bins [e0, e1) (relative to e_min, -1 when a
+// side is empty); returns g.
+__device__ double eqh_peaks(const double *lnn, const double *lnW, int e0, int e1, int e_min,
+                            int split, double bd, int &pl, int &pr, double &vl, double &vr,
+                            double *sh, int *shi)
 {
     vl = -INFINITY;
     vr = -INFINITY;
     pl = -1;
     pr = -1;
-    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += blockDim.x) {
         if (lnn[e] == -INFINITY) continue;
         const double v = eqh_lnp(lnn[e], bd, e_min + e, lnW[e]);
         if (e_min + e < split) {
@@ -416,35 +417,91 @@ __device__ double eqh_peaks(const double *lnn, const double *lnW, int nE, int e_
     return vl - vr;
 }
 
+// One CTA's best (value, bin) pairs for the two peaks, or its lowest bin.
+struct EqPart {
+    double vl, vr;
+    int pl, pr;
+};
+
+// Larger (want_max) or smaller value wins, ties to the smaller bin, bin -1 is empty.
+__device__ __forceinline__ bool eqh_better(double v2, int a2, double v, int a, bool want_max)
+{
+    if (a2 < 0) return false;
+    if (a < 0) return true;
+    if (want_max ? v2 > v : v2 < v) return true;
+    return v2 == v && a2 < a;
+}
+
+// The cluster's peaks from its CTAs' block results, combined in rank order
+// through the slot `slot` of every CTA's parts (slots alternate, so one
+// cluster barrier per combination suffices).
+__device__ double eqh_cluster_peaks(cg::cluster_group &cl, EqPart *part, int &slot, int &pl, int &pr,
+                                    double &vl, double &vr)
+{
+    if (threadIdx.x == 0) part[slot] = EqPart{vl, vr, pl, pr};
+    cl.sync();
+    double bl = -INFINITY, br = -INFINITY;
+    int al = -1, ar = -1;
+    for (int r = 0; r < (int)cl.num_blocks(); ++r) {
+        const EqPart q = cl.map_shared_rank(part, r)[slot];
+        if (eqh_better(q.vl, q.pl, bl, al, true)) {
+            bl = q.vl;
+            al = q.pl;
+        }
+        if (eqh_better(q.vr, q.pr, br, ar, true)) {
+            br = q.vr;
+            ar = q.pr;
+        }
+    }
+    slot ^= 1;
+    vl = bl;
+    vr = br;
+    pl = al;
+    pr = ar;
+    return vl - vr;
+}
+
+// One cluster per data set (each CTA over its slice [e0, e1) of the bins):
+// bisection on g = ln P_low - ln P_high, then the barrier at Delta_eqh.
 __global__ void __launch_bounds__(kPkThreads)
 eqh_kernel(const double *__restrict__ lnn_all, const double *__restrict__ lnW, int nE, int e_min,
            int split, double beta, double lo, double hi, int n_iter, double *res, int *bad)
 {
     __shared__ double sh[32];
     __shared__ int shi[32];
-    const int d = blockIdx.x;
+    __shared__ EqPart part[2];
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncta = (int)cl.num_blocks(), q = (int)cl.block_rank();
+    const int d = blockIdx.x / ncta;
+    const int e0 = (int)((int64_t)nE * q / ncta), e1 = (int)((int64_t)nE * (q + 1) / ncta);
     const double *lnn = lnn_all + (size_t)d * nE;
+    int slot = 0;
+    auto peaks = [&](double bd, int &pl, int &pr, double &vl, double &vr) {
+        eqh_peaks(lnn, lnW, e0, e1, e_min, split, bd, pl, pr, vl, vr, sh, shi);
+        return eqh_cluster_peaks(cl, part, slot, pl, pr, vl, vr);
+    };
     int pl, pr;
     double vl, vr;
-    const double g_lo = eqh_peaks(lnn, lnW, nE, e_min, split, beta * lo, pl, pr, vl, vr, sh, shi);
+    const double g_lo = peaks(beta * lo, pl, pr, vl, vr);
     const bool ok_lo = pl >= 0 && pr >= 0;
-    const double g_hi = eqh_peaks(lnn, lnW, nE, e_min, split, beta * hi, pl, pr, vl, vr, sh, shi);
+    const double g_hi = peaks(beta * hi, pl, pr, vl, vr);
     if (!ok_lo || pl < 0 || pr < 0 || !(g_lo < 0.0 && g_hi > 0.0)) {
-        if (threadIdx.x == 0) bad[d] = 1;
+        if (q == 0 && threadIdx.x == 0) bad[d] = 1;
+        cl.sync();
         return;
     }
     for (int i = 0; i < n_iter; ++i) {
         const double mid = lo + 0.5 * (hi - lo);
-        if (eqh_peaks(lnn, lnW, nE, e_min, split, beta * mid, pl, pr, vl, vr, sh, shi) < 0.0) lo = mid;
+        if (peaks(beta * mid, pl, pr, vl, vr) < 0.0) lo = mid;
         else hi = mid;
     }
     const double dq = lo + 0.5 * (hi - lo);
     const double bd = beta * dq;
-    eqh_peaks(lnn, lnW, nE, e_min, split, bd, pl, pr, vl, vr, sh, shi);
+    peaks(bd, pl, pr, vl, vr);
     const double vmax = vl > vr ? vl : vr;
     double vmin = INFINITY;
     int pm = -1;
-    for (int e = pl + (int)threadIdx.x; e <= pr; e += blockDim.x) {
+    for (int e = max(pl, e0) + (int)threadIdx.x; e <= min(pr, e1 - 1); e += blockDim.x) {
         if (lnn[e] == -INFINITY) continue;
         const double v = eqh_lnp(lnn[e], bd, e_min + e, lnW[e]);
         if (pm < 0 || v < vmin) {
@@ -453,7 +510,20 @@ eqh_kernel(const double *__restrict__ lnn_all, const double *__restrict__ lnW, i
         }
     }
     eqh_best(vmin, pm, false, sh, shi);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) part[slot] = EqPart{vmin, 0.0, pm, -1};
+    cl.sync();
+    double bm = INFINITY;
+    int am = -1;
+    for (int r = 0; r < ncta; ++r) {
+        const EqPart qq = cl.map_shared_rank(part, r)[slot];
+        if (eqh_better(qq.vl, qq.pl, bm, am, false)) {
+            bm = qq.vl;
+            am = qq.pl;
+        }
+    }
+    vmin = bm;
+    pm = am;
+    if (q == 0 && threadIdx.x == 0) {
         double *o = res + 5 * (size_t)d;
         o[0] = dq;
         o[1] = (vmax - vmin) / (2.0 * beta * dq);
@@ -461,6 +531,7 @@ eqh_kernel(const double *__restrict__ lnn_all, const double *__restrict__ lnW, i
         o[3] = (double)(e_min + pr);
         o[4] = (double)(e_min + pm);
     }
+    cl.sync();
 }
 
 int pk_fail(int code, const std::string &msg)
@@ -470,6 +541,44 @@ int pk_fail(int code, const std::string &msg)
 }
 
 }  // namespace
+
+// Launch configuration of a per-data-set cluster kernel: one cluster per data
+// set and one CTA per SM (the CTAs reserve unused dynamic shared memory above
+// half an SM's); the cluster size is the largest of 8 .. 1 for which every
+// data set's cluster can be resident at once (clusters live within a GPC, so
+// the SM count alone does not tell).  attr must outlive cfg.
+static cudaError_t cluster_config(const void *kernel, int n_sets, cudaStream_t st,
+                                  cudaLaunchConfig_t &cfg, cudaLaunchAttribute (&attr)[1])
+{
+    int dev = 0, nsm = 152, smem_sm = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return ce;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const size_t one_per_sm = smem_sm > 0 ? (size_t)smem_sm / 2 + 1024 : 0;
+    ce = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)one_per_sm);
+    if (ce != cudaSuccess) return ce;
+    cfg = cudaLaunchConfig_t{};
+    cfg.blockDim = dim3(kPkThreads);
+    cfg.dynamicSmemBytes = one_per_sm;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncta = std::max(1, std::min(8, nsm / std::max(n_sets, 1)));
+    for (; ncta > 1; --ncta) {
+        attr[0].val.clusterDim.x = (unsigned)ncta;
+        cfg.gridDim = dim3((unsigned)(n_sets * ncta));
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, kernel, &cfg) == cudaSuccess && nc >= n_sets) break;
+    }
+    (void)cudaGetLastError();
+    attr[0].val.clusterDim.x = (unsigned)ncta;
+    cfg.gridDim = dim3((unsigned)(n_sets * ncta));
+    return cudaSuccess;
+}
 
 extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_rows,
                               int32_t row_len, int64_t row_stride, const double *lnW,
@@ -539,41 +648,9 @@ extern "C" int muca_find_peak(const int32_t *e_j, const int32_t *e_d, int64_t n_
         dim3 g2((unsigned)((n_e + 255) / 256), (unsigned)n_sets);
         jk_stats_kernel<<<g2, 256, 0, st>>>(cnt, sej, n_blocks, n_e, n_all, mj_all);
         PCK(cudaGetLastError());
-        // One cluster per data set, one CTA per SM: the CTAs reserve (unused)
-        // dynamic shared memory above half an SM's, and the cluster size is
-        // the largest of 8 .. 1 for which every data set's cluster can be
-        // resident at once (clusters live within a GPC, so the SM count alone
-        // does not tell).
-        int dev = 0, nsm = 152, smem_sm = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess) {
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        }
-        const size_t one_per_sm = smem_sm > 0 ? (size_t)smem_sm / 2 + 1024 : 0;
-        PCK(cudaFuncSetAttribute(peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)one_per_sm));
-        cudaLaunchConfig_t cfg = {};
-        cfg.blockDim = dim3(kPkThreads);
-        cfg.dynamicSmemBytes = one_per_sm;
-        cfg.stream = st;
+        cudaLaunchConfig_t cfg;
         cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int ncta = std::max(1, std::min(8, nsm / n_sets));
-        for (; ncta > 1; --ncta) {
-            attr[0].val.clusterDim.x = (unsigned)ncta;
-            cfg.gridDim = dim3((unsigned)(n_sets * ncta));
-            int nc = 0;
-            if (cudaOccupancyMaxActiveClusters(&nc, peak_kernel, &cfg) == cudaSuccess &&
-                nc >= n_sets)
-                break;
-        }
-        (void)cudaGetLastError();
-        attr[0].val.clusterDim.x = (unsigned)ncta;
-        cfg.gridDim = dim3((unsigned)(n_sets * ncta));
+        PCK(cluster_config((const void *)peak_kernel, n_sets, st, cfg, attr));
         PCK(cudaLaunchKernelEx(&cfg, peak_kernel, (const double *)n_all, (const double *)mj_all,
                                (const double *)d_lnW, (int)n_e, (int)e_min, beta, delta_lo,
                                delta_hi, (int)n_iter, d_res, d_bad + 1, d_w));
@@ -691,9 +768,12 @@ extern "C" int muca_equal_height(const int32_t *e_d, int64_t n_rows, int32_t row
         dim3 g2((unsigned)((n_e + 255) / 256), (unsigned)n_sets);
         jk_lncount_kernel<<<g2, 256, 0, st>>>(cnt, n_blocks, n_e, lnn);
         PCK(cudaGetLastError());
-        eqh_kernel<<<n_sets, kPkThreads, 0, st>>>(lnn, d_lnW, n_e, e_min, split, beta, delta_lo,
-                                                  delta_hi, n_iter, d_res, d_bad + 1);
-        PCK(cudaGetLastError());
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute attr[1];
+        PCK(cluster_config((const void *)eqh_kernel, n_sets, st, cfg, attr));
+        PCK(cudaLaunchKernelEx(&cfg, eqh_kernel, (const double *)lnn, (const double *)d_lnW,
+                               (int)n_e, (int)e_min, (int)split, beta, delta_lo, delta_hi,
+                               (int)n_iter, d_res, d_bad + 1));
     }
     PCK(cudaMemcpyAsync(res.data(), d_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     PCK(cudaMemcpyAsync(bad.data(), d_bad, bad.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
