@@ -933,7 +933,7 @@ int reweight_on_scratch(const int32_t *e_j, const int32_t *e_d, const int32_t *m
         for (int64_t r0 = 0; r0 < n_rows; r0 += rows_pass) {
             const int64_t nr = std::min(rows_pass, n_rows - r0);
             const int64_t off = r0 * row_stride;
-            // one block per SM: fewer (bucket, block) write streams
+            // one 1024-thread block per SM
             const int g = (int)std::min<int64_t>(nr * cpr, std::min(nsm, kMaxG));
             bucket_count_kernel<<<g, kCsThreads, 0, st>>>(e_d + off, nr, row_len, row_stride,
                                                           e_min, n_e, nbk, cpr, d_cnt,
