@@ -1,8 +1,10 @@
 """The N-GPU form of the benchmark and the walker-sharded merge (Sec. II's
 parallel scheme over ranks).  Their cross-rank steps run here as two gloo
 ranks on the CPU (no GPU involved): the whole job's rate over the slowest
-rank, and a sharded run whose merged histograms, weights and tables equal one
-rank holding all the walkers."""
+rank, a sharded run whose merged histograms, weights and tables equal one
+rank holding all the walkers, and a rank that leaves between iterations
+(the next merge ends with an error instead of hanging, and the weights stay
+those of the last good merge)."""
 import os
 import socket
 
@@ -130,3 +132,75 @@ def test_two_ranks_sharded_merge_equals_one_rank():
         for w, s in spins.items():
             assert np.array_equal(s, ref["spins"][w]), (r, w)
     assert sorted(w for r in range(world) for w in res[r][3]) == list(range(W))
+
+
+def _leaving_rank(rank, world, port, out, stall=0.0):
+    """Rank 1 takes part in the first merge, then leaves between iterations:
+    its process ends without joining the second merge, after `stall` seconds
+    alive (a rank that hangs); rank 0 runs its second merge with a short
+    process-group timeout."""
+    import sys
+    from datetime import timedelta
+
+    sys.path.insert(0, os.path.dirname(HERE))
+    import time
+
+    import numpy as np
+
+    from paper_1502_07214_gb300 import muca, shard
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=5))
+    V = 64
+    lnW = np.zeros(V + 1)
+    H = np.full(V + 1, 3 + rank, dtype=np.uint64)
+    merged = shard.host_merge_update(H, lnW, dist.all_reduce)
+    if rank == 1:
+        out[rank] = ("left", merged.copy(), lnW.copy())
+        time.sleep(stall)
+        return  # leaves between iterations: no destroy, no second merge
+    before = lnW.copy()
+    t0 = time.monotonic()
+    try:
+        shard.host_merge_update(H, lnW, dist.all_reduce)
+        outcome = "merged"
+    except Exception as e:  # the missing rank ends the collective with an error
+        outcome = type(e).__name__
+    waited = time.monotonic() - t0
+    # the library still serves this rank: a local update on a copy of the weights
+    probe = lnW.copy()
+    muca.weight_update(muca.REC_PLAIN, H, probe)
+    out[rank] = (outcome, merged.copy(), lnW.copy(), before, waited, probe)
+    try:
+        dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+@pytest.mark.parametrize("stall", [0.0, 12.0])
+def test_a_rank_that_leaves_ends_the_next_merge_with_an_error(stall):
+    """Failure detection on the host: after one good merge (both ranks' integer
+    histograms summed), rank 1 leaves between iterations, at once (its
+    connections close) or after hanging for longer than the process group's
+    5 s timeout.  Rank 0's next merge does not hang: the collective ends with
+    an error (at once, or when the timeout runs out), and rank 0's weights are
+    those of the last good merge (the update runs only on a merged
+    histogram), so the run can continue from its last checkpoint."""
+    world = 2
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_leaving_rank, args=(world, port, out, stall), nprocs=world, join=True)
+        res = dict(out)
+    import numpy as np
+
+    outcome, merged0, lnW0, before, waited, probe = res[0]
+    left, merged1, lnW1 = res[1]
+    assert left == "left"
+    assert np.array_equal(merged0, np.full(65, 7, dtype=np.uint64))
+    assert np.array_equal(merged0, merged1) and np.array_equal(lnW1, before)
+    assert np.allclose(before, -np.log(7.0))  # lnW -= ln H after the good merge
+    assert outcome != "merged", "a merge without rank 1 must not succeed"
+    assert np.array_equal(lnW0, before), "a failed merge must leave lnW unchanged"
+    assert waited < (2.0 if stall == 0.0 else 11.0)
+    assert np.allclose(probe, before - np.log(3.0))
