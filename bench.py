@@ -688,6 +688,29 @@ def run_profile_case(what, cfg):
         ctx.sync()
         print("profile case: bonds", ctx.get_config(0))
         ctx.close()
+    elif what == "peak":
+        # Delta*_L (20, 0 and 200 jackknife blocks) and the equal-height search
+        # (20 and 0) on the reweight workload, four calls each, the bracket
+        # from an FP64 reweighting as in the benchmark's reweight leg
+        r = wl.REWEIGHT
+        ej, ed, m, lnW, dt = wl.synthetic_series()
+        beta, V = 1.0 / r["T"], r["L"] ** 3
+        dj, dd, dm = (torch.from_numpy(a.ravel()).cuda() for a in (ej, ed, m))
+        grid = wl.delta_grid(dt)
+        c = muca.reweight(dj, dd, dm, lnW, 0, beta, V, grid, 64)[:, 2]
+        k = int(np.argmax(c))
+        lo, hi = grid[max(k - 8, 0)], grid[min(k + 8, len(grid) - 1)]
+        for nj in (20, 0, 200):
+            for _ in range(4):
+                muca.find_peak(dj.view(ed.shape), dd.view(ed.shape), lnW, 0, beta, lo, hi,
+                               n_jack=nj)
+        split = int(0.525 * V)
+        for nj in (20, 0):
+            for _ in range(4):
+                muca.equal_height(dd.view(ed.shape), lnW, 0, beta, split, lo - 0.01, hi + 0.01,
+                                  n_jack=nj)
+        torch.cuda.synchronize()
+        print("profile case: peak")
     else:
         r = wl.REWEIGHT
         ej, ed, m, lnW, dt = wl.synthetic_series()
@@ -705,7 +728,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--profile", choices=["sweep", "reweight", "probes", "bonds"],
+    ap.add_argument("--profile", choices=["sweep", "reweight", "probes", "bonds", "peak"],
                     help="run a short untimed case for a profiler capture and exit")
     ap.add_argument("--profile-config", default="1,4,8",
                     help="sweep kernel configuration of --profile sweep")
